@@ -1,0 +1,375 @@
+"""FP64 CPU oracle for the segmented pull gather of Cagra
+("Making Caches Work for Graph Analytics", arXiv 1608.01362).
+
+TEST INFRASTRUCTURE.  Only ``tests/``, ``__graft_entry__.smoke()`` and the
+CPU-baseline leg of ``bench.py`` may import it; the product path never does.
+It is a plain, slow, obviously-correct restatement of what the hot path
+computes, in FP64, sharing no code with the CUDA library (its C part is
+``oracle.c``; the rest is numpy).  Each function cites the passage it follows.
+
+Readings of the paper that the oracle fixes (the paper is silent or loose):
+  * PageRank is the normalised form r_0 = 1/V,
+    r'[v] = (1-d)/V + d (sum_{u->v} r[u]/outdeg(u) + D/V), D = rank mass of
+    dangling vertices (Algorithm 5 prints the unnormalised 0.15 + 0.85 sum and
+    divides by a possibly-zero out-degree); fixed iteration count, no early
+    stop; d = 0.85.
+  * Segments are contiguous source-ID ranges [bounds[s], bounds[s+1]); the
+    paper's uniform choice is bounds[s] = min(s*N, V) with N = ceil(V/k)
+    (Algorithm 2's segmentID = src / N).
+  * Frequency-based clustering (Section V): mode 0 = stable sort by out-degree,
+    descending (ties keep ascending vertex ID); mode 1 = stable sort by
+    floor(outdeg / max(1, floor(E/V))), descending (the paper's "out-degree /
+    threshold" with the average degree as threshold).
+  * Label propagation is synchronous and includes the vertex's own label.
+  * Collaborative filtering uses the degree-averaged gradient (see orc_cf_sweep).
+  * Batched personalised PageRank returns dangling mass to each column's seed.
+
+Pins (tests/test_oracle_pins.py): directed cycle, in-star closed form, rank
+mass 1, dense brute-force power iteration and the linear-system fixed point,
+Fig. 4's destination sets and expansion factor 7/6, segment invariants,
+k = 1 segmented == plain bit for bit, label propagation == connected
+components (scipy), reverse-path pass count, CF gradient == finite
+differences of the loss, PPR column sums and one-hot equivalence.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "oracle.c")
+_SO = os.path.join(_HERE, "_oracle.so")
+_lock = threading.Lock()
+_lib = None
+
+DAMPING = 0.85
+
+
+def build(force: bool = False) -> str:
+    """Compile oracle.c in-tree (gcc, OpenMP when available)."""
+    if not force and os.path.exists(_SO) and os.path.getmtime(_SO) >= os.path.getmtime(_SRC):
+        return _SO
+    tmp = _SO + f".tmp{os.getpid()}"
+    base = ["gcc", "-O2", "-std=c11", "-shared", "-fPIC", _SRC, "-o", tmp, "-lm"]
+    try:
+        subprocess.run(base[:2] + ["-fopenmp"] + base[2:], check=True, capture_output=True)
+    except subprocess.CalledProcessError:
+        subprocess.run(base, check=True, capture_output=True)
+    os.replace(tmp, _SO)
+    return _SO
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            lib = ctypes.CDLL(build())
+            i64, i32, dbl, vp = ctypes.c_int64, ctypes.c_int32, ctypes.c_double, ctypes.c_void_p
+            lib.orc_out_degree.restype = None
+            lib.orc_out_degree.argtypes = [i64, vp, vp, vp]
+            lib.orc_pagerank.restype = ctypes.c_int
+            lib.orc_pagerank.argtypes = [i64, vp, vp, i32, dbl, vp, vp]
+            lib.orc_segments_count.restype = ctypes.c_int
+            lib.orc_segments_count.argtypes = [i64, vp, vp, i32, vp, vp, vp]
+            lib.orc_segments_fill.restype = ctypes.c_int
+            lib.orc_segments_fill.argtypes = [i64, vp, vp, i32, vp, i64, vp, vp, vp, vp, vp, vp]
+            lib.orc_pagerank_segmented.restype = ctypes.c_int
+            lib.orc_pagerank_segmented.argtypes = [i64, i32, i64, vp, vp, vp, vp, vp, vp, i32,
+                                                   dbl, vp, vp]
+            lib.orc_label_propagation.restype = i64
+            lib.orc_label_propagation.argtypes = [i64, vp, vp, vp, i64, vp]
+            lib.orc_ppr.restype = ctypes.c_int
+            lib.orc_ppr.argtypes = [i64, vp, vp, i32, vp, i32, dbl, vp]
+            lib.orc_cf_sweep.restype = ctypes.c_int
+            lib.orc_cf_sweep.argtypes = [i64, i64, i32, vp, vp, vp, vp, vp, vp, dbl, dbl, vp, vp,
+                                         vp]
+            lib.orc_num_threads.restype = ctypes.c_int
+            lib.orc_num_threads.argtypes = []
+            _lib = lib
+    return _lib
+
+
+def _c(a, dtype):
+    return np.ascontiguousarray(np.asarray(a, dtype=dtype))
+
+
+def num_threads() -> int:
+    return int(_load().orc_num_threads())
+
+
+# --------------------------------------------------------------------------
+# Degrees (Algorithm 1's `degree` array; Algorithm 5's contrib = rank/outDegree)
+# --------------------------------------------------------------------------
+
+def out_degree(offsets, src) -> np.ndarray:
+    """Out-degree of each vertex from an in-edge CSR (Section II-A)."""
+    offsets = _c(offsets, np.int64)
+    src = _c(src, np.int32)
+    V = offsets.shape[0] - 1
+    out = np.empty(V, dtype=np.int64)
+    _load().orc_out_degree(V, offsets.ctypes.data, src.ctypes.data, out.ctypes.data)
+    return out
+
+
+# --------------------------------------------------------------------------
+# PageRank (Algorithm 1 + Algorithm 5, normalised; see module docstring)
+# --------------------------------------------------------------------------
+
+def pagerank(offsets, src, iters: int = 20, d: float = DAMPING, rank0=None):
+    """Plain pull PageRank in FP64.  Returns (rank, residuals per iteration)."""
+    offsets = _c(offsets, np.int64)
+    src = _c(src, np.int32)
+    V = offsets.shape[0] - 1
+    rank = np.full(V, 1.0 / V) if rank0 is None else _c(rank0, np.float64).copy()
+    resid = np.zeros(max(iters, 1))
+    if _load().orc_pagerank(V, offsets.ctypes.data, src.ctypes.data, iters, d, rank.ctypes.data,
+                            resid.ctypes.data) != 0:
+        raise MemoryError("oracle: pagerank allocation failed")
+    return rank, resid[:iters]
+
+
+def pagerank_step_rows(offsets, src, outdeg, rank_in, rows, d: float = DAMPING) -> np.ndarray:
+    """One iteration of the same update evaluated only at destination `rows`,
+    from a given input rank vector (FP64).  Lets a full-size run be checked
+    one sampled output at a time."""
+    offsets = np.asarray(offsets)
+    V = offsets.shape[0] - 1
+    rank_in = np.asarray(rank_in, dtype=np.float64)
+    dang = np.asarray(outdeg) == 0
+    D = 0.0
+    for x in rank_in[dang]:
+        D += float(x)
+    out = np.empty(len(rows))
+    for j, v in enumerate(rows):
+        lo, hi = int(offsets[v]), int(offsets[v + 1])
+        s = 0.0
+        for u in np.asarray(src[lo:hi]):
+            s += rank_in[u] / float(outdeg[u])
+        out[j] = (1.0 - d) / V + d * (s + D / V)
+    return out
+
+
+# --------------------------------------------------------------------------
+# Frequency-based clustering (Section V)
+# --------------------------------------------------------------------------
+
+def cluster(outdeg, mode: int = 0, E: int | None = None):
+    """Stable degree-driven renumbering.  Returns (new_of_old, old_of_new).
+
+    mode 0: key = out-degree; mode 1: key = floor(outdeg / max(1, floor(E/V))).
+    Vertices are ordered by key descending; equal keys keep their old order
+    (the paper's parallel stable sort on out-degree/threshold)."""
+    outdeg = np.asarray(outdeg, dtype=np.int64)
+    V = outdeg.shape[0]
+    if mode == 0:
+        key = outdeg
+    elif mode == 1:
+        if E is None:
+            E = int(outdeg.sum())
+        thr = max(1, E // max(V, 1))
+        key = outdeg // thr
+    else:
+        raise ValueError("mode must be 0 or 1")
+    old_of_new = np.argsort(-key, kind="stable").astype(np.int32)
+    new_of_old = np.empty(V, dtype=np.int32)
+    new_of_old[old_of_new] = np.arange(V, dtype=np.int32)
+    return new_of_old, old_of_new
+
+
+def relabel(offsets, src, new_of_old, old_of_new):
+    """Apply the renumbering to an in-edge CSR: new row n is old row
+    old_of_new[n], each source replaced by new_of_old[source], in-row order
+    kept (Section V: the mapping updates the vertex index in G.edgeArray)."""
+    offsets = np.asarray(offsets, dtype=np.int64)
+    src = np.asarray(src, dtype=np.int32)
+    old_of_new = np.asarray(old_of_new, dtype=np.int64)
+    lens = np.diff(offsets)[old_of_new]
+    noff = np.zeros(offsets.shape[0], dtype=np.int64)
+    np.cumsum(lens, out=noff[1:])
+    starts = offsets[old_of_new]
+    # gather index of every new edge position
+    pos = np.repeat(starts - noff[:-1], lens) + np.arange(noff[-1], dtype=np.int64)
+    nsrc = np.asarray(new_of_old, dtype=np.int32)[src[pos]]
+    return noff, nsrc.astype(np.int32)
+
+
+# --------------------------------------------------------------------------
+# Segmenting (Algorithm 2) and segmented PageRank (Algorithms 3, 4)
+# --------------------------------------------------------------------------
+
+def uniform_bounds(V: int, k: int) -> np.ndarray:
+    """Algorithm 2's segments: N = ceil(V/k) vertices each, the last short."""
+    N = -(-V // k) if V else 0
+    return np.array([min(s * N, V) for s in range(k + 1)], dtype=np.int64)
+
+
+@dataclass
+class Segments:
+    V: int
+    k: int
+    B: int
+    bounds: np.ndarray       # int64[k+1]  source range of each segment
+    row_base: np.ndarray     # int64[k+1]
+    edge_base: np.ndarray    # int64[k+1]
+    row_ptr: np.ndarray      # int64[rows+1]
+    col: np.ndarray          # int32[E]
+    idx_map: np.ndarray      # int32[rows]
+    block_start: np.ndarray  # int32[k*(nb+1)]
+
+    @property
+    def rows(self) -> int:
+        return int(self.row_base[-1])
+
+    @property
+    def nblocks(self) -> int:
+        return -(-self.V // self.B)
+
+    @property
+    def q(self) -> float:
+        """Expansion factor q = s_adj / s (Section III-D): the mean number of
+        segments that contribute to a vertex = total subgraph rows / V."""
+        return self.rows / self.V if self.V else 0.0
+
+
+def build_segments(offsets, src, k: int | None = None, B: int = 2048, bounds=None) -> Segments:
+    """Algorithm 2 (Section III-A): subgraphs of the in-edges grouped by source
+    segment, each with idxMap, block indices for the merge and a CSR."""
+    offsets = _c(offsets, np.int64)
+    src = _c(src, np.int32)
+    V = offsets.shape[0] - 1
+    if bounds is None:
+        bounds = uniform_bounds(V, k)
+    bounds = _c(bounds, np.int64)
+    k = bounds.shape[0] - 1
+    if k < 1 or bounds[0] != 0 or bounds[-1] != V or np.any(np.diff(bounds) < 0) or B < 1:
+        raise ValueError("bad segment bounds or block size")
+    lib = _load()
+    row_base = np.empty(k + 1, dtype=np.int64)
+    edge_base = np.empty(k + 1, dtype=np.int64)
+    if lib.orc_segments_count(V, offsets.ctypes.data, src.ctypes.data, k, bounds.ctypes.data,
+                              row_base.ctypes.data, edge_base.ctypes.data) != 0:
+        raise MemoryError("oracle: segment count failed")
+    rows = int(row_base[-1])
+    E = int(edge_base[-1])
+    nb = -(-V // B)
+    row_ptr = np.empty(rows + 1, dtype=np.int64)
+    col = np.empty(max(E, 1), dtype=np.int32)
+    idx_map = np.empty(max(rows, 1), dtype=np.int32)
+    block_start = np.empty(k * (nb + 1), dtype=np.int32)
+    if lib.orc_segments_fill(V, offsets.ctypes.data, src.ctypes.data, k, bounds.ctypes.data, B,
+                             row_base.ctypes.data, edge_base.ctypes.data, row_ptr.ctypes.data,
+                             col.ctypes.data, idx_map.ctypes.data,
+                             block_start.ctypes.data) != 0:
+        raise MemoryError("oracle: segment fill failed")
+    return Segments(V, k, B, bounds, row_base, edge_base, row_ptr, col[:E], idx_map[:rows],
+                    block_start)
+
+
+def pagerank_segmented(seg: Segments, outdeg, iters: int = 20, d: float = DAMPING, rank0=None):
+    """PageRank computed through the segmented structure, FP64 (Algorithms
+    3 and 4 followed by the vertex update).  Returns (rank, residuals)."""
+    V = seg.V
+    outdeg = _c(outdeg, np.int64)
+    rank = np.full(V, 1.0 / V) if rank0 is None else _c(rank0, np.float64).copy()
+    resid = np.zeros(max(iters, 1))
+    col = seg.col if seg.col.size else np.zeros(1, np.int32)
+    idx = seg.idx_map if seg.idx_map.size else np.zeros(1, np.int32)
+    if _load().orc_pagerank_segmented(V, seg.k, seg.B, seg.row_base.ctypes.data,
+                                      seg.row_ptr.ctypes.data, col.ctypes.data, idx.ctypes.data,
+                                      seg.block_start.ctypes.data, outdeg.ctypes.data, iters, d,
+                                      rank.ctypes.data, resid.ctypes.data) != 0:
+        raise MemoryError("oracle: segmented pagerank allocation failed")
+    return rank, resid[:iters]
+
+
+# --------------------------------------------------------------------------
+# Label propagation (Table IV; min-label connected components)
+# --------------------------------------------------------------------------
+
+def label_propagation(offsets, src, labels0, max_passes: int = 1 << 30):
+    """Synchronous min-label passes until no label changes.
+    Returns (labels, passes, changes_per_pass)."""
+    offsets = _c(offsets, np.int64)
+    src = _c(src, np.int32)
+    V = offsets.shape[0] - 1
+    labels = _c(labels0, np.int32).copy()
+    cap = min(max_passes, V + 2)
+    changes = np.zeros(max(cap, 1), dtype=np.int64)
+    p = _load().orc_label_propagation(V, offsets.ctypes.data, src.ctypes.data, labels.ctypes.data,
+                                      cap, changes.ctypes.data)
+    if p < 0:
+        raise MemoryError("oracle: label propagation allocation failed")
+    return labels, int(p), changes[:p]
+
+
+def label_propagation_pass(offsets, src, labels):
+    """Exactly one synchronous pass; returns (new_labels, changed)."""
+    out, p, ch = label_propagation(offsets, src, labels, max_passes=1)
+    return out, int(ch[0]) if p else 0
+
+
+# --------------------------------------------------------------------------
+# Batched personalised PageRank (64 columns)
+# --------------------------------------------------------------------------
+
+def ppr(offsets, src, seeds, iters: int = 20, d: float = DAMPING) -> np.ndarray:
+    """Personalised PageRank for every seed at once; returns R[V, J] (FP64)."""
+    offsets = _c(offsets, np.int64)
+    src = _c(src, np.int32)
+    seeds = _c(seeds, np.int32)
+    V = offsets.shape[0] - 1
+    J = seeds.shape[0]
+    R = np.empty((V, J), dtype=np.float64)
+    if _load().orc_ppr(V, offsets.ctypes.data, src.ctypes.data, J, seeds.ctypes.data, iters, d,
+                       R.ctypes.data) != 0:
+        raise MemoryError("oracle: ppr allocation failed")
+    return R
+
+
+# --------------------------------------------------------------------------
+# Collaborative filtering (Table III)
+# --------------------------------------------------------------------------
+
+def item_major(U: int, I: int, user_offsets, items, ratings):
+    """Transpose a user-major rating CSR into item-major (users ascending)."""
+    user_offsets = np.asarray(user_offsets, dtype=np.int64)
+    items = np.asarray(items, dtype=np.int64)
+    users = np.repeat(np.arange(U, dtype=np.int64), np.diff(user_offsets))
+    order = np.lexsort((users, items))
+    ioff = np.zeros(I + 1, dtype=np.int64)
+    np.cumsum(np.bincount(items, minlength=I), out=ioff[1:])
+    return ioff, users[order].astype(np.int32), np.asarray(ratings, dtype=np.uint8)[order]
+
+
+def cf_sweep(U, I, uoff, uitem, urate, ioff, iuser, irate, P, Q, lam=0.05, step=1e-3):
+    """One Jacobi gradient sweep in FP64 (degree-averaged gradient).
+    Returns (P', Q', sse of the old P, Q)."""
+    P = _c(P, np.float64).copy()
+    Q = _c(Q, np.float64).copy()
+    K = P.shape[1]
+    uoff, ioff = _c(uoff, np.int64), _c(ioff, np.int64)
+    uitem, iuser = _c(uitem, np.int32), _c(iuser, np.int32)
+    urate, irate = _c(urate, np.uint8), _c(irate, np.uint8)
+    sse = ctypes.c_double()
+    if _load().orc_cf_sweep(U, I, K, uoff.ctypes.data, uitem.ctypes.data, urate.ctypes.data,
+                            ioff.ctypes.data, iuser.ctypes.data, irate.ctypes.data, lam, step,
+                            P.ctypes.data, Q.ctypes.data, ctypes.byref(sse)) != 0:
+        raise ValueError("oracle: cf sweep failed (K out of range or allocation)")
+    return P, Q, float(sse.value)
+
+
+def cf_sse(uoff, uitem, urate, P, Q) -> float:
+    """sum over ratings of (r_ui - p_u . q_i)^2 in FP64 (user-major order)."""
+    U = len(uoff) - 1
+    tot = 0.0
+    for u in range(U):
+        lo, hi = int(uoff[u]), int(uoff[u + 1])
+        if hi > lo:
+            e = urate[lo:hi].astype(np.float64) - Q[uitem[lo:hi]] @ P[u]
+            tot += float(np.dot(e, e))
+    return tot
