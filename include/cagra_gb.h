@@ -1,0 +1,279 @@
+/*
+ * cagra_gb — C ABI of the GB300 (sm_103a) implementation of the segmented
+ * pull gather of "Making Caches Work for Graph Analytics" (Cagra,
+ * arXiv 1608.01362): CSR segmenting (Section III), frequency-based
+ * clustering (Section V) and the applications built on them.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - Graphs are in-edge CSR (Section II-A): row v of (offsets, src) lists the
+ *    sources u of the edges u -> v.  offsets has V+1 entries (int64), src has
+ *    E entries (int32, each in [0, V)).  V < 2^31, E < 2^31.
+ *  - Every pointer argument named dev_* or documented "device" is a device
+ *    pointer owned by the CALLER (allocated, e.g., by PyTorch) unless stated
+ *    otherwise; "host" pointers are ordinary host memory.  Opaque handles
+ *    (cg_segmented, cg_plain) are owned by the LIBRARY: *_create / build
+ *    allocates, *_destroy frees.
+ *  - Every call is asynchronous on the given stream and returns an int
+ *    status: CG_OK (0) or a negative CG_ERR_* code.  Argument checks happen
+ *    on the host before anything is enqueued; on error nothing is enqueued
+ *    and cg_last_error_message() (thread-local) explains.  Calls that must
+ *    read a device result on the host (noted below) synchronize the stream.
+ *  - No entry point spins on device flags; no kernel waits on another.
+ *  - Handles are bound to the device that was current when they were built;
+ *    use them with that device current.
+ */
+#ifndef CAGRA_GB_H
+#define CAGRA_GB_H
+
+#include <stdint.h>
+#include <stddef.h>
+#include <cuda_runtime_api.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---------------------------------------------------------------- status */
+#define CG_OK 0
+#define CG_ERR_INVALID_ARG (-1)
+#define CG_ERR_OOM (-2)
+#define CG_ERR_CUDA (-3)
+#define CG_ERR_TIMEOUT (-4)
+#define CG_ERR_UNSUPPORTED (-5)
+
+/* Static text for a status code. */
+const char *cg_status_string(int status);
+/* Text of the last error raised on the calling thread ("" if none). */
+const char *cg_last_error_message(void);
+/* Library version as MAJOR*10000 + MINOR*100 + PATCH. */
+int cg_version(void);
+
+/* ---------------------------------------------------------------- degrees */
+
+/*
+ * Out-degree of every vertex (the `degree` array of Algorithm 1): the number
+ * of entries of src equal to u.  dev_src: int32[E]; dev_outdeg: int32[V],
+ * overwritten.  Errors: CG_ERR_INVALID_ARG on V < 1, E < 0 or a null pointer
+ * with E > 0.
+ */
+int cg_out_degree(const int32_t *dev_src, int64_t E, int32_t V,
+                  int32_t *dev_outdeg, cudaStream_t stream);
+
+/*
+ * Reciprocal out-degree (Section VI-B's reciprocal optimisation, Algorithm
+ * 5's contrib = rank / outDegree): inv[u] = 1/outdeg[u] in FP32, 0 for a
+ * dangling vertex (outdeg 0).  dev_outdeg: int32[V]; dev_inv: float[V].
+ */
+int cg_inv_outdeg(const int32_t *dev_outdeg, int32_t V, float *dev_inv,
+                  cudaStream_t stream);
+
+/* ---------------------------------------------------------------- clustering */
+
+/*
+ * Frequency-based clustering (Section V): a stable sort of the vertices on a
+ * degree key, hottest first.  mode 0: key = out-degree; mode 1: key =
+ * floor(out-degree / max(1, floor(E/V))) (out-degree over the average-degree
+ * threshold).  Vertices with equal keys keep their ascending-ID order.
+ * dev_outdeg: int32[V] (from cg_out_degree); outputs dev_new_of_old and
+ * dev_old_of_new: int32[V], each the inverse of the other.  Bit-exact and
+ * deterministic.  Uses stream-ordered scratch (cudaMallocAsync) of about
+ * 16 V bytes, freed before return (CG_ERR_OOM if it cannot be had).
+ */
+int cg_cluster(const int32_t *dev_outdeg, int32_t V, int64_t E, int32_t mode,
+               int32_t *dev_new_of_old, int32_t *dev_old_of_new,
+               cudaStream_t stream);
+
+/*
+ * Renumber an in-edge CSR with a clustering permutation (Section V: the map
+ * updates the vertex index in G.edgeArray): new row n is old row
+ * old_of_new[n], each source u replaced by new_of_old[u], in-row order kept.
+ * Outputs dev_out_offsets: int64[V+1], dev_out_src: int32[E] (must not alias
+ * the inputs).  Scratch: 8 (V+1) bytes, stream-ordered.
+ */
+int cg_relabel_csr(const int64_t *dev_offsets, const int32_t *dev_src,
+                   int32_t V, int64_t E, const int32_t *dev_new_of_old,
+                   const int32_t *dev_old_of_new, int64_t *dev_out_offsets,
+                   int32_t *dev_out_src, cudaStream_t stream);
+
+/*
+ * Gather of 4-byte values through an index: out[i] = in[idx[i]] for
+ * i in [0, n) (0 where idx[i] is outside [0, n_in)).  Used to carry vertex
+ * data between the original and the clustered numbering (Section V keeps
+ * both directions of the map): with idx = new_of_old it returns a vector in
+ * original IDs from one in clustered IDs.  in/out must not alias.
+ */
+int cg_permute4(const void *dev_in, int64_t n_in, const int32_t *dev_idx,
+                int64_t n, void *dev_out, cudaStream_t stream);
+
+/* ---------------------------------------------------------------- segmenting */
+
+typedef struct cg_segmented cg_segmented;
+
+typedef struct {
+  int32_t V;             /* vertices */
+  int64_t E;             /* edges */
+  int32_t num_segments;  /* k */
+  int32_t merge_block;   /* B: destinations per merge block */
+  int32_t num_blocks;    /* ceil(V / B) */
+  int64_t rows;          /* total subgraph rows = sum_s |dst(s)| = q V */
+  double q;              /* expansion factor rows / V (Section III-D) */
+  int64_t device_bytes;  /* device memory held by the handle */
+  int64_t gather_tiles;  /* work tiles of one segment-processing pass */
+} cg_segmented_info;
+
+/*
+ * Preprocessing of Algorithm 2 (Section III-A).  Sources are split into k
+ * contiguous ranges [bounds[s], bounds[s+1]); host_bounds (host int64[k+1],
+ * bounds[0] = 0, bounds[k] = V, non-decreasing) may be NULL for the paper's
+ * uniform split bounds[s] = min(s N, V), N = ceil(V/k).  Subgraph s keeps
+ * every in-edge whose source lies in segment s, grouped by destination in
+ * the parent's row order, parent edge order kept inside a row; it gets an
+ * idxMap (local row -> global destination) and the block indices of the
+ * cache-aware merge for blocks of merge_block destinations (Algorithm 4).
+ * The handle also owns the intermediate buffers (intermBuf) and the tiling
+ * of the gather.  Inputs: device CSR as in the conventions; 1 <= k <= 1024;
+ * 1 <= merge_block <= 12288.  The call synchronizes the stream (it reads
+ * segment sizes on the host).  Errors: CG_ERR_INVALID_ARG, CG_ERR_OOM,
+ * CG_ERR_CUDA.  Empty segments are legal.
+ */
+int pr_build_segments(const int64_t *dev_offsets, const int32_t *dev_src,
+                      int32_t V, int64_t E, int32_t num_segments,
+                      const int64_t *host_bounds, int32_t merge_block,
+                      cg_segmented **out, cudaStream_t stream);
+
+/* Sizes of a segmented graph (host struct, no device work). */
+int cg_segmented_get_info(const cg_segmented *seg, cg_segmented_info *info);
+
+/*
+ * Copy the segmented structure out in its canonical flat layout (the layout
+ * the FP64 oracle also builds):
+ *   host_bounds    int64[k+1]  source range of each segment
+ *   host_row_base  int64[k+1]  first subgraph row of each segment
+ *   host_edge_base int64[k+1]  first edge of each segment
+ *   dev_row_ptr    int64[rows+1] first edge of each subgraph row
+ *   dev_col        int32[E]     global source of each edge
+ *   dev_idx_map    int32[rows]  global destination of each subgraph row
+ *   dev_block_start int32[k*(num_blocks+1)] local row (row - row_base[s]) of
+ *                  segment s where block b's destinations begin
+ * Any pointer may be NULL to skip that array.  Synchronizes the stream.
+ */
+int cg_segmented_export(const cg_segmented *seg, int64_t *host_bounds,
+                        int64_t *host_row_base, int64_t *host_edge_base,
+                        int64_t *dev_row_ptr, int32_t *dev_col,
+                        int32_t *dev_idx_map, int32_t *dev_block_start,
+                        cudaStream_t stream);
+
+/* Free a segmented graph (synchronizes the device first).  NULL is a no-op. */
+int cg_segmented_destroy(cg_segmented *seg);
+
+#define CG_OP_SUM_F32 0
+#define CG_OP_MIN_I32 1
+
+/*
+ * Parallel segment processing alone (Algorithm 3, Section III-B): for every
+ * subgraph row i, interm[i] = op over the row's edges of x[col[e]] (SUM_F32:
+ * FP32 sum; MIN_I32: int32 minimum).  Subgraphs are processed in segment
+ * order; no atomics.  dev_x: float[V] or int32[V]; dev_interm: rows entries
+ * of the same type (caller-owned), or NULL for the handle's own intermBuf
+ * (the buffer pr_merge_update reads).
+ */
+int cg_seg_gather(const cg_segmented *seg, int32_t op, const void *dev_x,
+                  void *dev_interm, cudaStream_t stream);
+
+/*
+ * Cache-aware merge alone (Algorithm 4, Section III-C): for each block of
+ * merge_block destinations, out[v] = identity (0 / INT32_MAX), then for each
+ * segment in ascending order, for its rows i in the block,
+ * out[idx_map[i]] = op(out[idx_map[i]], interm[i]).  dev_interm: rows
+ * entries; dev_out: V entries.
+ */
+int merge(const cg_segmented *seg, int32_t op, const void *dev_interm,
+          void *dev_out, cudaStream_t stream);
+
+/* ---------------------------------------------------------------- PageRank */
+
+/*
+ * PageRank state of Algorithm 5 at r_0 = 1/V: rank[v] = 1/V,
+ * contrib[v] = rank[v] * inv[v], and *dev_dangling = sum of rank over the
+ * vertices with inv = 0 (FP64).  dev_inv: float[V]; outputs float[V] and one
+ * device double.
+ */
+int pr_init(const float *dev_inv, int32_t V, float *dev_rank,
+            float *dev_contrib, double *dev_dangling, cudaStream_t stream);
+
+/*
+ * PageRank state for a given rank vector (Algorithm 5's contrib, with the
+ * reciprocal degree): contrib[v] = rank[v] * inv[v] and *dev_dangling = sum
+ * of rank over the vertices with inv = 0 (FP64, fixed reduction order).
+ * Lets a solve start from any caller-supplied rank vector.
+ */
+int pr_contrib(const float *dev_inv, const float *dev_rank, int32_t V,
+               float *dev_contrib, double *dev_dangling, cudaStream_t stream);
+
+/*
+ * `iterations` PageRank iterations through the segmented graph: per
+ * iteration, Algorithm 3's gather of contrib over every subgraph, then
+ * Algorithm 4's blocked merge fused with the vertex update (normalised form,
+ * uniform dangling redistribution):
+ *   rank'[v]    = (1-d)/V + d (sum_{u->v} contrib[u] + D/V)
+ *   contrib'[v] = rank'[v] * inv[v]
+ *   D'          = sum of rank' over vertices with inv = 0   (FP64)
+ *   resid[t]    = sum_v |rank'[v] - rank[v]|               (FP64)
+ * Inputs: dev_inv float[V]; dev_rank_in, dev_contrib_in float[V];
+ * *dev_dangling_io (device double) = D of rank_in on entry, D of rank_out on
+ * exit.  Outputs: dev_rank_out, dev_contrib_out float[V] (must not alias the
+ * inputs); dev_resid: double[iterations] or NULL.  FP32 arithmetic, FP64 only
+ * for D and the residual.  Deterministic (fixed reduction order).
+ * Iterations > 1 ping-pong through buffers held by the handle.
+ */
+int pr_iterate(const cg_segmented *seg, const float *dev_inv,
+               const float *dev_rank_in, const float *dev_contrib_in,
+               float *dev_rank_out, float *dev_contrib_out, double damping,
+               int32_t iterations, double *dev_dangling_io, double *dev_resid,
+               cudaStream_t stream);
+
+/*
+ * One iteration's cache-aware merge fused with the vertex update (Algorithm 4
+ * then Algorithm 5's VertexUpdate), reading the handle's intermBuf as left by
+ * cg_seg_gather(seg, CG_OP_SUM_F32, contrib, NULL): the second half of one
+ * pr_iterate iteration.  *dev_D_in = dangling mass of rank_in; *dev_D_out
+ * receives that of rank_out; *dev_resid_out (may be NULL) the FP64 L1
+ * residual.  dev_D_in may equal dev_D_out.
+ */
+int pr_merge_update(const cg_segmented *seg, const float *dev_inv,
+                    const float *dev_rank_in, float *dev_rank_out,
+                    float *dev_contrib_out, double damping, const double *dev_D_in,
+                    double *dev_D_out, double *dev_resid_out, cudaStream_t stream);
+
+/* The plain pull baseline (Algorithm 1 without segmenting). */
+typedef struct cg_plain cg_plain;
+
+/*
+ * Analyse an in-edge CSR for the plain pull kernel (work tiling over rows +
+ * edges) and allocate its work buffers.  The CSR arrays are NOT copied: they
+ * must stay valid and unchanged while the handle is used.  Synchronizes.
+ */
+int pr_plain_create(const int64_t *dev_offsets, const int32_t *dev_src,
+                    int32_t V, int64_t E, cg_plain **out, cudaStream_t stream);
+int pr_plain_destroy(cg_plain *plain);
+
+/*
+ * Same iteration and arguments as pr_iterate, computed by the plain pull
+ * gather of Algorithm 1 over the whole CSR (random reads over all of
+ * contrib), followed by the vertex update.  probe != 0 is the paper's
+ * "lower bound" measurement program (Section I, Fig. 1): every gathered read
+ * goes to contrib[0] instead of contrib[src] while the edge stream is read
+ * as usual; its result is not PageRank.
+ */
+int pr_iterate_plain(const cg_plain *plain, const float *dev_inv,
+                     const float *dev_rank_in, const float *dev_contrib_in,
+                     float *dev_rank_out, float *dev_contrib_out,
+                     double damping, int32_t iterations,
+                     double *dev_dangling_io, double *dev_resid,
+                     int32_t probe, cudaStream_t stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CAGRA_GB_H */

@@ -1,0 +1,286 @@
+"""Thin Python binding of the cagra_gb C ABI (include/cagra_gb.h).
+
+Argument marshalling only: torch tensors are passed as raw device pointers,
+the current torch CUDA stream as the stream, and every status code is turned
+into an exception.  All computation happens in the CUDA library; there is no
+CPU fallback: if the library is missing or no GPU is present the calls fail.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libcagra_gb.so")
+_lock = threading.Lock()
+_lib = None
+
+CG_OP_SUM_F32 = 0
+CG_OP_MIN_I32 = 1
+
+# Every symbol include/cagra_gb.h declares (checked by the CPU test suite).
+EXPORTS = [
+    "cg_status_string", "cg_last_error_message", "cg_version",
+    "cg_out_degree", "cg_inv_outdeg", "cg_cluster", "cg_relabel_csr", "cg_permute4",
+    "pr_build_segments", "cg_segmented_get_info", "cg_segmented_export",
+    "cg_segmented_destroy", "cg_seg_gather", "merge",
+    "pr_init", "pr_contrib", "pr_iterate", "pr_merge_update", "pr_plain_create", "pr_plain_destroy", "pr_iterate_plain",
+]
+
+
+class CagraError(RuntimeError):
+    pass
+
+
+class SegInfo(ctypes.Structure):
+    _fields_ = [("V", ctypes.c_int32), ("E", ctypes.c_int64), ("num_segments", ctypes.c_int32),
+                ("merge_block", ctypes.c_int32), ("num_blocks", ctypes.c_int32),
+                ("rows", ctypes.c_int64), ("q", ctypes.c_double),
+                ("device_bytes", ctypes.c_int64), ("gather_tiles", ctypes.c_int64)]
+
+
+def load(path: str | None = None):
+    """Load libcagra_gb.so (raises if it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        p = path or LIB_PATH
+        if not os.path.exists(p):
+            raise CagraError(f"cagra_gb CUDA library not found at {p}; build it with "
+                             "paper_1608_01362_gb300.build.build()")
+        lib = ctypes.CDLL(p)
+        i32, i64, dbl, vp = ctypes.c_int32, ctypes.c_int64, ctypes.c_double, ctypes.c_void_p
+        sig = {
+            "cg_status_string": (ctypes.c_char_p, [ctypes.c_int]),
+            "cg_last_error_message": (ctypes.c_char_p, []),
+            "cg_version": (ctypes.c_int, []),
+            "cg_out_degree": (ctypes.c_int, [vp, i64, i32, vp, vp]),
+            "cg_inv_outdeg": (ctypes.c_int, [vp, i32, vp, vp]),
+            "cg_cluster": (ctypes.c_int, [vp, i32, i64, i32, vp, vp, vp]),
+            "cg_relabel_csr": (ctypes.c_int, [vp, vp, i32, i64, vp, vp, vp, vp, vp]),
+            "cg_permute4": (ctypes.c_int, [vp, i64, vp, i64, vp, vp]),
+            "pr_build_segments": (ctypes.c_int, [vp, vp, i32, i64, i32, vp, i32,
+                                                 ctypes.POINTER(vp), vp]),
+            "cg_segmented_get_info": (ctypes.c_int, [vp, ctypes.POINTER(SegInfo)]),
+            "cg_segmented_export": (ctypes.c_int, [vp, vp, vp, vp, vp, vp, vp, vp, vp]),
+            "cg_segmented_destroy": (ctypes.c_int, [vp]),
+            "cg_seg_gather": (ctypes.c_int, [vp, i32, vp, vp, vp]),
+            "merge": (ctypes.c_int, [vp, i32, vp, vp, vp]),
+            "pr_init": (ctypes.c_int, [vp, i32, vp, vp, vp, vp]),
+            "pr_contrib": (ctypes.c_int, [vp, vp, i32, vp, vp, vp]),
+            "pr_iterate": (ctypes.c_int, [vp, vp, vp, vp, vp, vp, dbl, i32, vp, vp, vp]),
+            "pr_merge_update": (ctypes.c_int, [vp, vp, vp, vp, vp, dbl, vp, vp, vp, vp]),
+            "pr_plain_create": (ctypes.c_int, [vp, vp, i32, i64, ctypes.POINTER(vp), vp]),
+            "pr_plain_destroy": (ctypes.c_int, [vp]),
+            "pr_iterate_plain": (ctypes.c_int, [vp, vp, vp, vp, vp, vp, dbl, i32, vp, vp, i32,
+                                                vp]),
+        }
+        for name, (res, args) in sig.items():
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = lib
+        return lib
+
+
+def _check(status: int, what: str):
+    if status != 0:
+        lib = load()
+        msg = lib.cg_last_error_message().decode(errors="replace")
+        name = lib.cg_status_string(status).decode()
+        raise CagraError(f"{what}: {name}: {msg}")
+
+
+def _ptr(t) -> int | None:
+    """Device pointer of a torch tensor (None -> NULL)."""
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise CagraError("expected a CUDA tensor")
+    if not t.is_contiguous():
+        raise CagraError("expected a contiguous tensor")
+    return t.data_ptr()
+
+
+def _stream(stream=None) -> int:
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return s.cuda_stream
+
+
+def _dtype_check(t, dtype, name):
+    if t.dtype != dtype:
+        raise CagraError(f"{name} must be {dtype}, got {t.dtype}")
+
+
+# ------------------------------------------------------------------ degrees
+
+def cg_out_degree(src, V: int, outdeg, stream=None):
+    import torch
+    _dtype_check(src, torch.int32, "src"); _dtype_check(outdeg, torch.int32, "outdeg")
+    _check(load().cg_out_degree(_ptr(src), src.numel(), V, _ptr(outdeg), _stream(stream)),
+           "cg_out_degree")
+
+
+def cg_inv_outdeg(outdeg, inv, stream=None):
+    _check(load().cg_inv_outdeg(_ptr(outdeg), outdeg.numel(), _ptr(inv), _stream(stream)),
+           "cg_inv_outdeg")
+
+
+def cg_cluster(outdeg, E: int, mode: int, new_of_old, old_of_new, stream=None):
+    _check(load().cg_cluster(_ptr(outdeg), outdeg.numel(), E, mode, _ptr(new_of_old),
+                             _ptr(old_of_new), _stream(stream)), "cg_cluster")
+
+
+def cg_relabel_csr(offsets, src, new_of_old, old_of_new, out_offsets, out_src, stream=None):
+    V = offsets.numel() - 1
+    _check(load().cg_relabel_csr(_ptr(offsets), _ptr(src), V, src.numel(), _ptr(new_of_old),
+                                 _ptr(old_of_new), _ptr(out_offsets), _ptr(out_src),
+                                 _stream(stream)), "cg_relabel_csr")
+
+
+def cg_permute4(x, idx, out, stream=None):
+    """out[i] = x[idx[i]] for 4-byte element tensors."""
+    if x.element_size() != 4 or out.element_size() != 4:
+        raise CagraError("cg_permute4 needs 4-byte elements")
+    _check(load().cg_permute4(_ptr(x), x.numel(), _ptr(idx), idx.numel(), _ptr(out),
+                              _stream(stream)), "cg_permute4")
+
+
+# ------------------------------------------------------------------ segmenting
+
+class Segmented:
+    """Owner of a cg_segmented handle (destroyed with the object)."""
+
+    def __init__(self, handle: int):
+        self.handle = handle
+
+    def __del__(self):
+        self.close()
+
+    def close(self):
+        if getattr(self, "handle", None):
+            try:
+                load().cg_segmented_destroy(self.handle)
+            finally:
+                self.handle = None
+
+    @property
+    def info(self) -> dict:
+        inf = SegInfo()
+        _check(load().cg_segmented_get_info(self.handle, ctypes.byref(inf)),
+               "cg_segmented_get_info")
+        return {f: getattr(inf, f) for f, _ in SegInfo._fields_}
+
+
+def pr_build_segments(offsets, src, num_segments: int, bounds=None, merge_block: int = 4096,
+                      stream=None) -> Segmented:
+    import torch
+    _dtype_check(offsets, torch.int64, "offsets"); _dtype_check(src, torch.int32, "src")
+    V = offsets.numel() - 1
+    hb = None
+    if bounds is not None:
+        b = np.ascontiguousarray(np.asarray(bounds, dtype=np.int64))
+        if b.shape != (num_segments + 1,):
+            raise CagraError("bounds must have num_segments + 1 entries")
+        hb = b.ctypes.data
+    h = ctypes.c_void_p()
+    _check(load().pr_build_segments(_ptr(offsets), _ptr(src) if src.numel() else None, V,
+                                    src.numel(), num_segments, hb, merge_block, ctypes.byref(h),
+                                    _stream(stream)), "pr_build_segments")
+    return Segmented(h.value)
+
+
+def cg_segmented_export(seg: Segmented, stream=None) -> dict:
+    """Canonical flat layout as numpy arrays (host copies)."""
+    import torch
+    inf = seg.info
+    k, rows, E, nb = inf["num_segments"], inf["rows"], inf["E"], inf["num_blocks"]
+    hb = np.empty(k + 1, np.int64); hr = np.empty(k + 1, np.int64); he = np.empty(k + 1, np.int64)
+    dev = torch.device("cuda")
+    rp = torch.empty(rows + 1, dtype=torch.int64, device=dev)
+    col = torch.empty(max(E, 1), dtype=torch.int32, device=dev)
+    idx = torch.empty(max(rows, 1), dtype=torch.int32, device=dev)
+    blk = torch.empty(k * (nb + 1), dtype=torch.int32, device=dev)
+    _check(load().cg_segmented_export(seg.handle, hb.ctypes.data, hr.ctypes.data, he.ctypes.data,
+                                      _ptr(rp), _ptr(col), _ptr(idx), _ptr(blk), _stream(stream)),
+           "cg_segmented_export")
+    return {"bounds": hb, "row_base": hr, "edge_base": he, "row_ptr": rp.cpu().numpy(),
+            "col": col.cpu().numpy()[:E], "idx_map": idx.cpu().numpy()[:rows],
+            "block_start": blk.cpu().numpy()}
+
+
+def cg_seg_gather(seg: Segmented, op: int, x, interm=None, stream=None):
+    _check(load().cg_seg_gather(seg.handle, op, _ptr(x), _ptr(interm), _stream(stream)),
+           "cg_seg_gather")
+
+
+def merge(seg: Segmented, op: int, interm, out, stream=None):
+    _check(load().merge(seg.handle, op, _ptr(interm), _ptr(out), _stream(stream)), "merge")
+
+
+# ------------------------------------------------------------------ PageRank
+
+def pr_init(inv, rank, contrib, dangling, stream=None):
+    _check(load().pr_init(_ptr(inv), inv.numel(), _ptr(rank), _ptr(contrib), _ptr(dangling),
+                          _stream(stream)), "pr_init")
+
+
+def pr_contrib(inv, rank, contrib, dangling, stream=None):
+    _check(load().pr_contrib(_ptr(inv), _ptr(rank), inv.numel(), _ptr(contrib), _ptr(dangling),
+                             _stream(stream)), "pr_contrib")
+
+
+def pr_iterate(seg: Segmented, inv, rank_in, contrib_in, rank_out, contrib_out, damping: float,
+               iterations: int, dangling, resid=None, stream=None):
+    _check(load().pr_iterate(seg.handle, _ptr(inv), _ptr(rank_in), _ptr(contrib_in),
+                             _ptr(rank_out), _ptr(contrib_out), damping, iterations,
+                             _ptr(dangling), _ptr(resid), _stream(stream)), "pr_iterate")
+
+
+def pr_merge_update(seg: Segmented, inv, rank_in, rank_out, contrib_out, damping: float,
+                    D_in, D_out, resid=None, stream=None):
+    _check(load().pr_merge_update(seg.handle, _ptr(inv), _ptr(rank_in), _ptr(rank_out),
+                                  _ptr(contrib_out), damping, _ptr(D_in), _ptr(D_out),
+                                  _ptr(resid), _stream(stream)), "pr_merge_update")
+
+
+class Plain:
+    """Owner of a cg_plain handle; keeps the CSR tensors alive."""
+
+    def __init__(self, handle: int, offsets, src):
+        self.handle = handle
+        self._keep = (offsets, src)
+
+    def __del__(self):
+        self.close()
+
+    def close(self):
+        if getattr(self, "handle", None):
+            try:
+                load().pr_plain_destroy(self.handle)
+            finally:
+                self.handle = None
+
+
+def pr_plain_create(offsets, src, stream=None) -> Plain:
+    import torch
+    _dtype_check(offsets, torch.int64, "offsets"); _dtype_check(src, torch.int32, "src")
+    h = ctypes.c_void_p()
+    _check(load().pr_plain_create(_ptr(offsets), _ptr(src) if src.numel() else None,
+                                  offsets.numel() - 1, src.numel(), ctypes.byref(h),
+                                  _stream(stream)), "pr_plain_create")
+    return Plain(h.value, offsets, src)
+
+
+def pr_iterate_plain(plain: Plain, inv, rank_in, contrib_in, rank_out, contrib_out,
+                     damping: float, iterations: int, dangling, resid=None, probe: bool = False,
+                     stream=None):
+    _check(load().pr_iterate_plain(plain.handle, _ptr(inv), _ptr(rank_in), _ptr(contrib_in),
+                                   _ptr(rank_out), _ptr(contrib_out), damping, iterations,
+                                   _ptr(dangling), _ptr(resid), int(probe), _stream(stream)),
+           "pr_iterate_plain")

@@ -1,0 +1,548 @@
+// CSR segmenting preprocessing (Algorithm 2, Section III-A) on the GPU.
+//
+// Steps (all device work except reading a few sizes back):
+//   A. per destination row: how many segments its in-edges come from;
+//   B. per (row, segment) pair: the edge count, rows in order, segments
+//      ascending inside a row;
+//   C. a stable sort of the pairs by segment gives the segment-major row
+//      order (segment by segment, destinations ascending inside each) =
+//      the subgraphs' rows, idxMap and row lengths;
+//   D. every edge is placed in its subgraph row, keeping parent order;
+//   E. merge-block indices (blockStarts / blockEnds of Algorithm 4);
+//   F. the gather tiling and the intermBuf of the handle.
+#include <algorithm>
+#include <vector>
+
+#include "handles.cuh"
+
+namespace cg {
+namespace {
+
+constexpr int kBuildWarps = 4;
+constexpr int kBuildThreads = kBuildWarps * 32;
+constexpr int kMaxSegments = 1024;
+
+// Segment of source u: last s with bounds[s] <= u (empty segments skipped).
+__device__ __forceinline__ int seg_of(int32_t u, const int32_t* sb, int k) {
+  int lo = 0, hi = k + 1;  // upper_bound over sb[0..k]
+  while (lo < hi) {
+    const int mid = (lo + hi) >> 1;
+    if (sb[mid] <= u) lo = mid + 1; else hi = mid;
+  }
+  return lo - 1;
+}
+
+__global__ void validate_csr_kernel(const int64_t* __restrict__ offsets,
+                                    const int32_t* __restrict__ src, int32_t V, int64_t E,
+                                    unsigned long long* __restrict__ bad) {
+  unsigned long long nbad = 0;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  const int64_t t0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  for (int64_t v = t0; v < V; v += stride) nbad += offsets[v + 1] < offsets[v];
+  if (t0 == 0) nbad += (offsets[0] != 0) + (offsets[V] != E);
+  for (int64_t e = t0; e < E; e += stride) {
+    const int32_t u = __ldcs(src + e);
+    nbad += (u < 0 || u >= V);
+  }
+  nbad = warp_sum(nbad);
+  if ((threadIdx.x & 31) == 0 && nbad) atomicAdd(bad, nbad);
+}
+
+// A. number of distinct segments among each row's sources.
+__global__ void row_nseg_kernel(const int64_t* __restrict__ offsets,
+                                const int32_t* __restrict__ src, int32_t V,
+                                const int32_t* __restrict__ bounds, int k,
+                                int32_t* __restrict__ nseg) {
+  extern __shared__ int32_t sm[];
+  int32_t* sb = sm;                                   // [k+1]
+  const int words = (k + 31) >> 5;
+  uint32_t* bm = reinterpret_cast<uint32_t*>(sb + ((k + 1 + 3) & ~3));  // [warps][words]
+  for (int i = threadIdx.x; i <= k; i += blockDim.x) sb[i] = bounds[i];
+  __syncthreads();
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  uint32_t* mybm = bm + w * words;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t v = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; v < V; v += nwarps) {
+    for (int q = lane; q < words; q += 32) mybm[q] = 0u;
+    __syncwarp();
+    const int64_t lo = offsets[v], hi = offsets[v + 1];
+    for (int64_t e = lo + lane; e < hi; e += 32) {
+      const int s = seg_of(src[e], sb, k);
+      atomicOr(mybm + (s >> 5), 1u << (s & 31));
+    }
+    __syncwarp();
+    int c = 0;
+    for (int q = lane; q < words; q += 32) c += __popc(mybm[q]);
+    c = warp_sum(c);
+    if (lane == 0) nseg[v] = c;
+    __syncwarp();
+  }
+}
+
+// B. (segment, row, count) for every (row, segment) pair; a row's pairs are
+// written at pos[v] in ascending segment order.
+__global__ void row_pairs_kernel(const int64_t* __restrict__ offsets,
+                                 const int32_t* __restrict__ src, int32_t V,
+                                 const int32_t* __restrict__ bounds, int k,
+                                 const int64_t* __restrict__ pos, uint32_t* __restrict__ pseg,
+                                 int32_t* __restrict__ prow, int32_t* __restrict__ pcnt) {
+  extern __shared__ int32_t sm[];
+  const int words = (k + 31) >> 5;
+  int32_t* sb = sm;                                             // [k+1]
+  int32_t* cnt = sb + ((k + 1 + 3) & ~3);                       // [warps][k]
+  uint32_t* bm = reinterpret_cast<uint32_t*>(cnt + kBuildWarps * k);  // [warps][words]
+  for (int i = threadIdx.x; i <= k; i += blockDim.x) sb[i] = bounds[i];
+  for (int i = threadIdx.x; i < kBuildWarps * k; i += blockDim.x) cnt[i] = 0;
+  __syncthreads();
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  int32_t* mycnt = cnt + w * k;
+  uint32_t* mybm = bm + w * words;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t v = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; v < V; v += nwarps) {
+    for (int q = lane; q < words; q += 32) mybm[q] = 0u;
+    __syncwarp();
+    const int64_t lo = offsets[v], hi = offsets[v + 1];
+    for (int64_t e = lo + lane; e < hi; e += 32) {
+      const int s = seg_of(src[e], sb, k);
+      atomicOr(mybm + (s >> 5), 1u << (s & 31));
+      atomicAdd(mycnt + s, 1);
+    }
+    __syncwarp();
+    // enumerate set bits word by word; lane q owns words q, q+32, ... (k <= 1024: one word)
+    int64_t base = pos[v];
+    for (int q0 = 0; q0 < words; q0 += 32) {
+      const int q = q0 + lane;
+      uint32_t word = q < words ? mybm[q] : 0u;
+      const int n = __popc(word);
+      int incl = n;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
+      }
+      int64_t p = base + incl - n;
+      while (word) {
+        const int b = __ffs(word) - 1;
+        const int s = q * 32 + b;
+        pseg[p] = (uint32_t)s;
+        prow[p] = (int32_t)v;
+        pcnt[p] = mycnt[s];
+        mycnt[s] = 0;
+        ++p;
+        word &= word - 1u;
+      }
+      base += __shfl_sync(0xffffffffu, incl, 31);
+    }
+    __syncwarp();
+  }
+}
+
+__global__ void iota_kernel(int32_t* __restrict__ a, int64_t n) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    a[i] = (int32_t)i;
+}
+
+// C. segment-major rows from the sorted pair order.
+__global__ void pairs_to_rows_kernel(const int32_t* __restrict__ perm,
+                                     const int32_t* __restrict__ prow,
+                                     const int32_t* __restrict__ pcnt, int64_t n,
+                                     int32_t* __restrict__ idx_map, int32_t* __restrict__ rowlen,
+                                     int32_t* __restrict__ inv) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t p = perm[i];
+    idx_map[i] = prow[p];
+    rowlen[i] = pcnt[p];
+    inv[p] = (int32_t)i;
+  }
+}
+
+// row_base[s] = first sorted pair with segment >= s (k+1 threads).
+__global__ void segment_starts_kernel(const uint32_t* __restrict__ skey, int64_t n, int k,
+                                      int64_t* __restrict__ row_base) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s > k) return;
+  int64_t lo = 0, hi = n;
+  while (lo < hi) {
+    const int64_t mid = (lo + hi) >> 1;
+    if ((int64_t)skey[mid] < s) lo = mid + 1; else hi = mid;
+  }
+  row_base[s] = lo;
+}
+
+__global__ void to_i32_kernel(const int64_t* __restrict__ in, int64_t n,
+                              int32_t* __restrict__ out) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = (int32_t)in[i];
+}
+
+// D. place every edge: cur[s] = next free slot of this row's segment-s subrow.
+__global__ void scatter_edges_kernel(const int64_t* __restrict__ offsets,
+                                     const int32_t* __restrict__ src, int32_t V,
+                                     const int32_t* __restrict__ bounds, int k,
+                                     const int64_t* __restrict__ pos,
+                                     const uint32_t* __restrict__ pseg,
+                                     const int32_t* __restrict__ inv,
+                                     const int64_t* __restrict__ rp, int32_t* __restrict__ col) {
+  extern __shared__ int64_t sm64[];
+  int64_t* cur = sm64;                                          // [warps][k]
+  int32_t* sb = reinterpret_cast<int32_t*>(cur + kBuildWarps * k);  // [k+1]
+  for (int i = threadIdx.x; i <= k; i += blockDim.x) sb[i] = bounds[i];
+  __syncthreads();
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const unsigned lt = (1u << lane) - 1u;
+  int64_t* mycur = cur + w * k;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t v = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; v < V; v += nwarps) {
+    for (int64_t p = pos[v] + lane; p < pos[v + 1]; p += 32) mycur[pseg[p]] = rp[inv[p]];
+    __syncwarp();
+    const int64_t lo = offsets[v], hi = offsets[v + 1];
+    for (int64_t e0 = lo; e0 < hi; e0 += 32) {
+      const int64_t e = e0 + lane;
+      const bool ok = e < hi;
+      const int32_t u = ok ? src[e] : 0;
+      const int s = ok ? seg_of(u, sb, k) : 0;
+      const unsigned key = ok ? (unsigned)s : (0x10000u | (unsigned)lane);
+      const unsigned peers = __match_any_sync(0xffffffffu, key);
+      if (ok) col[mycur[s] + __popc(peers & lt)] = u;
+      __syncwarp();
+      if (ok && lane == __ffs(peers) - 1) mycur[s] += __popc(peers);
+      __syncwarp();
+    }
+  }
+}
+
+// E. merge-block indices.
+__global__ void blk_prefill_kernel(const int64_t* __restrict__ row_base, int k, int nb,
+                                   int32_t* __restrict__ blk) {
+  const int64_t n = (int64_t)k * (nb + 1);
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    blk[i] = (int32_t)row_base[i / (nb + 1)];
+}
+
+__global__ void blk_rows_kernel(const int64_t* __restrict__ row_base, int k,
+                                const int32_t* __restrict__ idx_map, int64_t rows, int B, int nb,
+                                int32_t* __restrict__ blk) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < rows;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    int lo = 0, hi = k + 1;  // segment of row i: last s with row_base[s] <= i
+    while (lo < hi) {
+      const int mid = (lo + hi) >> 1;
+      if (row_base[mid] <= i) lo = mid + 1; else hi = mid;
+    }
+    const int s = lo - 1;
+    int32_t* b_s = blk + (int64_t)s * (nb + 1);
+    const int bk = idx_map[i] / B;
+    const int pbk = (i == row_base[s]) ? -1 : idx_map[i - 1] / B;
+    for (int b = pbk + 1; b <= bk; ++b) b_s[b] = (int32_t)i;
+    if (i == row_base[s + 1] - 1)
+      for (int b = bk + 1; b <= nb; ++b) b_s[b] = (int32_t)row_base[s + 1];
+  }
+}
+
+// Export helpers.
+__global__ void to_i64_kernel(const int32_t* __restrict__ in, int64_t n,
+                              int64_t* __restrict__ out) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = in[i];
+}
+
+__global__ void blk_local_kernel(const int32_t* __restrict__ blk, const int64_t* __restrict__ rb,
+                                 int k, int nb, int32_t* __restrict__ out) {
+  const int64_t n = (int64_t)k * (nb + 1);
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = (int32_t)(blk[i] - rb[i / (nb + 1)]);
+}
+
+struct Scratch {
+  std::vector<void*> ptrs;
+  cudaStream_t s;
+  explicit Scratch(cudaStream_t st) : s(st) {}
+  template <typename T>
+  cudaError_t get(T** p, size_t n) {
+    cudaError_t e = cudaMallocAsync((void**)p, sizeof(T) * (n > 0 ? n : 1), s);
+    if (e == cudaSuccess) ptrs.push_back((void*)*p);
+    return e;
+  }
+  ~Scratch() {
+    for (void* p : ptrs) cudaFreeAsync(p, s);
+  }
+};
+
+int build_impl(const int64_t* offsets, const int32_t* src, int32_t V, int64_t E, int32_t k,
+               const std::vector<int64_t>& bounds, int32_t B, cg_segmented* g, cudaStream_t s) {
+  Scratch tmp(s);
+  int32_t* d_bounds = nullptr;
+  CG_CUDA(tmp.get(&d_bounds, k + 1));
+  {
+    std::vector<int32_t> b32(bounds.begin(), bounds.end());
+    CG_CUDA(cudaMemcpyAsync(d_bounds, b32.data(), sizeof(int32_t) * (k + 1),
+                            cudaMemcpyHostToDevice, s));
+    CG_CUDA(cudaStreamSynchronize(s));  // b32 is a host temporary
+  }
+  const int words = (k + 31) / 32;
+  const size_t sb_bytes = sizeof(int32_t) * (size_t)((k + 1 + 3) & ~3);
+  const int grid_rows = grid_for((int64_t)V * 32, kBuildThreads, 16);
+
+  // A
+  int32_t* nseg = nullptr;
+  int64_t* pos = nullptr;
+  CG_CUDA(tmp.get(&nseg, V));
+  CG_CUDA(tmp.get(&pos, (size_t)V + 1));
+  row_nseg_kernel<<<grid_rows, kBuildThreads, sb_bytes + sizeof(uint32_t) * kBuildWarps * words,
+                    s>>>(offsets, src, V, d_bounds, k, nseg);
+  CG_LAUNCH_CHECK();
+  CG_TRY(exclusive_scan_i32_to_i64(nseg, pos, V, s));
+  int64_t npairs = 0;
+  CG_CUDA(cudaMemcpyAsync(&npairs, pos + V, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+  CG_CUDA(cudaStreamSynchronize(s));
+  if (npairs >= 0x7FFFFFFF) {
+    set_error("pr_build_segments: %lld subgraph rows exceed the int32 range", (long long)npairs);
+    return CG_ERR_UNSUPPORTED;
+  }
+  g->rows = npairs;
+
+  // B
+  uint32_t* pseg = nullptr;
+  uint32_t* sseg = nullptr;
+  int32_t *prow = nullptr, *pcnt = nullptr, *piota = nullptr, *perm = nullptr, *inv = nullptr;
+  int32_t* rowlen = nullptr;
+  int64_t* rp = nullptr;
+  CG_CUDA(tmp.get(&pseg, npairs));
+  CG_CUDA(tmp.get(&sseg, npairs));
+  CG_CUDA(tmp.get(&prow, npairs));
+  CG_CUDA(tmp.get(&pcnt, npairs));
+  CG_CUDA(tmp.get(&piota, npairs));
+  CG_CUDA(tmp.get(&perm, npairs));
+  CG_CUDA(tmp.get(&inv, npairs));
+  CG_CUDA(tmp.get(&rowlen, npairs));
+  CG_CUDA(tmp.get(&rp, (size_t)npairs + 1));
+  row_pairs_kernel<<<grid_rows, kBuildThreads,
+                     sb_bytes + sizeof(int32_t) * kBuildWarps * k +
+                         sizeof(uint32_t) * kBuildWarps * words,
+                     s>>>(offsets, src, V, d_bounds, k, pos, pseg, prow, pcnt);
+  CG_LAUNCH_CHECK();
+
+  // C
+  int bits = 0;
+  while ((1 << bits) < k) ++bits;
+  if (npairs > 0) {
+    iota_kernel<<<grid_for(npairs, 256), 256, 0, s>>>(piota, npairs);
+    CG_LAUNCH_CHECK();
+    CG_TRY(radix_sort_pairs(pseg, piota, sseg, perm, npairs, bits > 0 ? bits : 1, s));
+  }
+  CG_CUDA(cudaMalloc((void**)&g->idx_map, sizeof(int32_t) * (size_t)(npairs > 0 ? npairs : 1)));
+  if (npairs > 0) {
+    pairs_to_rows_kernel<<<grid_for(npairs, 256), 256, 0, s>>>(perm, prow, pcnt, npairs,
+                                                                g->idx_map, rowlen, inv);
+    CG_LAUNCH_CHECK();
+  }
+  CG_TRY(exclusive_scan_i32_to_i64(rowlen, rp, npairs, s));
+  CG_CUDA(cudaMalloc((void**)&g->row_ptr, sizeof(int32_t) * (size_t)(npairs + 1)));
+  to_i32_kernel<<<grid_for(npairs + 1, 256), 256, 0, s>>>(rp, npairs + 1, g->row_ptr);
+  CG_LAUNCH_CHECK();
+  int64_t* d_rb = nullptr;
+  CG_CUDA(tmp.get(&d_rb, k + 1));
+  segment_starts_kernel<<<(k + 1 + 127) / 128, 128, 0, s>>>(sseg, npairs, k, d_rb);
+  CG_LAUNCH_CHECK();
+  g->row_base.assign(k + 1, 0);
+  CG_CUDA(cudaMemcpyAsync(g->row_base.data(), d_rb, sizeof(int64_t) * (k + 1),
+                          cudaMemcpyDeviceToHost, s));
+  CG_CUDA(cudaStreamSynchronize(s));
+  g->edge_base.assign(k + 1, 0);
+  for (int q = 0; q <= k; ++q) {
+    CG_CUDA(cudaMemcpyAsync(&g->edge_base[q], rp + g->row_base[q], sizeof(int64_t),
+                            cudaMemcpyDeviceToHost, s));
+  }
+
+  // D
+  CG_CUDA(cudaMalloc((void**)&g->col, sizeof(int32_t) * (size_t)(E > 0 ? E : 1)));
+  if (E > 0) {
+    const size_t smem = sizeof(int64_t) * kBuildWarps * k + sizeof(int32_t) * (k + 1);
+    scatter_edges_kernel<<<grid_rows, kBuildThreads, smem, s>>>(offsets, src, V, d_bounds, k, pos,
+                                                                pseg, inv, rp, g->col);
+    CG_LAUNCH_CHECK();
+  }
+
+  // E
+  g->nb = (int32_t)ceil_div(V, B);
+  CG_CUDA(cudaMalloc((void**)&g->blk, sizeof(int32_t) * (size_t)k * (g->nb + 1)));
+  blk_prefill_kernel<<<grid_for((int64_t)k * (g->nb + 1), 256), 256, 0, s>>>(d_rb, k, g->nb,
+                                                                              g->blk);
+  CG_LAUNCH_CHECK();
+  if (npairs > 0) {
+    blk_rows_kernel<<<grid_for(npairs, 256), 256, 0, s>>>(d_rb, k, g->idx_map, npairs, B, g->nb,
+                                                          g->blk);
+    CG_LAUNCH_CHECK();
+  }
+
+  // F
+  CG_TRY(plan_gather<int32_t>(g->row_ptr + 1, npairs, E, &g->plan, s));
+  CG_CUDA(cudaMalloc(&g->interm, sizeof(float) * (size_t)(npairs > 0 ? npairs : 1)));
+  CG_CUDA(cudaMalloc((void**)&g->partials, sizeof(double) * 2 * (size_t)g->nb));
+  CG_CUDA(cudaMalloc((void**)&g->counter, sizeof(unsigned)));
+  CG_CUDA(cudaMemsetAsync(g->counter, 0, sizeof(unsigned), s));
+  CG_CUDA(cudaMalloc((void**)&g->dslot, sizeof(double) * 4));
+  CG_CUDA(cudaMemsetAsync(g->dslot, 0, sizeof(double) * 4, s));
+  CG_CUDA(cudaMalloc((void**)&g->rank_tmp, sizeof(float) * (size_t)V));
+  CG_CUDA(cudaMalloc((void**)&g->contrib_tmp, sizeof(float) * (size_t)V));
+  CG_CUDA(cudaStreamSynchronize(s));
+  g->bytes = 4 * (npairs + 1) + 4 * E + 4 * npairs + 4 * (int64_t)k * (g->nb + 1) +
+             plan_bytes(g->plan) + 4 * npairs + 16 * (int64_t)g->nb + 4 + 32 + 8 * (int64_t)V;
+  return CG_OK;
+}
+
+void free_segmented(cg_segmented* g) {
+  cudaFree(g->row_ptr);
+  cudaFree(g->col);
+  cudaFree(g->idx_map);
+  cudaFree(g->blk);
+  free_plan(&g->plan);
+  cudaFree(g->interm);
+  cudaFree(g->partials);
+  cudaFree(g->counter);
+  cudaFree(g->dslot);
+  cudaFree(g->rank_tmp);
+  cudaFree(g->contrib_tmp);
+}
+
+}  // namespace
+
+int validate_csr(const int64_t* offsets, const int32_t* src, int32_t V, int64_t E,
+                 cudaStream_t s) {
+  unsigned long long* bad = nullptr;
+  CG_CUDA(cudaMallocAsync((void**)&bad, sizeof(unsigned long long), s));
+  cudaError_t e = cudaMemsetAsync(bad, 0, sizeof(unsigned long long), s);
+  unsigned long long h = 0;
+  if (e == cudaSuccess) {
+    validate_csr_kernel<<<grid_for(std::max<int64_t>(V, E), 256), 256, 0, s>>>(offsets, src, V,
+                                                                              E, bad);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(&h, bad, sizeof(h), cudaMemcpyDeviceToHost, s);
+  cudaFreeAsync(bad, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_fail(e, "validate_csr", __FILE__, __LINE__);
+  if (h) {
+    set_error("invalid CSR: %llu violations (offsets must rise from 0 to E; sources in [0, V))",
+              h);
+    return CG_ERR_INVALID_ARG;
+  }
+  return CG_OK;
+}
+
+}  // namespace cg
+
+using namespace cg;
+
+extern "C" {
+
+int pr_build_segments(const int64_t* offsets, const int32_t* src, int32_t V, int64_t E,
+                      int32_t k, const int64_t* host_bounds, int32_t B, cg_segmented** out,
+                      cudaStream_t stream) {
+  CG_ARG(out != nullptr, "pr_build_segments: out is NULL");
+  *out = nullptr;
+  CG_ARG(V >= 1, "pr_build_segments: V must be >= 1 (got %d)", V);
+  CG_ARG(E >= 0 && E < 0x7FFFFFFFLL, "pr_build_segments: E must be in [0, 2^31-1)");
+  CG_ARG(offsets && (E == 0 || src), "pr_build_segments: null CSR pointer");
+  CG_ARG(k >= 1 && k <= kMaxSegments, "pr_build_segments: num_segments must be in [1, %d]",
+         kMaxSegments);
+  CG_ARG(B >= 1 && B <= 12288, "pr_build_segments: merge_block must be in [1, 12288]");
+  std::vector<int64_t> bounds(k + 1);
+  if (host_bounds) {
+    for (int q = 0; q <= k; ++q) bounds[q] = host_bounds[q];
+    CG_ARG(bounds[0] == 0 && bounds[k] == V, "pr_build_segments: bounds must run from 0 to V");
+    for (int q = 0; q < k; ++q)
+      CG_ARG(bounds[q] <= bounds[q + 1], "pr_build_segments: bounds must be non-decreasing");
+  } else {
+    const int64_t N = ceil_div(V, k);
+    for (int q = 0; q <= k; ++q) bounds[q] = std::min<int64_t>((int64_t)q * N, V);
+  }
+  CG_TRY(validate_csr(offsets, src, V, E, stream));
+  cg_segmented* g = new cg_segmented();
+  CG_CUDA(cudaGetDevice(&g->device));
+  g->V = V;
+  g->E = E;
+  g->k = k;
+  g->B = B;
+  g->bounds = bounds;
+  int st = build_impl(offsets, src, V, E, k, bounds, B, g, stream);
+  if (st != CG_OK) {
+    cudaStreamSynchronize(stream);
+    free_segmented(g);
+    delete g;
+    return st;
+  }
+  *out = g;
+  return CG_OK;
+}
+
+int cg_segmented_get_info(const cg_segmented* g, cg_segmented_info* info) {
+  CG_ARG(g && info, "cg_segmented_get_info: null pointer");
+  info->V = g->V;
+  info->E = g->E;
+  info->num_segments = g->k;
+  info->merge_block = g->B;
+  info->num_blocks = g->nb;
+  info->rows = g->rows;
+  info->q = g->V ? (double)g->rows / (double)g->V : 0.0;
+  info->device_bytes = g->bytes;
+  info->gather_tiles = g->plan.ntiles;
+  return CG_OK;
+}
+
+int cg_segmented_export(const cg_segmented* g, int64_t* h_bounds, int64_t* h_row_base,
+                        int64_t* h_edge_base, int64_t* d_row_ptr, int32_t* d_col,
+                        int32_t* d_idx_map, int32_t* d_block_start, cudaStream_t s) {
+  CG_ARG(g != nullptr, "cg_segmented_export: null handle");
+  for (int q = 0; q <= g->k; ++q) {
+    if (h_bounds) h_bounds[q] = g->bounds[q];
+    if (h_row_base) h_row_base[q] = g->row_base[q];
+    if (h_edge_base) h_edge_base[q] = g->edge_base[q];
+  }
+  if (d_row_ptr) {
+    to_i64_kernel<<<grid_for(g->rows + 1, 256), 256, 0, s>>>(g->row_ptr, g->rows + 1, d_row_ptr);
+    CG_LAUNCH_CHECK();
+  }
+  if (d_col && g->E > 0)
+    CG_CUDA(cudaMemcpyAsync(d_col, g->col, sizeof(int32_t) * g->E, cudaMemcpyDeviceToDevice, s));
+  if (d_idx_map && g->rows > 0)
+    CG_CUDA(cudaMemcpyAsync(d_idx_map, g->idx_map, sizeof(int32_t) * g->rows,
+                            cudaMemcpyDeviceToDevice, s));
+  if (d_block_start) {
+    int64_t* d_rb = nullptr;
+    CG_CUDA(cudaMallocAsync((void**)&d_rb, sizeof(int64_t) * (g->k + 1), s));
+    cudaError_t e = cudaMemcpyAsync(d_rb, g->row_base.data(), sizeof(int64_t) * (g->k + 1),
+                                    cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) {
+      blk_local_kernel<<<grid_for((int64_t)g->k * (g->nb + 1), 256), 256, 0, s>>>(
+          g->blk, d_rb, g->k, g->nb, d_block_start);
+      e = cudaGetLastError();
+    }
+    cudaFreeAsync(d_rb, s);
+    if (e != cudaSuccess) return cuda_fail(e, "cg_segmented_export", __FILE__, __LINE__);
+  }
+  CG_CUDA(cudaStreamSynchronize(s));
+  return CG_OK;
+}
+
+int cg_segmented_destroy(cg_segmented* g) {
+  if (!g) return CG_OK;
+  int cur = 0;
+  const int dev = g->device;
+  cudaGetDevice(&cur);
+  if (cur != dev) cudaSetDevice(dev);
+  cudaDeviceSynchronize();
+  free_segmented(g);
+  delete g;
+  if (cur != dev) cudaSetDevice(cur);
+  return CG_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,145 @@
+"""The call sequence a user makes, chained: out-degrees -> (optional)
+frequency-based clustering -> CSR segmenting -> PageRank iterations, every
+step a call into the CUDA library (no computation here).
+"""
+from __future__ import annotations
+
+import torch
+
+from . import cagra as C
+
+
+def _dev_csr(offsets, src, device):
+    off = torch.as_tensor(offsets, dtype=torch.int64).to(device).contiguous()
+    s = torch.as_tensor(src, dtype=torch.int32).to(device).contiguous()
+    return off, s
+
+
+class Graph:
+    """An in-edge CSR on the GPU with its out-degrees, optionally renumbered
+    hottest-first by frequency-based clustering (Section V)."""
+
+    def __init__(self, offsets, src, cluster_mode: int | None = 0, device="cuda"):
+        off, s = _dev_csr(offsets, src, device)
+        self.device = torch.device(device)
+        self.V = off.numel() - 1
+        self.E = s.numel()
+        outdeg = torch.empty(self.V, dtype=torch.int32, device=self.device)
+        C.cg_out_degree(s, self.V, outdeg)
+        self.cluster_mode = cluster_mode
+        if cluster_mode is None:
+            self.offsets, self.src, self.outdeg = off, s, outdeg
+            self.new_of_old = self.old_of_new = None
+        else:
+            n2o = torch.empty(self.V, dtype=torch.int32, device=self.device)
+            o2n = torch.empty_like(n2o)
+            C.cg_cluster(outdeg, self.E, cluster_mode, n2o, o2n)
+            noff = torch.empty_like(off)
+            nsrc = torch.empty_like(s)
+            C.cg_relabel_csr(off, s, n2o, o2n, noff, nsrc)
+            nout = torch.empty_like(outdeg)
+            C.cg_permute4(outdeg, o2n, nout)
+            self.offsets, self.src, self.outdeg = noff, nsrc, nout
+            self.new_of_old, self.old_of_new = n2o, o2n
+        self.inv = torch.empty(self.V, dtype=torch.float32, device=self.device)
+        C.cg_inv_outdeg(self.outdeg, self.inv)
+
+    def to_original(self, x):
+        """Vertex vector in the clustered numbering -> original numbering."""
+        if self.new_of_old is None:
+            return x
+        out = torch.empty_like(x)
+        C.cg_permute4(x, self.new_of_old, out)
+        return out
+
+
+class _PageRankBase:
+    def __init__(self, graph: Graph):
+        self.g = graph
+        V, dev = graph.V, graph.device
+        self.rank = [torch.empty(V, dtype=torch.float32, device=dev) for _ in range(2)]
+        self.contrib = [torch.empty(V, dtype=torch.float32, device=dev) for _ in range(2)]
+        self.dangling = torch.zeros(1, dtype=torch.float64, device=dev)
+
+    def init(self):
+        C.pr_init(self.g.inv, self.rank[0], self.contrib[0], self.dangling)
+
+    def run(self, iterations: int = 20, damping: float = 0.85, resid=None):
+        """r_0 = 1/V, then `iterations` iterations; returns (rank in original
+        IDs, residual per iteration as a device FP64 tensor)."""
+        if resid is None:
+            resid = torch.zeros(iterations, dtype=torch.float64, device=self.g.device)
+        self.init()
+        self.step(self.rank[0], self.contrib[0], self.rank[1], self.contrib[1], damping,
+                  iterations, resid)
+        return self.g.to_original(self.rank[1]), resid
+
+
+class SegmentedPageRank(_PageRankBase):
+    """PageRank through CSR segmenting (Algorithms 2-5)."""
+
+    def __init__(self, graph: Graph, num_segments: int, merge_block: int = 4096, bounds=None):
+        super().__init__(graph)
+        self.seg = C.pr_build_segments(graph.offsets, graph.src, num_segments, bounds=bounds,
+                                       merge_block=merge_block)
+
+    @property
+    def info(self):
+        return self.seg.info
+
+    def step(self, rank_in, contrib_in, rank_out, contrib_out, damping, iterations, resid=None):
+        C.pr_iterate(self.seg, self.g.inv, rank_in, contrib_in, rank_out, contrib_out, damping,
+                     iterations, self.dangling, resid)
+
+
+class PlainPageRank(_PageRankBase):
+    """The plain pull baseline (Algorithm 1) over the whole CSR."""
+
+    def __init__(self, graph: Graph, probe: bool = False):
+        super().__init__(graph)
+        self.plain = C.pr_plain_create(graph.offsets, graph.src)
+        self.probe = probe
+
+    def step(self, rank_in, contrib_in, rank_out, contrib_out, damping, iterations, resid=None):
+        C.pr_iterate_plain(self.plain, self.g.inv, rank_in, contrib_in, rank_out, contrib_out,
+                           damping, iterations, self.dangling, resid, probe=self.probe)
+
+
+def time_iterations(pr, iterations: int = 3, damping: float = 0.85, reps: int = 1) -> float:
+    """Median seconds per PageRank iteration of `pr` (CUDA events)."""
+    times = []
+    for _ in range(reps):
+        pr.init()
+        start = torch.cuda.Event(enable_timing=True)
+        stop = torch.cuda.Event(enable_timing=True)
+        start.record()
+        pr.step(pr.rank[0], pr.contrib[0], pr.rank[1], pr.contrib[1], damping, iterations)
+        stop.record()
+        stop.synchronize()
+        times.append(start.elapsed_time(stop) / 1e3 / iterations)
+    times.sort()
+    return times[len(times) // 2]
+
+
+def autotune_segments(graph: Graph, candidates=(1, 2, 4, 8, 16, 32, 64), merge_block: int = 4096,
+                      iterations: int = 3, reps: int = 3):
+    """Pick the segment count k by measuring a few iterations for each
+    candidate (Section III-D's trade-off: smaller segments confine the
+    random reads to a smaller, faster cache level but raise the expansion
+    factor q and the merge traffic).  Returns (best_k, table) where table
+    maps k -> {"s_per_iter", "q"}."""
+    table = {}
+    best = None
+    for k in candidates:
+        if k > graph.V:
+            continue
+        pr = SegmentedPageRank(graph, k, merge_block=merge_block)
+        pr.init()
+        pr.step(pr.rank[0], pr.contrib[0], pr.rank[1], pr.contrib[1], 0.85, 1)  # warm-up
+        t = time_iterations(pr, iterations, reps=reps)
+        table[k] = {"s_per_iter": t, "q": pr.info["q"]}
+        if best is None or t < table[best]["s_per_iter"]:
+            best = k
+        pr.seg.close()
+        del pr
+    return best, table

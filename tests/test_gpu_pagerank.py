@@ -1,0 +1,285 @@
+"""Parity of the CUDA path (through the C ABI) against the FP64 oracle:
+degrees, clustering, renumbering and segment construction bit for bit;
+PageRank within 1e-5 relative L1 after 20 iterations (FP32 vs FP64)."""
+import numpy as np
+import pytest
+
+import graphgen
+import oracle as O
+
+pytestmark = pytest.mark.gpu
+
+TOL_L1 = 1e-5  # relative L1 of FP32 PageRank vs the FP64 oracle after 20 iterations
+
+
+@pytest.fixture(scope="module")
+def C():
+    import torch
+    assert torch.cuda.is_available()
+    from paper_1608_01362_gb300 import build, cagra
+    build.build()
+    cagra.load()
+    return cagra
+
+
+@pytest.fixture(scope="module")
+def torch_mod():
+    import torch
+    return torch
+
+
+def _dev(torch, a, dtype):
+    return torch.as_tensor(np.ascontiguousarray(a), dtype=dtype).cuda()
+
+
+def rel_l1(a, b):
+    return float(np.sum(np.abs(np.asarray(a, np.float64) - b)) / np.sum(np.abs(b)))
+
+
+@pytest.fixture(scope="module")
+def rmat16():
+    return graphgen.rmat(16, 16, seed=1)
+
+
+def _special_graphs():
+    out = {}
+    out["single"] = graphgen.from_edges(1, [], [])
+    out["two_isolated"] = graphgen.from_edges(2, [], [])
+    n = 5000  # in-star: one row much longer than a tile (carry fix-up across tiles)
+    out["in_star"] = graphgen.from_edges(n + 1, np.arange(1, n + 1), np.zeros(n, dtype=int))
+    out["out_star"] = graphgen.from_edges(n + 1, np.zeros(n, dtype=int), np.arange(1, n + 1))
+    m = 3000
+    out["cycle"] = graphgen.from_edges(m, np.arange(m), (np.arange(m) + 1) % m)
+    rng = np.random.default_rng(5)
+    out["ragged"] = graphgen.from_edges(777, rng.integers(0, 777, 5000) ** 1,
+                                        (rng.integers(0, 777, 5000) ** 2) % 777)
+    return out
+
+
+# ------------------------------------------------------------------ integer work (bit-exact)
+
+def test_out_degree_bitexact(C, torch_mod, rmat16):
+    torch = torch_mod
+    g = rmat16
+    od = torch.empty(g.V, dtype=torch.int32, device="cuda")
+    C.cg_out_degree(_dev(torch, g.src, torch.int32), g.V, od)
+    assert np.array_equal(od.cpu().numpy(), O.out_degree(g.offsets, g.src))
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_cluster_and_relabel_bitexact(C, torch_mod, rmat16, mode):
+    torch = torch_mod
+    g = rmat16
+    od_ref = O.out_degree(g.offsets, g.src)
+    n2o_ref, o2n_ref = O.cluster(od_ref, mode, E=g.E)
+    od = _dev(torch, od_ref, torch.int32)
+    n2o = torch.empty(g.V, dtype=torch.int32, device="cuda")
+    o2n = torch.empty_like(n2o)
+    C.cg_cluster(od, g.E, mode, n2o, o2n)
+    assert np.array_equal(o2n.cpu().numpy(), o2n_ref)
+    assert np.array_equal(n2o.cpu().numpy(), n2o_ref)
+    off, src = _dev(torch, g.offsets, torch.int64), _dev(torch, g.src, torch.int32)
+    noff, nsrc = torch.empty_like(off), torch.empty_like(src)
+    C.cg_relabel_csr(off, src, n2o, o2n, noff, nsrc)
+    roff, rsrc = O.relabel(g.offsets, g.src, n2o_ref, o2n_ref)
+    assert np.array_equal(noff.cpu().numpy(), roff) and np.array_equal(nsrc.cpu().numpy(), rsrc)
+
+
+def test_cluster_large_keys_and_ties(C, torch_mod):
+    torch = torch_mod
+    rng = np.random.default_rng(3)
+    V = 300_000
+    od = np.where(rng.random(V) < 0.01, rng.integers(0, 2_000_000, V), rng.integers(0, 4, V))
+    od = od.astype(np.int32)
+    _, o2n_ref = O.cluster(od, 0)
+    n2o = torch.empty(V, dtype=torch.int32, device="cuda")
+    o2n = torch.empty_like(n2o)
+    C.cg_cluster(_dev(torch, od, torch.int32), int(od.sum()), 0, n2o, o2n)
+    assert np.array_equal(o2n.cpu().numpy(), o2n_ref)
+
+
+def _check_segments(C, torch, offsets, src, k, B, bounds=None):
+    ref = O.build_segments(offsets, src, k=k, B=B, bounds=bounds)
+    seg = C.pr_build_segments(_dev(torch, offsets, torch.int64), _dev(torch, src, torch.int32), k,
+                              bounds=bounds, merge_block=B)
+    got = C.cg_segmented_export(seg)
+    for name in ("bounds", "row_base", "edge_base", "row_ptr", "col", "idx_map", "block_start"):
+        want = getattr(ref, name)
+        assert np.array_equal(got[name], want), f"{name} differs (k={k}, B={B})"
+    info = seg.info
+    assert info["rows"] == ref.rows and abs(info["q"] - ref.q) < 1e-12
+    return seg
+
+
+@pytest.mark.parametrize("k,B", [(1, 4096), (2, 1024), (4, 4096), (7, 333), (16, 4096),
+                                 (64, 12288), (1024, 64)])
+def test_segments_bitexact_rmat16(C, torch_mod, rmat16, k, B):
+    _check_segments(C, torch_mod, rmat16.offsets, rmat16.src, k, B)
+
+
+def test_segments_bitexact_clustered_and_nonuniform(C, torch_mod, rmat16):
+    g = rmat16
+    n2o, o2n = O.cluster(O.out_degree(g.offsets, g.src), 0)
+    off, src = O.relabel(g.offsets, g.src, n2o, o2n)
+    _check_segments(C, torch_mod, off, src, 8, 2048)
+    bounds = np.array([0, 1000, 1000, 20000, 20001, g.V], dtype=np.int64)  # empty + 1-vertex
+    _check_segments(C, torch_mod, off, src, 5, 4096, bounds=bounds)
+
+
+@pytest.mark.parametrize("name", list(_special_graphs().keys()))
+def test_segments_bitexact_special(C, torch_mod, name):
+    g = _special_graphs()[name]
+    for k in (1, 3):
+        if k <= g.V:
+            _check_segments(C, torch_mod, g.offsets, g.src, k, 7)
+
+
+def test_build_rejects_bad_input(C, torch_mod):
+    torch = torch_mod
+    off = _dev(torch, np.array([0, 2, 1, 3]), torch.int64)   # not monotone
+    src = _dev(torch, np.array([0, 1, 2]), torch.int32)
+    with pytest.raises(C.CagraError, match="INVALID_ARG"):
+        C.pr_build_segments(off, src, 1)
+    off = _dev(torch, np.array([0, 1, 2, 3]), torch.int64)
+    src = _dev(torch, np.array([0, 7, 2]), torch.int32)      # source out of range
+    with pytest.raises(C.CagraError, match="INVALID_ARG"):
+        C.pr_build_segments(off, src, 1)
+    src = _dev(torch, np.array([0, 1, 2]), torch.int32)
+    with pytest.raises(C.CagraError, match="num_segments"):
+        C.pr_build_segments(off, src, 0)
+    with pytest.raises(C.CagraError, match="bounds"):
+        C.pr_build_segments(off, src, 2, bounds=np.array([0, 2, 1]))
+
+
+# ------------------------------------------------------------------ gather / merge alone
+
+@pytest.mark.parametrize("k", [1, 5])
+def test_seg_gather_and_merge(C, torch_mod, rmat16, k):
+    torch = torch_mod
+    g = rmat16
+    ref = O.build_segments(g.offsets, g.src, k=k, B=1000)
+    seg = C.pr_build_segments(_dev(torch, g.offsets, torch.int64), _dev(torch, g.src, torch.int32),
+                              k, merge_block=1000)
+    rng = np.random.default_rng(k)
+    x = rng.random(g.V).astype(np.float32)
+    interm = torch.empty(ref.rows, dtype=torch.float32, device="cuda")
+    C.cg_seg_gather(seg, C.CG_OP_SUM_F32, _dev(torch, x, torch.float32), interm)
+    want = np.array([x[ref.col[ref.row_ptr[i]:ref.row_ptr[i + 1]]].astype(np.float64).sum()
+                     for i in range(ref.rows)])
+    got = interm.cpu().numpy().astype(np.float64)
+    assert np.max(np.abs(got - want) / np.maximum(want, 1e-30)) < 1e-5
+    out = torch.empty(g.V, dtype=torch.float32, device="cuda")
+    C.merge(seg, C.CG_OP_SUM_F32, interm, out)
+    dense = np.zeros(g.V)
+    np.add.at(dense, ref.idx_map, got)
+    assert np.max(np.abs(out.cpu().numpy() - dense) / np.maximum(dense, 1e-30)) < 1e-6
+    # integer min: bit-exact
+    lab = rng.permutation(g.V).astype(np.int32)
+    imin = torch.empty(ref.rows, dtype=torch.int32, device="cuda")
+    C.cg_seg_gather(seg, C.CG_OP_MIN_I32, _dev(torch, lab, torch.int32), imin)
+    want = np.array([lab[ref.col[ref.row_ptr[i]:ref.row_ptr[i + 1]]].min()
+                     for i in range(ref.rows)])
+    assert np.array_equal(imin.cpu().numpy(), want)
+    omin = torch.empty(g.V, dtype=torch.int32, device="cuda")
+    C.merge(seg, C.CG_OP_MIN_I32, imin, omin)
+    dm = np.full(g.V, 2**31 - 1, dtype=np.int64)
+    np.minimum.at(dm, ref.idx_map, want)
+    assert np.array_equal(omin.cpu().numpy(), dm)
+
+
+# ------------------------------------------------------------------ PageRank
+
+def _pagerank_gpu(torch, g, k=None, cluster=0, iters=20, B=4096, bounds=None, probe=False):
+    from paper_1608_01362_gb300 import pipeline as P
+    graph = P.Graph(g.offsets, g.src, cluster_mode=cluster)
+    pr = P.PlainPageRank(graph, probe=probe) if k is None else \
+        P.SegmentedPageRank(graph, k, merge_block=B, bounds=bounds)
+    rank, resid = pr.run(iterations=iters)
+    torch.cuda.synchronize()
+    return rank.cpu().numpy(), resid.cpu().numpy(), pr
+
+
+@pytest.fixture(scope="module")
+def rmat16_oracle(rmat16):
+    return O.pagerank(rmat16.offsets, rmat16.src, iters=20)
+
+
+@pytest.mark.parametrize("cluster", [None, 0])
+def test_plain_pagerank_parity(C, torch_mod, rmat16, rmat16_oracle, cluster):
+    rank, resid, _ = _pagerank_gpu(torch_mod, rmat16, None, cluster)
+    want, want_resid = rmat16_oracle
+    assert rel_l1(rank, want) <= TOL_L1
+    assert abs(rank.astype(np.float64).sum() - 1.0) < 1e-4
+    assert np.max(np.abs(resid - want_resid) / want_resid) < 1e-2
+
+
+@pytest.mark.parametrize("k,cluster,B", [(1, None, 4096), (2, None, 4096), (4, 0, 4096),
+                                         (8, 0, 1024), (16, 1, 4096), (64, 0, 12288),
+                                         (1024, 0, 256)])
+def test_segmented_pagerank_parity(C, torch_mod, rmat16, rmat16_oracle, k, cluster, B):
+    rank, resid, pr = _pagerank_gpu(torch_mod, rmat16, k, cluster, B=B)
+    want, want_resid = rmat16_oracle
+    assert rel_l1(rank, want) <= TOL_L1
+    assert np.max(np.abs(resid - want_resid) / want_resid) < 1e-2
+    assert pr.info["num_segments"] == k
+
+
+def test_segmented_nonuniform_bounds(C, torch_mod, rmat16, rmat16_oracle):
+    V = rmat16.V
+    bounds = np.array([0, 4096, 4096, 30000, V], dtype=np.int64)
+    rank, _, _ = _pagerank_gpu(torch_mod, rmat16, 4, 0, bounds=bounds)
+    assert rel_l1(rank, rmat16_oracle[0]) <= TOL_L1
+
+
+@pytest.mark.parametrize("name", list(_special_graphs().keys()))
+def test_pagerank_special_graphs(C, torch_mod, name):
+    g = _special_graphs()[name]
+    want, _ = O.pagerank(g.offsets, g.src, iters=20)
+    for k in (None, 1, 3):
+        if k is not None and k > g.V:
+            continue
+        rank, _, _ = _pagerank_gpu(torch_mod, g, k, 0, B=64)
+        assert rel_l1(rank, want) <= TOL_L1, (name, k)
+
+
+def test_single_iteration_and_ping_pong(C, torch_mod, rmat16):
+    """iterations = 1, 2, 3 land in the output buffers and match the oracle."""
+    for it in (1, 2, 3):
+        want, _ = O.pagerank(rmat16.offsets, rmat16.src, iters=it)
+        rank, resid, _ = _pagerank_gpu(torch_mod, rmat16, 4, 0, iters=it)
+        assert rel_l1(rank, want) <= TOL_L1 and resid.shape == (it,)
+
+
+def test_probe_reads_vertex_zero_only(C, torch_mod):
+    """The lower-bound probe gathers contrib[0] for every edge (Fig. 1)."""
+    torch = torch_mod
+    g = graphgen.rmat(12, 8, seed=2)
+    from paper_1608_01362_gb300 import pipeline as P
+    graph = P.Graph(g.offsets, g.src, cluster_mode=None)
+    pr = P.PlainPageRank(graph, probe=True)
+    pr.init()
+    pr.step(pr.rank[0], pr.contrib[0], pr.rank[1], pr.contrib[1], 0.85, 1)
+    got = pr.rank[1].cpu().numpy().astype(np.float64)
+    od = O.out_degree(g.offsets, g.src)
+    c0 = (1.0 / g.V) / od[0] if od[0] else 0.0
+    D = (od == 0).sum() / g.V
+    want = 0.15 / g.V + 0.85 * (np.diff(g.offsets) * c0 + D / g.V)
+    assert np.max(np.abs(got - want) / want) < 1e-5
+
+
+def test_pagerank_rejects_aliasing(C, torch_mod, rmat16):
+    torch = torch_mod
+    from paper_1608_01362_gb300 import pipeline as P
+    graph = P.Graph(rmat16.offsets, rmat16.src, cluster_mode=None)
+    pr = P.SegmentedPageRank(graph, 2)
+    pr.init()
+    with pytest.raises(C.CagraError, match="alias"):
+        pr.step(pr.rank[0], pr.contrib[0], pr.rank[0], pr.contrib[1], 0.85, 1)
+    with pytest.raises(C.CagraError, match="iterations"):
+        pr.step(pr.rank[0], pr.contrib[0], pr.rank[1], pr.contrib[1], 0.85, 0)
+
+
+def test_deterministic_repeat(C, torch_mod, rmat16):
+    a, ra, _ = _pagerank_gpu(torch_mod, rmat16, 4, 0)
+    b, rb, _ = _pagerank_gpu(torch_mod, rmat16, 4, 0)
+    assert np.array_equal(a, b) and np.array_equal(ra, rb)
