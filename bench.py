@@ -216,17 +216,19 @@ def main():
     torch.cuda.synchronize()
     cluster_s = time.time() - t0
 
-    sweep = (1, 2, 4, 8, 16, 32, 64) if args.sweep else (1, 2, 4, 8, 16)
     if args.k:
-        best_k, table = args.k, {}
+        best, table = {"kind": "uniform", "k": args.k, "ctas": 2}, []
     else:
-        best_k, table = P.autotune_segments(graph, sweep, merge_block=args.merge_block)
+        uk = (1, 2, 4, 8, 16, 32, 64) if args.sweep else (1, 4, 16)
+        best, table = P.autotune_segments(graph, P.default_candidates(uniform_k=uk),
+                                          merge_block=args.merge_block)
     torch.cuda.synchronize()
     t0 = time.time()
-    pr = P.SegmentedPageRank(graph, best_k, merge_block=args.merge_block)
+    pr = P.build_candidate(graph, best, merge_block=args.merge_block)
     torch.cuda.synchronize()
     seg_s = time.time() - t0
     info = pr.info
+    best_k = info["num_segments"]
 
     stream = torch.cuda.current_stream()
     resid = torch.zeros(ITERS, dtype=torch.float64, device=dev)
@@ -345,6 +347,8 @@ def main():
         "config": {"workload": f"pagerank_rmat{args.scale}_directed_ef16_segmented_clustered",
                    "V": V, "E": E, "iterations_per_step": ITERS, "damping": DAMPING,
                    "segments": best_k, "merge_block": args.merge_block, "q": info["q"],
+                   "segmenting": best, "table_vertices": info["table_vertices"],
+                   "ctas_per_sm": info["ctas_per_sm"],
                    "clustering": "descending out-degree (stable)",
                    "l2_policy": "inputs larger than L2 (2.1 GB edge stream per iteration)",
                    "parallelism": "replicas" if world > 1 else "single GPU"},
@@ -364,8 +368,8 @@ def main():
             "speedup_vs_plain_original": t_plain_orig / seg_iter_s,
             "speedup_vs_plain_clustered": t_plain_cl / seg_iter_s,
         },
-        "k_table": {str(k): {"gteps": E / v["s_per_iter"] / 1e9, "q": v["q"]}
-                    for k, v in table.items()},
+        "autotune": [{**r["candidate"], "k": r["k"], "q": round(r["q"], 4),
+                      "gteps": round(E / r["s_per_iter"] / 1e9, 2)} for r in table],
         "preprocessing_s": {"generate_host": gen_s, "degrees_cluster_relabel": cluster_s,
                             "segment_build": seg_s},
         "rank_mass": mass,

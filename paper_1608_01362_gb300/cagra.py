@@ -25,7 +25,8 @@ CG_OP_MIN_I32 = 1
 EXPORTS = [
     "cg_status_string", "cg_last_error_message", "cg_version",
     "cg_out_degree", "cg_inv_outdeg", "cg_cluster", "cg_relabel_csr", "cg_permute4",
-    "pr_build_segments", "cg_segmented_get_info", "cg_segmented_export",
+    "pr_build_segments", "cg_segmented_get_info", "pr_plan_bounds", "pr_set_gather_config",
+    "pr_gather_table_capacity", "cg_segmented_export",
     "cg_segmented_destroy", "cg_seg_gather", "merge",
     "pr_init", "pr_contrib", "pr_iterate", "pr_merge_update", "pr_plain_create", "pr_plain_destroy", "pr_iterate_plain",
 ]
@@ -39,7 +40,8 @@ class SegInfo(ctypes.Structure):
     _fields_ = [("V", ctypes.c_int32), ("E", ctypes.c_int64), ("num_segments", ctypes.c_int32),
                 ("merge_block", ctypes.c_int32), ("num_blocks", ctypes.c_int32),
                 ("rows", ctypes.c_int64), ("q", ctypes.c_double),
-                ("device_bytes", ctypes.c_int64), ("gather_tiles", ctypes.c_int64)]
+                ("device_bytes", ctypes.c_int64), ("gather_tiles", ctypes.c_int64),
+                ("table_vertices", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32)]
 
 
 def load(path: str | None = None):
@@ -66,6 +68,9 @@ def load(path: str | None = None):
             "pr_build_segments": (ctypes.c_int, [vp, vp, i32, i64, i32, vp, i32,
                                                  ctypes.POINTER(vp), vp]),
             "cg_segmented_get_info": (ctypes.c_int, [vp, ctypes.POINTER(SegInfo)]),
+            "pr_plan_bounds": (ctypes.c_int, [vp, i32, i32, dbl, i32, i32, vp, vp, vp]),
+            "pr_set_gather_config": (ctypes.c_int, [vp, i32, i32, vp]),
+            "pr_gather_table_capacity": (ctypes.c_int, [i32]),
             "cg_segmented_export": (ctypes.c_int, [vp, vp, vp, vp, vp, vp, vp, vp, vp]),
             "cg_segmented_destroy": (ctypes.c_int, [vp]),
             "cg_seg_gather": (ctypes.c_int, [vp, i32, vp, vp, vp]),
@@ -193,6 +198,27 @@ def pr_build_segments(offsets, src, num_segments: int, bounds=None, merge_block:
                                     src.numel(), num_segments, hb, merge_block, ctypes.byref(h),
                                     _stream(stream)), "pr_build_segments")
     return Segmented(h.value)
+
+
+def pr_plan_bounds(outdeg, smem_vertices: int = -1, min_avg_degree: float = 64.0,
+                   max_global_vertices: int = 1 << 24, k_max: int = 1024, stream=None):
+    """Segment bounds for this GPU (host int64 array of k+1 entries)."""
+    out = np.empty(k_max + 1, dtype=np.int64)
+    k = ctypes.c_int32()
+    _check(load().pr_plan_bounds(_ptr(outdeg), outdeg.numel(), smem_vertices, min_avg_degree,
+                                 max_global_vertices, k_max, out.ctypes.data, ctypes.byref(k),
+                                 _stream(stream)), "pr_plan_bounds")
+    return out[:k.value + 1].copy()
+
+
+def pr_set_gather_config(seg: Segmented, table_vertices: int = -1, ctas_per_sm: int = 2,
+                         stream=None):
+    _check(load().pr_set_gather_config(seg.handle, table_vertices, ctas_per_sm,
+                                       _stream(stream)), "pr_set_gather_config")
+
+
+def pr_gather_table_capacity(ctas_per_sm: int = 2) -> int:
+    return int(load().pr_gather_table_capacity(ctas_per_sm))
 
 
 def cg_segmented_export(seg: Segmented, stream=None) -> dict:

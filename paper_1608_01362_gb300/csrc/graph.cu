@@ -169,7 +169,7 @@ int cg_relabel_csr(const int64_t* offsets, const int32_t* src, int32_t V, int64_
   CG_ARG(V >= 1 && E >= 0, "cg_relabel_csr: V must be >= 1 and E >= 0");
   CG_ARG(offsets && new_of_old && old_of_new && out_offsets && (E == 0 || (src && out_src)),
          "cg_relabel_csr: null pointer");
-  CG_ARG((const void*)out_src != (const void*)src &&
+  CG_ARG((E == 0 || (const void*)out_src != (const void*)src) &&
              (const void*)out_offsets != (const void*)offsets,
          "cg_relabel_csr: outputs must not alias inputs");
   int64_t* len = nullptr;

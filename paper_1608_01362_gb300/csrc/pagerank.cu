@@ -191,8 +191,9 @@ __global__ void sum_partials_kernel(const double* __restrict__ partials, int n,
 }
 
 int set_merge_smem(const void* fn, int B, size_t elem) {
+  // the kernels also hold a little static shared memory, so opt in above 32 KB
   const size_t bytes = (size_t)B * elem;
-  if (bytes > 48 * 1024)
+  if (bytes > 32 * 1024)
     CG_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
   return CG_OK;
 }
@@ -390,7 +391,8 @@ int pr_plain_create(const int64_t* offsets, const int32_t* src, int32_t V, int64
   p->offsets = offsets;
   p->src = src;
   p->nb = (int32_t)ceil_div(V, 4096);
-  int st = plan_gather<int64_t>(offsets + 1, V, E, &p->plan, stream);
+  const std::vector<int64_t> rb = {0, (int64_t)V}, eb = {0, E};
+  int st = plan_gather<int64_t>(offsets + 1, V, E, 1, rb, eb, rb, 0, 8, &p->plan, stream);
   cudaError_t e = cudaSuccess;
   if (st == CG_OK) e = cudaMalloc((void**)&p->acc, sizeof(float) * (size_t)V);
   if (e == cudaSuccess) e = cudaMalloc((void**)&p->partials, sizeof(double) * 2 * p->nb);

@@ -382,7 +382,9 @@ int build_impl(const int64_t* offsets, const int32_t* src, int32_t V, int64_t E,
   }
 
   // F
-  CG_TRY(plan_gather<int32_t>(g->row_ptr + 1, npairs, E, &g->plan, s));
+  CG_CUDA(cudaStreamSynchronize(s));  // edge_base copies have landed
+  CG_TRY(plan_gather<int32_t>(g->row_ptr + 1, npairs, E, k, g->row_base, g->edge_base, bounds,
+                              -1, 2, &g->plan, s));
   CG_CUDA(cudaMalloc(&g->interm, sizeof(float) * (size_t)(npairs > 0 ? npairs : 1)));
   CG_CUDA(cudaMalloc((void**)&g->partials, sizeof(double) * 2 * (size_t)g->nb));
   CG_CUDA(cudaMalloc((void**)&g->counter, sizeof(unsigned)));
@@ -494,6 +496,60 @@ int cg_segmented_get_info(const cg_segmented* g, cg_segmented_info* info) {
   info->q = g->V ? (double)g->rows / (double)g->V : 0.0;
   info->device_bytes = g->bytes;
   info->gather_tiles = g->plan.ntiles;
+  info->table_vertices = g->plan.tab_cap;
+  info->ctas_per_sm = g->plan.ctas_per_sm;
+  return CG_OK;
+}
+
+int pr_set_gather_config(cg_segmented* g, int32_t table_vertices, int32_t ctas_per_sm,
+                         cudaStream_t stream) {
+  CG_ARG(g != nullptr, "pr_set_gather_config: null handle");
+  CG_ARG(ctas_per_sm >= 1 && ctas_per_sm <= 32, "pr_set_gather_config: ctas_per_sm in [1, 32]");
+  CG_ARG(table_vertices >= -1, "pr_set_gather_config: table_vertices must be >= -1");
+  return configure_gather(&g->plan, table_vertices, ctas_per_sm, stream);
+}
+
+int pr_gather_table_capacity(int32_t ctas_per_sm) {
+  return gather_table_capacity(ctas_per_sm);
+}
+
+int pr_plan_bounds(const int32_t* dev_outdeg, int32_t V, int32_t smem_vertices,
+                   double min_avg_degree, int32_t max_global_vertices, int32_t k_max,
+                   int64_t* host_bounds, int32_t* k_out, cudaStream_t stream) {
+  CG_ARG(dev_outdeg && host_bounds && k_out && V >= 1, "pr_plan_bounds: bad arguments");
+  CG_ARG(k_max >= 1 && k_max <= kMaxSegments, "pr_plan_bounds: k_max must be in [1, %d]",
+         kMaxSegments);
+  CG_ARG(max_global_vertices >= 1, "pr_plan_bounds: max_global_vertices must be >= 1");
+  if (smem_vertices < 0) smem_vertices = gather_table_capacity(2);
+  std::vector<int32_t> deg(V);
+  CG_CUDA(cudaMemcpyAsync(deg.data(), dev_outdeg, sizeof(int32_t) * (size_t)V,
+                          cudaMemcpyDeviceToHost, stream));
+  CG_CUDA(cudaStreamSynchronize(stream));
+  std::vector<int64_t> b = {0};
+  int64_t lo = 0;
+  if (smem_vertices > 0) {
+    while (lo < V && (int)b.size() < k_max) {
+      const int64_t n = std::min<int64_t>(smem_vertices, V - lo);
+      int64_t edges = 0;
+      for (int64_t u = lo; u < lo + n; ++u) edges += deg[u];
+      if ((double)edges < min_avg_degree * (double)n) break;
+      lo += n;
+      b.push_back(lo);
+    }
+  }
+  if (lo < V) {
+    const int64_t left_k = k_max - ((int64_t)b.size() - 1);
+    if (left_k < 1) {
+      b.back() = V;  // no room: the last shared-memory segment absorbs the rest
+    } else {
+      int64_t parts = std::max<int64_t>(1, ceil_div(V - lo, max_global_vertices));
+      if (parts > left_k) parts = left_k;
+      const int64_t step = ceil_div(V - lo, parts);
+      for (int64_t q = 1; q <= parts; ++q) b.push_back(std::min<int64_t>(V, lo + q * step));
+    }
+  }
+  *k_out = (int32_t)(b.size() - 1);
+  for (size_t q = 0; q < b.size(); ++q) host_bounds[q] = b[q];
   return CG_OK;
 }
 

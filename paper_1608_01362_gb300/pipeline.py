@@ -4,6 +4,7 @@ step a call into the CUDA library (no computation here).
 """
 from __future__ import annotations
 
+import numpy as np
 import torch
 
 from . import cagra as C
@@ -75,13 +76,27 @@ class _PageRankBase:
         return self.g.to_original(self.rank[1]), resid
 
 
+def plan_bounds(graph: Graph, ctas_per_sm: int = 2, min_avg_degree: float = 64.0,
+                max_global_vertices: int = 1 << 24):
+    """Segment bounds for this GPU: shared-memory-sized segments over the hot
+    (clustered) head, L2-sized segments over the cold rest."""
+    H = C.pr_gather_table_capacity(ctas_per_sm)
+    return C.pr_plan_bounds(graph.outdeg, H, min_avg_degree, max_global_vertices)
+
+
 class SegmentedPageRank(_PageRankBase):
     """PageRank through CSR segmenting (Algorithms 2-5)."""
 
-    def __init__(self, graph: Graph, num_segments: int, merge_block: int = 4096, bounds=None):
+    def __init__(self, graph: Graph, num_segments: int | None = None, merge_block: int = 4096,
+                 bounds=None, table_vertices: int = -1, ctas_per_sm: int = 2):
         super().__init__(graph)
+        if bounds is not None:
+            bounds = np.asarray(bounds, dtype=np.int64)
+            num_segments = len(bounds) - 1
         self.seg = C.pr_build_segments(graph.offsets, graph.src, num_segments, bounds=bounds,
                                        merge_block=merge_block)
+        if (table_vertices, ctas_per_sm) != (-1, 2):
+            C.pr_set_gather_config(self.seg, table_vertices, ctas_per_sm)
 
     @property
     def info(self):
@@ -121,25 +136,49 @@ def time_iterations(pr, iterations: int = 3, damping: float = 0.85, reps: int = 
     return times[len(times) // 2]
 
 
-def autotune_segments(graph: Graph, candidates=(1, 2, 4, 8, 16, 32, 64), merge_block: int = 4096,
+def default_candidates(uniform_k=(1, 2, 4, 8, 16), ctas=(2, 3, 4), min_deg=(16.0, 64.0, 256.0)):
+    """Autotuner search space: the paper's uniform split into k segments, and
+    the GPU plan (shared-memory segments over the hot head, L2 segments over
+    the rest) at several blocks-per-SM / staging thresholds."""
+    out = [{"kind": "uniform", "k": k, "ctas": c} for k in uniform_k for c in (2, 4)]
+    out += [{"kind": "plan", "ctas": c, "min_avg_degree": m} for c in ctas for m in min_deg]
+    return out
+
+
+def _build(graph, cand, merge_block):
+    if cand["kind"] == "uniform":
+        return SegmentedPageRank(graph, cand["k"], merge_block=merge_block,
+                                 ctas_per_sm=cand["ctas"])
+    b = plan_bounds(graph, cand["ctas"], cand["min_avg_degree"])
+    return SegmentedPageRank(graph, bounds=b, merge_block=merge_block, ctas_per_sm=cand["ctas"])
+
+
+def autotune_segments(graph: Graph, candidates=None, merge_block: int = 4096,
                       iterations: int = 3, reps: int = 3):
-    """Pick the segment count k by measuring a few iterations for each
-    candidate (Section III-D's trade-off: smaller segments confine the
-    random reads to a smaller, faster cache level but raise the expansion
-    factor q and the merge traffic).  Returns (best_k, table) where table
-    maps k -> {"s_per_iter", "q"}."""
-    table = {}
+    """Pick the segmenting by measuring a few iterations of each candidate
+    (Section III-D's trade-off: smaller segments confine the random reads to
+    a smaller, faster memory but raise the expansion factor q and the merge
+    traffic).  Returns (best candidate, list of {candidate, s_per_iter, q, k})."""
+    if candidates is None:
+        candidates = default_candidates()
+    results = []
     best = None
-    for k in candidates:
-        if k > graph.V:
+    for cand in candidates:
+        if cand["kind"] == "uniform" and cand["k"] > graph.V:
             continue
-        pr = SegmentedPageRank(graph, k, merge_block=merge_block)
+        pr = _build(graph, cand, merge_block)
         pr.init()
         pr.step(pr.rank[0], pr.contrib[0], pr.rank[1], pr.contrib[1], 0.85, 1)  # warm-up
         t = time_iterations(pr, iterations, reps=reps)
-        table[k] = {"s_per_iter": t, "q": pr.info["q"]}
-        if best is None or t < table[best]["s_per_iter"]:
-            best = k
+        inf = pr.info
+        results.append({"candidate": cand, "s_per_iter": t, "q": inf["q"],
+                        "k": inf["num_segments"], "table_vertices": inf["table_vertices"]})
+        if best is None or t < best[1]:
+            best = (cand, t)
         pr.seg.close()
         del pr
-    return best, table
+    return best[0], results
+
+
+def build_candidate(graph: Graph, cand: dict, merge_block: int = 4096) -> SegmentedPageRank:
+    return _build(graph, cand, merge_block)
