@@ -119,9 +119,10 @@ typedef struct {
   int64_t rows;          /* total subgraph rows = sum_s |dst(s)| = q V */
   double q;              /* expansion factor rows / V (Section III-D) */
   int64_t device_bytes;  /* device memory held by the handle */
-  int64_t gather_tiles;  /* work tiles of one segment-processing pass */
+  int64_t gather_tiles;  /* 256-edge chunks of one segment-processing pass */
   int32_t table_vertices; /* shared-memory table entries per block */
   int32_t ctas_per_sm;   /* gather blocks per SM */
+  int32_t gather_threads; /* threads per gather block */
 } cg_segmented_info;
 
 /*
@@ -151,8 +152,8 @@ int cg_segmented_get_info(const cg_segmented *seg, cg_segmented_info *info);
  * Segment sizes for this GPU (Section III-D's segment-size choice, re-derived
  * for an SM's shared memory and the L2): after frequency-based clustering the
  * hottest sources come first, so the vertex range is cut into segments of
- * `smem_vertices` sources (-1: the gather's shared-table capacity at two
- * blocks per SM) for as long as such a segment still carries at least
+ * `smem_vertices` sources (-1: the gather's shared-table capacity at one
+ * block per SM) for as long as such a segment still carries at least
  * `min_avg_degree` out-edges per vertex, i.e. enough reads to repay staging
  * it on chip; the colder rest is cut into segments of at most
  * `max_global_vertices` sources, served through L1/L2.  dev_outdeg: int32[V]
@@ -165,14 +166,16 @@ int pr_plan_bounds(const int32_t *dev_outdeg, int32_t V, int32_t smem_vertices,
                    cudaStream_t stream);
 
 /*
- * Launch shape of the segment-processing gather of `seg`: each block keeps
- * the first `table_vertices` source values of its current segment in shared
- * memory (-1: as many as fit with `ctas_per_sm` blocks per SM; 0: none), with
- * `ctas_per_sm` persistent blocks per SM.  Results do not depend on it.
+ * Launch shape of the segment-processing gather of `seg`: `threads` (512 or
+ * 1024) per block, `ctas_per_sm` persistent blocks per SM (at most
+ * 2048/threads); each block keeps the first `table_vertices` source values of
+ * its current segment in shared memory (-1: as many as fit; 0: none) when
+ * the segment has enough edges to repay loading them.  Results do not depend
+ * on it.  Default after pr_build_segments: 1024 threads, 1 block/SM, -1.
  * Synchronizes the stream.
  */
-int pr_set_gather_config(cg_segmented *seg, int32_t table_vertices,
-                         int32_t ctas_per_sm, cudaStream_t stream);
+int pr_set_gather_config(cg_segmented *seg, int32_t threads, int32_t ctas_per_sm,
+                         int32_t table_vertices, cudaStream_t stream);
 
 /* Shared-table capacity (entries) of the gather at ctas_per_sm blocks/SM. */
 int pr_gather_table_capacity(int32_t ctas_per_sm);

@@ -41,7 +41,8 @@ class SegInfo(ctypes.Structure):
                 ("merge_block", ctypes.c_int32), ("num_blocks", ctypes.c_int32),
                 ("rows", ctypes.c_int64), ("q", ctypes.c_double),
                 ("device_bytes", ctypes.c_int64), ("gather_tiles", ctypes.c_int64),
-                ("table_vertices", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32)]
+                ("table_vertices", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32),
+                ("gather_threads", ctypes.c_int32)]
 
 
 def load(path: str | None = None):
@@ -69,7 +70,7 @@ def load(path: str | None = None):
                                                  ctypes.POINTER(vp), vp]),
             "cg_segmented_get_info": (ctypes.c_int, [vp, ctypes.POINTER(SegInfo)]),
             "pr_plan_bounds": (ctypes.c_int, [vp, i32, i32, dbl, i32, i32, vp, vp, vp]),
-            "pr_set_gather_config": (ctypes.c_int, [vp, i32, i32, vp]),
+            "pr_set_gather_config": (ctypes.c_int, [vp, i32, i32, i32, vp]),
             "pr_gather_table_capacity": (ctypes.c_int, [i32]),
             "cg_segmented_export": (ctypes.c_int, [vp, vp, vp, vp, vp, vp, vp, vp, vp]),
             "cg_segmented_destroy": (ctypes.c_int, [vp]),
@@ -211,13 +212,13 @@ def pr_plan_bounds(outdeg, smem_vertices: int = -1, min_avg_degree: float = 64.0
     return out[:k.value + 1].copy()
 
 
-def pr_set_gather_config(seg: Segmented, table_vertices: int = -1, ctas_per_sm: int = 2,
-                         stream=None):
-    _check(load().pr_set_gather_config(seg.handle, table_vertices, ctas_per_sm,
+def pr_set_gather_config(seg: Segmented, threads: int = 1024, ctas_per_sm: int = 1,
+                         table_vertices: int = -1, stream=None):
+    _check(load().pr_set_gather_config(seg.handle, threads, ctas_per_sm, table_vertices,
                                        _stream(stream)), "pr_set_gather_config")
 
 
-def pr_gather_table_capacity(ctas_per_sm: int = 2) -> int:
+def pr_gather_table_capacity(ctas_per_sm: int = 1) -> int:
     return int(load().pr_gather_table_capacity(ctas_per_sm))
 
 

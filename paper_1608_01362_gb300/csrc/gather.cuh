@@ -1,23 +1,14 @@
-// The pull gather shared by every application: for every row i of a CSR
-// (rows = subgraph rows of the segmented graph, or destinations of the plain
-// graph) out[i] = op over the row's edges e of x[col[e]].
+// The plain pull gather (Algorithm 1) over a caller's CSR: for every row i,
+// out[i] = op over the row's edges e of x[col[e]].  The segmented graph uses
+// the flagged-edge gather of seg_gather.cuh instead.
 //
 // Work split (merge-path over rows + edges): the merged sequence of "row
-// ends" and "edges" (rows + E items) of every segment is cut into tiles of
-// TILE = THREADS * IPT items, so every tile costs the same however skewed the
-// row lengths are; tiles never straddle two segments.  The tiles' start
-// (row, edge) and segment are computed once per graph.
-//
-// A persistent grid walks the tiles round-robin (tile t goes to block
-// t mod grid), so all blocks move through the segments together, in segment
-// order, as Algorithm 3 prescribes.  Each block keeps a shared-memory copy of
-// the first `tab_cap` source values of its current segment: a segment no
-// larger than that is served entirely from shared memory (the on-chip
-// analogue of the paper's cache-sized segment); in a larger segment the
-// table holds its hottest head (vertices are clustered hottest-first) and
-// the other reads go through L1/L2.  In a tile:
-//   1. edges: coalesced streaming reads of col, then the value reads (table
-//      or global) into shared memory;
+// ends" and "edges" (rows + E items) is cut into tiles of TILE = THREADS *
+// IPT items, so every block does the same amount of work however skewed the
+// row lengths are.  A tile's start (row, edge) is precomputed once per graph
+// (static across iterations).  In a tile:
+//   1. edges: coalesced streaming reads of col, then the random reads of x
+//      (many independent loads in flight per thread) into shared memory;
 //   2. row ends of the tile's rows into shared memory;
 //   3. each thread walks IPT consecutive merged items sequentially, folding
 //      edges into its running value and emitting a row at each row end;
@@ -29,8 +20,6 @@
 // Shared arrays indexed by item are padded one word per 32 so the threads'
 // strided walks hit distinct banks.  No atomics; deterministic.
 #pragma once
-
-#include <vector>
 
 #include "common.cuh"
 
@@ -47,9 +36,15 @@ struct MinI32 {
   static __device__ __forceinline__ T op(T a, T b) { return a < b ? a : b; }
 };
 
+// Read-only random load of a gathered vertex value (L1-cached).
+template <typename T>
+__device__ __forceinline__ T ld_gather(const T* p) { return __ldg(p); }
+
+__device__ __forceinline__ int pad32(int p) { return p + (p >> 5); }
+
 // Merge-path search: number of rows consumed among the first `diag` merged
 // items, given row_end[] relative to the first edge (edge j is consumed
-// before row i iff j < row_end[i]).  PADDED reads row_end[i + i/32].
+// before row i iff j < row_end[i]).
 template <bool PADDED, typename RowEndT>
 __device__ __forceinline__ int64_t merge_path_search(int64_t diag, const RowEndT* row_end,
                                                      int64_t nrows, int64_t nedges,
@@ -67,188 +62,145 @@ __device__ __forceinline__ int64_t merge_path_search(int64_t diag, const RowEndT
   return lo;
 }
 
-__device__ __forceinline__ int pad32(int p) { return p + (p >> 5); }
-
-// Tile boundaries: tile t lies in segment s = tile_seg[t]; its start is the
-// merge-path point at diagonal seg_diag[s] + (t - tile_base[s]) * tile.
+// One thread per tile boundary t in [0, ntiles]: (row, edge) at diagonal t*TILE.
 template <typename RowEndT>
 __global__ void tile_partition_kernel(const RowEndT* __restrict__ row_end, int64_t nrows,
-                                      int64_t nedges, int64_t tile, int64_t ntiles, int k,
-                                      const int64_t* __restrict__ tile_base,
-                                      const int64_t* __restrict__ seg_diag,
+                                      int64_t nedges, int64_t tile, int64_t ntiles,
                                       int32_t* __restrict__ tile_row,
-                                      int32_t* __restrict__ tile_edge,
-                                      int32_t* __restrict__ tile_seg) {
+                                      int32_t* __restrict__ tile_edge) {
   for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t <= ntiles;
        t += (int64_t)gridDim.x * blockDim.x) {
-    int64_t d;
-    if (t == ntiles) {
-      d = nrows + nedges;
-    } else {
-      int lo = 0, hi = k + 1;  // last s with tile_base[s] <= t (non-empty segments only)
-      while (lo < hi) {
-        const int mid = (lo + hi) >> 1;
-        if (tile_base[mid] <= t) lo = mid + 1; else hi = mid;
-      }
-      const int s = lo - 1;
-      tile_seg[t] = s;
-      d = seg_diag[s] + (t - tile_base[s]) * tile;
-    }
+    int64_t d = t * tile;
+    if (d > nrows + nedges) d = nrows + nedges;
     const int64_t i = merge_path_search<false>(d, row_end, nrows, nedges, 0);
     tile_row[t] = (int32_t)i;
     tile_edge[t] = (int32_t)(d - i);
   }
 }
 
-// The persistent gather kernel.  row_end[i] = first edge after row i (global
-// edge index); col: global source IDs; seg_lo[s]: first source of segment s;
-// seg_tab[s]: how many of its first sources the shared table holds.  PROBE
-// sends every read to x[0] (the paper's lower-bound program).
+// The gather tile kernel.  row_end[i] = first edge after row i (global edge
+// index); col: global source IDs; PROBE sends every gathered read to x[0].
 template <class Op, int THREADS, int IPT, bool PROBE, typename RowEndT>
 __global__ void __launch_bounds__(THREADS)
-gather_kernel(const RowEndT* __restrict__ row_end, const int32_t* __restrict__ col,
-              const typename Op::T* __restrict__ x, int32_t nx,
-              const int32_t* __restrict__ tile_row, const int32_t* __restrict__ tile_edge,
-              const int32_t* __restrict__ tile_seg, int64_t ntiles,
-              const int32_t* __restrict__ seg_lo, const int32_t* __restrict__ seg_tab,
-              int tab_cap, typename Op::T* __restrict__ out, typename Op::T* __restrict__ carry,
-              int32_t* __restrict__ carry_row) {
+gather_tile_kernel(const RowEndT* __restrict__ row_end, const int32_t* __restrict__ col,
+                   const typename Op::T* __restrict__ x, int32_t nx,
+                   const int32_t* __restrict__ tile_row, const int32_t* __restrict__ tile_edge,
+                   typename Op::T* __restrict__ out, typename Op::T* __restrict__ carry,
+                   int32_t* __restrict__ carry_row) {
   using T = typename Op::T;
   constexpr int TILE = THREADS * IPT;
-  constexpr int PADT = TILE + TILE / 32;
   constexpr int WARPS = THREADS / 32;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  T* tab = reinterpret_cast<T*>(smem_raw);       // [tab_cap]
-  T* s_val = tab + tab_cap;                      // [PADT] edge values
-  int32_t* s_rend = reinterpret_cast<int32_t*>(s_val + PADT);  // [PADT] row ends, then results
+  constexpr int PADT = TILE + TILE / 32;
+  __shared__ T s_val[PADT];
+  __shared__ int32_t s_rend[PADT];  // row ends (relative), later row results (as T bits)
   __shared__ T s_wval[WARPS];
   __shared__ int32_t s_wrow[WARPS];
   __shared__ T s_prev_val[THREADS];
   __shared__ int32_t s_prev_row[THREADS];
 
   const int tid = threadIdx.x;
-  const int lane = tid & 31, w = tid >> 5;
-  int cur_seg = -1;
-  int32_t lo = 0, tn = 0;
+  const int64_t t = blockIdx.x;
+  const int32_t r0 = tile_row[t], r1 = tile_row[t + 1];
+  const int32_t e0 = tile_edge[t], e1 = tile_edge[t + 1];
+  const int nr = r1 - r0, ne = e1 - e0;
 
-  for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
-    const int s = tile_seg[t];
-    const int32_t r0 = tile_row[t], r1 = tile_row[t + 1];
-    const int32_t e0 = tile_edge[t], e1 = tile_edge[t + 1];
-    const int nr = r1 - r0, ne = e1 - e0;
-    __syncthreads();  // the previous tile is done with every shared array
-    if (!PROBE && s != cur_seg) {
-      cur_seg = s;
-      lo = seg_lo[s];
-      tn = seg_tab[s] < tab_cap ? seg_tab[s] : tab_cap;
-      for (int i = tid; i < tn; i += THREADS) tab[i] = x[lo + i];
-      __syncthreads();
+  // 1. edges: stream col, gather x
+  {
+    int32_t c[IPT];
+#pragma unroll
+    for (int u = 0; u < IPT; ++u) {
+      const int j = u * THREADS + tid;
+      c[u] = j < ne ? __ldcs(col + e0 + j) : -1;
     }
-
-    // 1. edges: stream col, read values (shared table or global)
-    {
-      int32_t c[IPT];
+    T v[IPT];
 #pragma unroll
-      for (int u = 0; u < IPT; ++u) {
-        const int j = u * THREADS + tid;
-        c[u] = j < ne ? __ldcs(col + e0 + j) : -1;
-      }
-      T v[IPT];
-#pragma unroll
-      for (int u = 0; u < IPT; ++u) {
-        const int32_t cu = c[u];
-        if (PROBE) {
-          v[u] = cu >= 0 ? __ldg(x) : Op::identity();
-        } else {
-          const uint32_t off = (uint32_t)(cu - lo);
-          if (off < (uint32_t)tn)
-            v[u] = tab[off];
-          else
-            v[u] = (cu >= 0 && cu < nx) ? __ldg(x + cu) : Op::identity();
-        }
-      }
-#pragma unroll
-      for (int u = 0; u < IPT; ++u) {
-        const int j = u * THREADS + tid;
-        if (j < ne) s_val[pad32(j)] = v[u];
-      }
+    for (int u = 0; u < IPT; ++u) {
+      const int32_t cu = c[u];
+      const bool ok = cu >= 0 && cu < nx;
+      v[u] = ok ? ld_gather(x + (PROBE ? 0 : cu)) : Op::identity();
     }
-    // 2. row ends relative to e0 (in [0, ne] for the tile's rows)
-    for (int i = tid; i < nr; i += THREADS)
-      s_rend[pad32(i)] = (int32_t)((int64_t)row_end[r0 + i] - e0);
-    __syncthreads();
+#pragma unroll
+    for (int u = 0; u < IPT; ++u) {
+      const int j = u * THREADS + tid;
+      if (j < ne) s_val[pad32(j)] = v[u];
+    }
+  }
+  // 2. row ends relative to e0 (in [0, ne] for the tile's rows)
+  for (int i = tid; i < nr; i += THREADS)
+    s_rend[pad32(i)] = (int32_t)((int64_t)row_end[r0 + i] - e0);
+  __syncthreads();
 
-    // 3. sequential walk over this thread's merged items
-    const int items = nr + ne;
-    const int d0 = tid * IPT < items ? tid * IPT : items;
-    const int d1 = d0 + IPT < items ? d0 + IPT : items;
-    int i = (int)merge_path_search<true, int32_t>(d0, s_rend, nr, ne, 0);
-    int j = d0 - i;
-    __syncthreads();  // every search is done before row results overwrite s_rend
-    const int first_row = i;
-    bool emitted = false;
-    T first_val = Op::identity();
-    T acc = Op::identity();
-    for (int d = d0; d < d1; ++d) {
-      if (i < nr && s_rend[pad32(i)] <= j) {
-        if (!emitted) {
-          first_val = acc;
-          emitted = true;
-        } else {
-          reinterpret_cast<T*>(s_rend)[pad32(i)] = acc;
-        }
-        acc = Op::identity();
-        ++i;
+  // 3. sequential walk over this thread's merged items
+  const int items = nr + ne;
+  const int d0 = tid * IPT < items ? tid * IPT : items;
+  const int d1 = d0 + IPT < items ? d0 + IPT : items;
+  int i = (int)merge_path_search<true, int32_t>(d0, s_rend, nr, ne, 0);
+  int j = d0 - i;
+  __syncthreads();  // all searches done before row results overwrite s_rend
+  const int first_row = i;
+  bool emitted = false;
+  T first_val = Op::identity();
+  T acc = Op::identity();
+  for (int d = d0; d < d1; ++d) {
+    if (i < nr && s_rend[pad32(i)] <= j) {
+      if (!emitted) {
+        first_val = acc;
+        emitted = true;
       } else {
-        acc = Op::op(acc, s_val[pad32(j)]);
-        ++j;
+        reinterpret_cast<T*>(s_rend)[pad32(i)] = acc;
       }
+      acc = Op::identity();
+      ++i;
+    } else {
+      acc = Op::op(acc, s_val[pad32(j)]);
+      ++j;
     }
+  }
+  // carry of this thread: (open row i, acc)
 
-    // 4. block segmented inclusive scan of the (open row, value) carries
-    int32_t crow = i;
-    T cval = acc;
+  // 4. block segmented inclusive scan of (row, value) over threads
+  const int lane = tid & 31, w = tid >> 5;
+  int32_t crow = i;
+  T cval = acc;
 #pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const int32_t prow = __shfl_up_sync(0xffffffffu, crow, o);
-      const T pval = __shfl_up_sync(0xffffffffu, cval, o);
-      if (lane >= o && prow == crow) cval = Op::op(pval, cval);
-    }
-    if (lane == 31) {
-      s_wrow[w] = crow;
-      s_wval[w] = cval;
-    }
-    __syncthreads();
-    if (w == 0) {
-      int32_t r = lane < WARPS ? s_wrow[lane] : -1;
-      T v = lane < WARPS ? s_wval[lane] : Op::identity();
+  for (int o = 1; o < 32; o <<= 1) {
+    const int32_t prow = __shfl_up_sync(0xffffffffu, crow, o);
+    const T pval = __shfl_up_sync(0xffffffffu, cval, o);
+    if (lane >= o && prow == crow) cval = Op::op(pval, cval);
+  }
+  if (lane == 31) {
+    s_wrow[w] = crow;
+    s_wval[w] = cval;
+  }
+  __syncthreads();
+  if (w == 0) {
+    int32_t r = lane < WARPS ? s_wrow[lane] : -1;
+    T v = lane < WARPS ? s_wval[lane] : Op::identity();
 #pragma unroll
-      for (int o = 1; o < WARPS; o <<= 1) {
-        const int32_t prow = __shfl_up_sync(0xffffffffu, r, o);
-        const T pval = __shfl_up_sync(0xffffffffu, v, o);
-        if (lane >= o && prow == r) v = Op::op(pval, v);
-      }
-      if (lane < WARPS) s_wval[lane] = v;  // inclusive over warps
+    for (int o = 1; o < WARPS; o <<= 1) {
+      const int32_t prow = __shfl_up_sync(0xffffffffu, r, o);
+      const T pval = __shfl_up_sync(0xffffffffu, v, o);
+      if (lane >= o && prow == r) v = Op::op(pval, v);
     }
-    __syncthreads();
-    if (w > 0 && s_wrow[w - 1] == crow) cval = Op::op(s_wval[w - 1], cval);
-    s_prev_row[tid] = crow;
-    s_prev_val[tid] = cval;
-    __syncthreads();
-    if (emitted) {
-      T v = first_val;
-      if (tid > 0 && s_prev_row[tid - 1] == first_row) v = Op::op(s_prev_val[tid - 1], v);
-      reinterpret_cast<T*>(s_rend)[pad32(first_row)] = v;
-    }
-    __syncthreads();
+    if (lane < WARPS) s_wval[lane] = v;  // inclusive over warps
+  }
+  __syncthreads();
+  if (w > 0 && s_wrow[w - 1] == crow) cval = Op::op(s_wval[w - 1], cval);
+  s_prev_row[tid] = crow;
+  s_prev_val[tid] = cval;
+  __syncthreads();
+  if (emitted) {
+    T v = first_val;
+    if (tid > 0 && s_prev_row[tid - 1] == first_row) v = Op::op(s_prev_val[tid - 1], v);
+    reinterpret_cast<T*>(s_rend)[pad32(first_row)] = v;
+  }
+  __syncthreads();
 
-    // 5. coalesced row results; tile carry for the row open at the tile end
-    for (int r = tid; r < nr; r += THREADS)
-      out[r0 + r] = reinterpret_cast<T*>(s_rend)[pad32(r)];
-    if (tid == THREADS - 1) {
-      carry[t] = cval;  // the last thread's inclusive value is the open row's tile part
-      carry_row[t] = r0 + crow;
-    }
+  // 5. coalesced row results; tile carry for the row open at the tile end
+  for (int r = tid; r < nr; r += THREADS) out[r0 + r] = reinterpret_cast<T*>(s_rend)[pad32(r)];
+  if (tid == THREADS - 1) {
+    carry[t] = cval;     // the last thread's inclusive value is the open row's tile part
+    carry_row[t] = r0 + crow;
   }
 }
 
@@ -270,52 +222,62 @@ __global__ void carry_fixup_kernel(const typename Op::T* __restrict__ carry,
   }
 }
 
-constexpr int kGatherThreads = 256;
-constexpr int kGatherIPT = 8;
-constexpr int kGatherTile = kGatherThreads * kGatherIPT;
-constexpr int kGatherPadTile = kGatherTile + kGatherTile / 32;
-// Static shared memory of gather_kernel (scan scratch), for occupancy sizing.
-constexpr int kGatherStaticSmem = kGatherThreads * 8 + 64 + 64;
-
-// Tiling of one gather: per-tile start row / edge / segment, per-segment
-// source range and table length, the carry buffers and the launch shape.
-struct GatherPlan {
+// Tiling of one gather: per-tile start row / edge and the carry buffers.
+struct TilePlan {
   int64_t nrows = 0, nedges = 0, ntiles = 0, tile = 0;
-  int k = 0;
   int32_t* tile_row = nullptr;   // [ntiles+1]
   int32_t* tile_edge = nullptr;  // [ntiles+1]
-  int32_t* tile_seg = nullptr;   // [ntiles]
-  int32_t* seg_lo = nullptr;     // [k] first source of each segment
-  int32_t* seg_tab = nullptr;    // [k] table length of each segment
-  void* carry = nullptr;         // [ntiles] 4-byte values
+  void* carry = nullptr;         // [ntiles] of 4-byte values
   int32_t* carry_row = nullptr;  // [ntiles]
-  std::vector<int64_t> src_bounds;  // host copy [k+1]
-  int tab_cap = 0;               // shared table capacity (entries)
-  int ctas_per_sm = 2;
-  int grid = 0;
 };
 
-// Largest table (entries, multiple of 32) that lets `ctas` blocks share an SM.
-int gather_table_capacity(int ctas);
+constexpr int kTileThreads = 256;
+constexpr int kTileIPT = 8;
+constexpr int kTileItems = kTileThreads * kTileIPT;
 
-// Build a plan (cudaMalloc: the plan lives with its handle).  row_base /
-// edge_base / src_bounds: host arrays of k+1 entries (one segment for the
-// plain CSR).  Synchronizes the stream.
+// Allocate and fill a plan (cudaMalloc: the plan lives with its handle).
 template <typename RowEndT>
-int plan_gather(const RowEndT* row_end, int64_t nrows, int64_t nedges, int k,
-                const std::vector<int64_t>& row_base, const std::vector<int64_t>& edge_base,
-                const std::vector<int64_t>& src_bounds, int tab_vertices, int ctas_per_sm,
-                GatherPlan* p, cudaStream_t s);
+int plan_tiles(const RowEndT* row_end, int64_t nrows, int64_t nedges, TilePlan* p,
+                cudaStream_t s) {
+  p->nrows = nrows;
+  p->nedges = nedges;
+  p->tile = kTileItems;
+  p->ntiles = ceil_div(nrows + nedges, kTileItems);
+  const size_t nb = sizeof(int32_t) * (size_t)(p->ntiles + 1);
+  CG_CUDA(cudaMalloc((void**)&p->tile_row, nb));
+  CG_CUDA(cudaMalloc((void**)&p->tile_edge, nb));
+  CG_CUDA(cudaMalloc(&p->carry, nb));
+  CG_CUDA(cudaMalloc((void**)&p->carry_row, nb));
+  tile_partition_kernel<RowEndT><<<grid_for(p->ntiles + 1, 256), 256, 0, s>>>(
+      row_end, nrows, nedges, kTileItems, p->ntiles, p->tile_row, p->tile_edge);
+  CG_LAUNCH_CHECK();
+  return CG_OK;
+}
 
-// Set the shared table size (-1: the largest that fits ctas_per_sm blocks,
-// 0: none) and the blocks per SM; recomputes the per-segment table lengths.
-int configure_gather(GatherPlan* p, int tab_vertices, int ctas_per_sm, cudaStream_t s);
+inline void free_tile_plan(TilePlan* p) {
+  cudaFree(p->tile_row);
+  cudaFree(p->tile_edge);
+  cudaFree(p->carry);
+  cudaFree(p->carry_row);
+  *p = TilePlan();
+}
 
-void free_plan(GatherPlan* p);
-int64_t plan_bytes(const GatherPlan& p);
+inline int64_t tile_plan_bytes(const TilePlan& p) { return 16 * (p.ntiles + 1); }
 
+// Launch gather + fix-up.  row_end points at the first row's end.
 template <class Op, bool PROBE, typename RowEndT>
-int run_gather(const GatherPlan& p, const RowEndT* row_end, const int32_t* col,
-               const typename Op::T* x, int32_t nx, typename Op::T* out, cudaStream_t s);
+int run_tile_gather(const TilePlan& p, const RowEndT* row_end, const int32_t* col,
+               const typename Op::T* x, int32_t nx, typename Op::T* out, cudaStream_t s) {
+  if (p.ntiles == 0) return CG_OK;
+  gather_tile_kernel<Op, kTileThreads, kTileIPT, PROBE, RowEndT>
+      <<<(unsigned)p.ntiles, kTileThreads, 0, s>>>(
+          row_end, col, x, nx, p.tile_row, p.tile_edge, out,
+          reinterpret_cast<typename Op::T*>(p.carry), p.carry_row);
+  CG_LAUNCH_CHECK();
+  carry_fixup_kernel<Op><<<grid_for(p.ntiles, 256, 4), 256, 0, s>>>(
+      reinterpret_cast<const typename Op::T*>(p.carry), p.carry_row, p.ntiles, p.nrows, out);
+  CG_LAUNCH_CHECK();
+  return CG_OK;
+}
 
 }  // namespace cg

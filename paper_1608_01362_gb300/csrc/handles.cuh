@@ -3,13 +3,14 @@
 
 #include <vector>
 
-#include "gather.cuh"
+#include "seg_gather.cuh"
 
 // The segmented graph of Algorithm 2, flattened: all subgraphs concatenated
 // in segment order.  Subgraph row i (global row index over all segments)
-// holds edges [row_ptr[i], row_ptr[i+1]) of col and its destination is
-// idx_map[i].  blk[s*(nb+1) + b] is the first (global) row of segment s whose
-// destination is >= b*B; rows of segment s inside merge block b are
+// holds edges [row_ptr[i], row_ptr[i+1]) (stored flagged and padded in
+// plan.colf) and its destination is idx_map[i].  blk[s*(nb+1) + b] is the
+// first (global) row of segment s whose destination is >= b*B; rows of
+// segment s inside merge block b are
 // [blk[s*(nb+1)+b], blk[s*(nb+1)+b+1]).
 struct cg_segmented {
   int device = 0;
@@ -20,11 +21,10 @@ struct cg_segmented {
   int32_t nb = 0;
   int64_t rows = 0;
   std::vector<int64_t> bounds, row_base, edge_base;  // host copies, k+1 each
-  int32_t* row_ptr = nullptr;  // [rows+1]
-  int32_t* col = nullptr;      // [E]
+  int32_t* row_ptr = nullptr;  // [rows+1] (export only; the gather reads flagged edges)
   int32_t* idx_map = nullptr;  // [rows]
   int32_t* blk = nullptr;      // [k*(nb+1)]
-  cg::GatherPlan plan;
+  cg::SegPlan plan;            // flagged padded edges + chunk index + launch shape
   void* interm = nullptr;        // [rows] 4-byte values (intermBuf)
   double* partials = nullptr;    // [2*nb] per-block FP64 partial sums
   unsigned* counter = nullptr;   // last-block detection
@@ -41,7 +41,7 @@ struct cg_plain {
   int64_t E = 0;
   const int64_t* offsets = nullptr;  // caller-owned
   const int32_t* src = nullptr;      // caller-owned
-  cg::GatherPlan plan;
+  cg::TilePlan plan;
   float* acc = nullptr;          // [V] gathered sums
   double* partials = nullptr;    // [2*nb]
   unsigned* counter = nullptr;

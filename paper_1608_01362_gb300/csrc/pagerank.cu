@@ -296,11 +296,9 @@ int cg_seg_gather(const cg_segmented* g, int32_t op, const void* x, void* interm
   CG_ARG(g && x, "cg_seg_gather: null argument");
   if (!interm) interm = g->interm;
   if (op == CG_OP_SUM_F32)
-    return run_gather<SumF32, false, int32_t>(g->plan, g->row_ptr + 1, g->col,
-                                              (const float*)x, g->V, (float*)interm, stream);
+    return run_seg_gather<SumF32>(g->plan, (const float*)x, g->V, (float*)interm, stream);
   if (op == CG_OP_MIN_I32)
-    return run_gather<MinI32, false, int32_t>(g->plan, g->row_ptr + 1, g->col,
-                                              (const int32_t*)x, g->V, (int32_t*)interm, stream);
+    return run_seg_gather<MinI32>(g->plan, (const int32_t*)x, g->V, (int32_t*)interm, stream);
   set_error("cg_seg_gather: unknown op %d", op);
   return CG_ERR_INVALID_ARG;
 }
@@ -367,8 +365,7 @@ int pr_iterate(const cg_segmented* g, const float* inv, const float* rank_in,
   for (int t = 0; t < iterations; ++t) {
     IterBufs b = iter_bufs(t, iterations, rank_in, contrib_in, rank_out, contrib_out,
                            g->rank_tmp, g->contrib_tmp, D_io, g->dslot, resid);
-    CG_TRY((run_gather<SumF32, false, int32_t>(g->plan, g->row_ptr + 1, g->col, b.contrib_in,
-                                               g->V, (float*)g->interm, stream)));
+    CG_TRY(run_seg_gather<SumF32>(g->plan, b.contrib_in, g->V, (float*)g->interm, stream));
     CG_TRY(pr_merge_update(g, inv, b.rank_in, b.rank_out, b.contrib_out, damping, b.D_in,
                            b.D_out, b.resid, stream));
   }
@@ -391,8 +388,7 @@ int pr_plain_create(const int64_t* offsets, const int32_t* src, int32_t V, int64
   p->offsets = offsets;
   p->src = src;
   p->nb = (int32_t)ceil_div(V, 4096);
-  const std::vector<int64_t> rb = {0, (int64_t)V}, eb = {0, E};
-  int st = plan_gather<int64_t>(offsets + 1, V, E, 1, rb, eb, rb, 0, 8, &p->plan, stream);
+  int st = plan_tiles<int64_t>(offsets + 1, V, E, &p->plan, stream);
   cudaError_t e = cudaSuccess;
   if (st == CG_OK) e = cudaMalloc((void**)&p->acc, sizeof(float) * (size_t)V);
   if (e == cudaSuccess) e = cudaMalloc((void**)&p->partials, sizeof(double) * 2 * p->nb);
@@ -408,7 +404,7 @@ int pr_plain_create(const int64_t* offsets, const int32_t* src, int32_t V, int64
     pr_plain_destroy(p);
     return st;
   }
-  p->bytes = plan_bytes(p->plan) + 12 * (int64_t)V + 16 * (int64_t)p->nb + 36;
+  p->bytes = tile_plan_bytes(p->plan) + 12 * (int64_t)V + 16 * (int64_t)p->nb + 36;
   *out = p;
   return CG_OK;
 }
@@ -420,7 +416,7 @@ int pr_plain_destroy(cg_plain* p) {
   cudaGetDevice(&cur);
   if (cur != dev) cudaSetDevice(dev);
   cudaDeviceSynchronize();
-  free_plan(&p->plan);
+  free_tile_plan(&p->plan);
   cudaFree(p->acc);
   cudaFree(p->partials);
   cudaFree(p->counter);
@@ -446,10 +442,10 @@ int pr_iterate_plain(const cg_plain* p, const float* inv, const float* rank_in,
     IterBufs b = iter_bufs(t, iterations, rank_in, contrib_in, rank_out, contrib_out,
                            p->rank_tmp, p->contrib_tmp, D_io, p->dslot, resid);
     if (probe)
-      CG_TRY((run_gather<SumF32, true, int64_t>(p->plan, p->offsets + 1, p->src, b.contrib_in,
+      CG_TRY((run_tile_gather<SumF32, true, int64_t>(p->plan, p->offsets + 1, p->src, b.contrib_in,
                                                 p->V, p->acc, stream)));
     else
-      CG_TRY((run_gather<SumF32, false, int64_t>(p->plan, p->offsets + 1, p->src, b.contrib_in,
+      CG_TRY((run_tile_gather<SumF32, false, int64_t>(p->plan, p->offsets + 1, p->src, b.contrib_in,
                                                  p->V, p->acc, stream)));
     PrArgs a;
     a.inv = inv;

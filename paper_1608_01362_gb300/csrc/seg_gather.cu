@@ -1,0 +1,391 @@
+// Flagged-edge segment gather: plan construction and the kernel.
+#include <algorithm>
+
+#include "seg_gather.cuh"
+
+namespace cg {
+namespace {
+
+__device__ __forceinline__ int last_le(const int64_t* a, int n, int64_t v) {
+  // last index q in [0, n) with a[q] <= v (a ascending, a[0] <= v)
+  int lo = 0, hi = n;
+  while (lo < hi) {
+    const int mid = (lo + hi) >> 1;
+    if (a[mid] <= v) lo = mid + 1; else hi = mid;
+  }
+  return lo - 1;
+}
+
+// One warp per subgraph row: copy its sources into the padded layout and
+// flag the last one.
+__global__ void colf_fill_kernel(const int32_t* __restrict__ col, const int64_t* __restrict__ rp,
+                                 int64_t rows, const int64_t* __restrict__ row_base,
+                                 const int64_t* __restrict__ edge_base,
+                                 const int64_t* __restrict__ cstart, int k,
+                                 uint32_t* __restrict__ colf) {
+  const int lane = threadIdx.x & 31;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < rows; i += nw) {
+    const int s = last_le(row_base, k + 1, i);
+    const int64_t lo = rp[i], hi = rp[i + 1];
+    const int64_t shift = cstart[s] - edge_base[s];
+    for (int64_t e = lo + lane; e < hi; e += 32)
+      colf[e + shift] = (uint32_t)col[e] | (e == hi - 1 ? kRowEndFlag : 0u);
+  }
+}
+
+__global__ void export_col_kernel(const uint32_t* __restrict__ colf,
+                                  const int32_t* __restrict__ rp, int64_t rows,
+                                  const int64_t* __restrict__ row_base,
+                                  const int64_t* __restrict__ edge_base,
+                                  const int64_t* __restrict__ cstart, int k,
+                                  int32_t* __restrict__ col) {
+  const int lane = threadIdx.x & 31;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < rows; i += nw) {
+    const int s = last_le(row_base, k + 1, i);
+    const int64_t shift = cstart[s] - edge_base[s];
+    for (int64_t e = rp[i] + lane; e < rp[i + 1]; e += 32)
+      col[e] = (int32_t)(colf[e + shift] & ~kRowEndFlag);
+  }
+}
+
+// Subgraph row of each chunk's first edge.
+__global__ void first_row_kernel(const int64_t* __restrict__ rp,
+                                 const int64_t* __restrict__ row_base,
+                                 const int64_t* __restrict__ edge_base,
+                                 const int64_t* __restrict__ chunk_base, int k, int64_t nchunks,
+                                 int32_t* __restrict__ first_row) {
+  for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < nchunks;
+       c += (int64_t)gridDim.x * blockDim.x) {
+    const int s = last_le(chunk_base, k + 1, c);
+    const int64_t e = edge_base[s] + (c - chunk_base[s]) * kChunkEdges;
+    int64_t lo = row_base[s], hi = row_base[s + 1];  // last row with rp[row] <= e
+    while (lo < hi) {
+      const int64_t mid = (lo + hi) >> 1;
+      if (rp[mid] <= e) lo = mid + 1; else hi = mid;
+    }
+    first_row[c] = (int32_t)(lo - 1);
+  }
+}
+
+template <class Op, int THREADS>
+__global__ void __launch_bounds__(THREADS)
+seg_gather_kernel(const uint32_t* __restrict__ colf, const typename Op::T* __restrict__ x,
+                  int32_t nx, const int32_t* __restrict__ first_row,
+                  const int64_t* __restrict__ seg_cstart, const int32_t* __restrict__ seg_E,
+                  const int64_t* __restrict__ seg_chunk, const int32_t* __restrict__ seg_ctile,
+                  const int32_t* __restrict__ seg_lo, const int32_t* __restrict__ seg_tab, int k,
+                  int64_t n_ctiles, int tab_cap, typename Op::T* __restrict__ out,
+                  typename Op::T* __restrict__ carry, int32_t* __restrict__ carry_row) {
+  using T = typename Op::T;
+  constexpr int WARPS = THREADS / 32;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* tab = reinterpret_cast<T*>(smem_raw);
+  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  int cur = -1;
+  int32_t lo = 0, tn = 0, Es = 0;
+  int64_t cstart = 0, cbase = 0;
+  int32_t ctbase = 0;
+
+  for (int64_t ct = blockIdx.x; ct < n_ctiles; ct += gridDim.x) {
+    // segment of this block-group (the same for every thread of the block)
+    int a = 0, b = k + 1;
+    while (a < b) {
+      const int mid = (a + b) >> 1;
+      if (seg_ctile[mid] <= ct) a = mid + 1; else b = mid;
+    }
+    const int s = a - 1;
+    if (s != cur) {
+      __syncthreads();  // every warp is done reading the previous table
+      cur = s;
+      lo = seg_lo[s];
+      tn = seg_tab[s] < tab_cap ? seg_tab[s] : tab_cap;
+      Es = seg_E[s];
+      cstart = seg_cstart[s];
+      cbase = seg_chunk[s];
+      ctbase = seg_ctile[s];
+      for (int i = tid; i < tn; i += THREADS) tab[i] = x[lo + i];
+      __syncthreads();
+    }
+    const int64_t j = (ct - ctbase) * WARPS + w;  // chunk of this warp within the segment
+    const int64_t e0 = j * kChunkEdges;
+    if (e0 >= Es) continue;  // warp-uniform
+    const int n = (int)(Es - e0 < kChunkEdges ? Es - e0 : kChunkEdges);
+    const int64_t c = cbase + j;
+
+    // 1. this lane's 8 edges (two 16-byte streaming loads; colf is padded)
+    const uint4* p = reinterpret_cast<const uint4*>(colf + cstart + e0 + lane * 8);
+    const uint4 qa = __ldcs(p), qb = __ldcs(p + 1);
+    const uint32_t cf[8] = {qa.x, qa.y, qa.z, qa.w, qb.x, qb.y, qb.z, qb.w};
+    T v[8];
+    uint32_t fl = 0;
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const bool ok = lane * 8 + u < n;
+      const int32_t src = (int32_t)(cf[u] & ~kRowEndFlag);
+      if (ok && (cf[u] & kRowEndFlag)) fl |= 1u << u;
+      const uint32_t off = (uint32_t)(src - lo);
+      T val = Op::identity();
+      if (ok) {
+        if (off < (uint32_t)tn)
+          val = tab[off];
+        else if (src < nx)
+          val = __ldg(x + src);
+      }
+      v[u] = val;
+    }
+
+    // 2. rows ended before this lane (exclusive warp prefix of flag counts)
+    const int F = __popc(fl);
+    int incl = F;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += y;
+    }
+    const int32_t row0 = first_row[c] + (incl - F);
+
+    // 3. sequential fold; rows that start and end in this lane are final
+    T acc = Op::identity(), first_val = Op::identity();
+    int nf = 0;
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      acc = Op::op(acc, v[u]);
+      if (fl & (1u << u)) {
+        if (nf == 0)
+          first_val = acc;
+        else
+          out[row0 + nf] = acc;
+        ++nf;
+        acc = Op::identity();
+      }
+    }
+
+    // 4. segmented scan of the open-row parts; completes each lane's first row
+    T S = acc;
+    int h = F > 0;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const T y = __shfl_up_sync(0xffffffffu, S, o);
+      const int g = __shfl_up_sync(0xffffffffu, h, o);
+      if (lane >= o) {
+        if (!h) S = Op::op(y, S);
+        h |= g;
+      }
+    }
+    const T P = __shfl_up_sync(0xffffffffu, S, 1);
+    if (F > 0) out[row0] = lane > 0 ? Op::op(P, first_val) : first_val;
+
+    // 5. the row open at the chunk's end
+    const int total = __shfl_sync(0xffffffffu, incl, 31);
+    const uint32_t lf = __shfl_sync(0xffffffffu, fl, (n - 1) >> 3);
+    if (lane == 31) {
+      const bool closed = (lf >> ((n - 1) & 7)) & 1u;
+      carry[c] = closed ? Op::identity() : S;
+      carry_row[c] = closed ? -1 : first_row[c] + total;
+    }
+  }
+}
+
+}  // namespace
+
+int seg_table_capacity(int ctas) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+  int sm_smem = 0, reserved = 0, optin = 0;
+  cudaDeviceGetAttribute(&sm_smem, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+  cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev);
+  cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  if (ctas < 1) ctas = 1;
+  int64_t per = (int64_t)sm_smem / ctas - reserved;
+  if (per > optin) per = optin;
+  if (per <= 0) return 0;
+  return (int)((per / 4) & ~31LL);
+}
+
+int seg_plan_build(const int32_t* col, const int64_t* rp, int64_t rows, int64_t E, int k,
+                   const std::vector<int64_t>& row_base, const std::vector<int64_t>& edge_base,
+                   const std::vector<int64_t>& src_bounds, SegPlan* p, cudaStream_t s) {
+  p->k = k;
+  p->E = E;
+  p->rows = rows;
+  p->row_base = row_base;
+  p->edge_base = edge_base;
+  p->src_bounds = src_bounds;
+  p->h_cstart.assign(k + 1, 0);
+  p->h_chunk.assign(k + 1, 0);
+  for (int q = 0; q < k; ++q) {
+    const int64_t Eq = edge_base[q + 1] - edge_base[q];
+    p->h_cstart[q + 1] = p->h_cstart[q] + ((Eq + 7) & ~7LL);
+    p->h_chunk[q + 1] = p->h_chunk[q] + ceil_div(Eq, kChunkEdges);
+  }
+  p->nchunks = p->h_chunk[k];
+  p->colf_len = p->h_cstart[k] + kChunkEdges;  // chunks may read past their segment's end
+  CG_CUDA(cudaMalloc((void**)&p->colf, sizeof(uint32_t) * p->colf_len));
+  CG_CUDA(cudaMemsetAsync(p->colf, 0, sizeof(uint32_t) * p->colf_len, s));
+  const size_t kk = (size_t)(k > 0 ? k : 1);
+  CG_CUDA(cudaMalloc((void**)&p->seg_cstart, sizeof(int64_t) * kk));
+  CG_CUDA(cudaMalloc((void**)&p->seg_E, sizeof(int32_t) * kk));
+  CG_CUDA(cudaMalloc((void**)&p->seg_chunk, sizeof(int64_t) * kk));
+  CG_CUDA(cudaMalloc((void**)&p->seg_ctile, sizeof(int32_t) * (kk + 1)));
+  CG_CUDA(cudaMalloc((void**)&p->seg_lo, sizeof(int32_t) * kk));
+  CG_CUDA(cudaMalloc((void**)&p->seg_tab, sizeof(int32_t) * kk));
+  const size_t nc = (size_t)(p->nchunks > 0 ? p->nchunks : 1);
+  CG_CUDA(cudaMalloc((void**)&p->first_row, sizeof(int32_t) * nc));
+  CG_CUDA(cudaMalloc(&p->carry, sizeof(int32_t) * nc));
+  CG_CUDA(cudaMalloc((void**)&p->carry_row, sizeof(int32_t) * nc));
+
+  std::vector<int32_t> segE(kk, 0);
+  for (int q = 0; q < k; ++q) segE[q] = (int32_t)(edge_base[q + 1] - edge_base[q]);
+  CG_CUDA(cudaMemcpyAsync(p->seg_cstart, p->h_cstart.data(), sizeof(int64_t) * k,
+                          cudaMemcpyHostToDevice, s));
+  CG_CUDA(cudaMemcpyAsync(p->seg_E, segE.data(), sizeof(int32_t) * k, cudaMemcpyHostToDevice, s));
+  CG_CUDA(cudaMemcpyAsync(p->seg_chunk, p->h_chunk.data(), sizeof(int64_t) * k,
+                          cudaMemcpyHostToDevice, s));
+  int64_t* meta = nullptr;  // row_base, edge_base, cstart, chunk_base: 4 x (k+1)
+  CG_CUDA(cudaMallocAsync((void**)&meta, sizeof(int64_t) * 4 * (k + 1), s));
+  cudaError_t e = cudaMemcpyAsync(meta, row_base.data(), sizeof(int64_t) * (k + 1),
+                                  cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(meta + (k + 1), edge_base.data(), sizeof(int64_t) * (k + 1),
+                        cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(meta + 2 * (k + 1), p->h_cstart.data(), sizeof(int64_t) * (k + 1),
+                        cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(meta + 3 * (k + 1), p->h_chunk.data(), sizeof(int64_t) * (k + 1),
+                        cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess && rows > 0) {
+    colf_fill_kernel<<<grid_for(rows * 32, 256, 16), 256, 0, s>>>(
+        col, rp, rows, meta, meta + (k + 1), meta + 2 * (k + 1), k, p->colf);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess && p->nchunks > 0) {
+    first_row_kernel<<<grid_for(p->nchunks, 256), 256, 0, s>>>(
+        rp, meta, meta + (k + 1), meta + 3 * (k + 1), k, p->nchunks, p->first_row);
+    e = cudaGetLastError();
+  }
+  cudaFreeAsync(meta, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);  // host vectors above go out of scope
+  if (e != cudaSuccess) return cuda_fail(e, "seg_plan_build", __FILE__, __LINE__);
+  return seg_plan_configure(p, 1024, 1, -1, s);
+}
+
+int seg_plan_configure(SegPlan* p, int threads, int ctas_per_sm, int tab_vertices,
+                       cudaStream_t s) {
+  if (threads != 512 && threads != 1024) {
+    set_error("gather threads must be 512 or 1024 (got %d)", threads);
+    return CG_ERR_INVALID_ARG;
+  }
+  const int max_ctas = 2048 / threads;
+  if (ctas_per_sm < 1 || ctas_per_sm > max_ctas) {
+    set_error("ctas_per_sm must be in [1, %d] for %d threads", max_ctas, threads);
+    return CG_ERR_INVALID_ARG;
+  }
+  DeviceInfo di{};
+  CG_TRY(device_info(&di));
+  const int warps = threads / 32;
+  const int cap = seg_table_capacity(ctas_per_sm);
+  int tab = tab_vertices < 0 ? cap : std::min(tab_vertices, cap);
+  tab &= ~3;
+  const int k = p->k;
+  std::vector<int32_t> ctile(k + 1, 0), lo(k > 0 ? k : 1, 0), tn(k > 0 ? k : 1, 0);
+  for (int q = 0; q < k; ++q)
+    ctile[q + 1] = ctile[q] + (int32_t)ceil_div(p->h_chunk[q + 1] - p->h_chunk[q], warps);
+  p->n_ctiles = ctile[k];
+  p->grid = (int)std::max<int64_t>(1, std::min<int64_t>(p->n_ctiles, (int64_t)di.sm_count *
+                                                                         ctas_per_sm));
+  for (int q = 0; q < k; ++q) {
+    lo[q] = (int32_t)p->src_bounds[q];
+    const int64_t size = p->src_bounds[q + 1] - p->src_bounds[q];
+    const int64_t Eq = p->edge_base[q + 1] - p->edge_base[q];
+    int64_t t = std::min<int64_t>(tab, size);
+    // stage a table only when every block reads it at least ~t/4 times
+    if ((double)Eq < 0.25 * (double)p->grid * (double)t) t = 0;
+    tn[q] = (int32_t)t;
+  }
+  CG_CUDA(cudaMemcpyAsync(p->seg_ctile, ctile.data(), sizeof(int32_t) * (k + 1),
+                          cudaMemcpyHostToDevice, s));
+  if (k > 0) {
+    CG_CUDA(cudaMemcpyAsync(p->seg_lo, lo.data(), sizeof(int32_t) * k, cudaMemcpyHostToDevice, s));
+    CG_CUDA(cudaMemcpyAsync(p->seg_tab, tn.data(), sizeof(int32_t) * k, cudaMemcpyHostToDevice,
+                            s));
+  }
+  CG_CUDA(cudaStreamSynchronize(s));
+  p->threads = threads;
+  p->ctas_per_sm = ctas_per_sm;
+  p->tab_cap = tab;
+  return CG_OK;
+}
+
+void seg_plan_free(SegPlan* p) {
+  cudaFree(p->colf);
+  cudaFree(p->seg_cstart);
+  cudaFree(p->seg_E);
+  cudaFree(p->seg_chunk);
+  cudaFree(p->seg_ctile);
+  cudaFree(p->seg_lo);
+  cudaFree(p->seg_tab);
+  cudaFree(p->first_row);
+  cudaFree(p->carry);
+  cudaFree(p->carry_row);
+  *p = SegPlan();
+}
+
+int64_t seg_plan_bytes(const SegPlan& p) { return 4 * p.colf_len + 12 * p.nchunks + 40 * p.k; }
+
+int seg_plan_export_col(const SegPlan& p, const int32_t* rp, int32_t* col, cudaStream_t s) {
+  if (p.rows == 0) return CG_OK;
+  const int k = p.k;
+  int64_t* meta = nullptr;
+  CG_CUDA(cudaMallocAsync((void**)&meta, sizeof(int64_t) * 3 * (k + 1), s));
+  cudaError_t e = cudaMemcpyAsync(meta, p.row_base.data(), sizeof(int64_t) * (k + 1),
+                                  cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(meta + (k + 1), p.edge_base.data(), sizeof(int64_t) * (k + 1),
+                        cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(meta + 2 * (k + 1), p.h_cstart.data(), sizeof(int64_t) * (k + 1),
+                        cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) {
+    export_col_kernel<<<grid_for(p.rows * 32, 256, 16), 256, 0, s>>>(
+        p.colf, rp, p.rows, meta, meta + (k + 1), meta + 2 * (k + 1), k, col);
+    e = cudaGetLastError();
+  }
+  cudaFreeAsync(meta, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_fail(e, "seg_plan_export_col", __FILE__, __LINE__);
+  return CG_OK;
+}
+
+template <class Op>
+int run_seg_gather(const SegPlan& p, const typename Op::T* x, int32_t nx, typename Op::T* out,
+                   cudaStream_t s) {
+  if (p.nchunks == 0) return CG_OK;
+  const size_t smem = (size_t)p.tab_cap * 4;
+  const void* fn = p.threads == 1024 ? (const void*)seg_gather_kernel<Op, 1024>
+                                     : (const void*)seg_gather_kernel<Op, 512>;
+  if (smem > 48 * 1024)
+    CG_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  using T = typename Op::T;
+  if (p.threads == 1024)
+    seg_gather_kernel<Op, 1024><<<p.grid, 1024, smem, s>>>(
+        p.colf, x, nx, p.first_row, p.seg_cstart, p.seg_E, p.seg_chunk, p.seg_ctile, p.seg_lo,
+        p.seg_tab, p.k, p.n_ctiles, p.tab_cap, out, reinterpret_cast<T*>(p.carry), p.carry_row);
+  else
+    seg_gather_kernel<Op, 512><<<p.grid, 512, smem, s>>>(
+        p.colf, x, nx, p.first_row, p.seg_cstart, p.seg_E, p.seg_chunk, p.seg_ctile, p.seg_lo,
+        p.seg_tab, p.k, p.n_ctiles, p.tab_cap, out, reinterpret_cast<T*>(p.carry), p.carry_row);
+  CG_LAUNCH_CHECK();
+  carry_fixup_kernel<Op><<<grid_for(p.nchunks, 256, 4), 256, 0, s>>>(
+      reinterpret_cast<const T*>(p.carry), p.carry_row, p.nchunks, p.rows, out);
+  CG_LAUNCH_CHECK();
+  return CG_OK;
+}
+
+template int run_seg_gather<SumF32>(const SegPlan&, const float*, int32_t, float*, cudaStream_t);
+template int run_seg_gather<MinI32>(const SegPlan&, const int32_t*, int32_t, int32_t*,
+                                    cudaStream_t);
+
+}  // namespace cg

@@ -1,0 +1,81 @@
+// Segment processing (Algorithm 3) over the flattened segmented graph.
+//
+// Edge layout ("colf"): the subgraphs' source IDs, segment after segment,
+// each segment starting on an 8-entry (32-byte) boundary; bit 31 of an entry
+// marks the last edge of its subgraph row.  Every subgraph row has at least
+// one edge, so row i is the (i+1)-th flagged edge: the gather needs no row
+// pointers at all.
+//
+// Work unit: a warp owns a chunk of 256 consecutive edges of one segment;
+// lane l holds edges [8l, 8l+8) of it (two 16-byte streaming loads).  Lanes
+// fold their 8 values sequentially, emit every row that starts and ends
+// inside them, and a warp-wide segmented scan over the lanes' open-row parts
+// completes each lane's first row.  The row still open at the chunk's end
+// goes to carry[chunk], folded in afterwards in chunk order.  No shared
+// staging of edges and no block barriers between chunks.
+//
+// Source values come from a per-block shared-memory copy of the first
+// `tab` sources of the current segment (the whole segment when it fits:
+// the paper's cache-sized segment, sized to an SM's shared memory), and
+// through L1/L2 otherwise.  Blocks are persistent and take block-sized
+// groups of chunks round-robin, so the grid moves through the segments in
+// order; a block reloads its table when its segment changes.
+#pragma once
+
+#include <vector>
+
+#include "gather.cuh"
+
+namespace cg {
+
+constexpr uint32_t kRowEndFlag = 0x80000000u;
+constexpr int kChunkEdges = 256;  // 32 lanes x 8 edges
+
+struct SegPlan {
+  int k = 0;
+  int64_t E = 0, rows = 0, nchunks = 0;
+  uint32_t* colf = nullptr;        // [colf_len] flagged, padded sources
+  int64_t colf_len = 0;
+  int64_t* seg_cstart = nullptr;   // [k]   first colf entry of each segment
+  int32_t* seg_E = nullptr;        // [k]   edges of each segment
+  int64_t* seg_chunk = nullptr;    // [k]   first global chunk of each segment
+  int32_t* seg_ctile = nullptr;    // [k+1] first block-group of each segment
+  int32_t* seg_lo = nullptr;       // [k]   first source of each segment
+  int32_t* seg_tab = nullptr;      // [k]   table entries used for each segment
+  int32_t* first_row = nullptr;    // [nchunks] subgraph row of each chunk's first edge
+  void* carry = nullptr;           // [nchunks] 4-byte values
+  int32_t* carry_row = nullptr;    // [nchunks]
+  std::vector<int64_t> h_cstart, h_chunk, src_bounds, edge_base, row_base;
+  int threads = 1024;
+  int ctas_per_sm = 1;
+  int tab_cap = 0;
+  int64_t n_ctiles = 0;
+  int grid = 0;
+};
+
+// Largest shared table (entries, multiple of 32) for `ctas` blocks per SM.
+int seg_table_capacity(int ctas);
+
+// Build colf, the chunk index and the carry buffers from the unpadded
+// segmented CSR (col[E] int32 global sources, rp[rows+1] int64 row starts).
+// Synchronizes the stream.
+int seg_plan_build(const int32_t* col, const int64_t* rp, int64_t rows, int64_t E, int k,
+                   const std::vector<int64_t>& row_base, const std::vector<int64_t>& edge_base,
+                   const std::vector<int64_t>& src_bounds, SegPlan* p, cudaStream_t s);
+
+// Launch shape: threads per block (512 or 1024), blocks per SM, table size
+// (-1: the capacity; 0: none).  Synchronizes the stream.
+int seg_plan_configure(SegPlan* p, int threads, int ctas_per_sm, int tab_vertices,
+                       cudaStream_t s);
+
+void seg_plan_free(SegPlan* p);
+int64_t seg_plan_bytes(const SegPlan& p);
+
+// Recover the unpadded source array (flags cleared) for export.
+int seg_plan_export_col(const SegPlan& p, const int32_t* rp, int32_t* col, cudaStream_t s);
+
+template <class Op>
+int run_seg_gather(const SegPlan& p, const typename Op::T* x, int32_t nx, typename Op::T* out,
+                   cudaStream_t s);
+
+}  // namespace cg

@@ -361,11 +361,12 @@ int build_impl(const int64_t* offsets, const int32_t* src, int32_t V, int64_t E,
   }
 
   // D
-  CG_CUDA(cudaMalloc((void**)&g->col, sizeof(int32_t) * (size_t)(E > 0 ? E : 1)));
+  int32_t* col = nullptr;
+  CG_CUDA(tmp.get(&col, (size_t)(E > 0 ? E : 1)));
   if (E > 0) {
     const size_t smem = sizeof(int64_t) * kBuildWarps * k + sizeof(int32_t) * (k + 1);
     scatter_edges_kernel<<<grid_rows, kBuildThreads, smem, s>>>(offsets, src, V, d_bounds, k, pos,
-                                                                pseg, inv, rp, g->col);
+                                                                pseg, inv, rp, col);
     CG_LAUNCH_CHECK();
   }
 
@@ -383,8 +384,7 @@ int build_impl(const int64_t* offsets, const int32_t* src, int32_t V, int64_t E,
 
   // F
   CG_CUDA(cudaStreamSynchronize(s));  // edge_base copies have landed
-  CG_TRY(plan_gather<int32_t>(g->row_ptr + 1, npairs, E, k, g->row_base, g->edge_base, bounds,
-                              -1, 2, &g->plan, s));
+  CG_TRY(seg_plan_build(col, rp, npairs, E, k, g->row_base, g->edge_base, bounds, &g->plan, s));
   CG_CUDA(cudaMalloc(&g->interm, sizeof(float) * (size_t)(npairs > 0 ? npairs : 1)));
   CG_CUDA(cudaMalloc((void**)&g->partials, sizeof(double) * 2 * (size_t)g->nb));
   CG_CUDA(cudaMalloc((void**)&g->counter, sizeof(unsigned)));
@@ -394,17 +394,16 @@ int build_impl(const int64_t* offsets, const int32_t* src, int32_t V, int64_t E,
   CG_CUDA(cudaMalloc((void**)&g->rank_tmp, sizeof(float) * (size_t)V));
   CG_CUDA(cudaMalloc((void**)&g->contrib_tmp, sizeof(float) * (size_t)V));
   CG_CUDA(cudaStreamSynchronize(s));
-  g->bytes = 4 * (npairs + 1) + 4 * E + 4 * npairs + 4 * (int64_t)k * (g->nb + 1) +
-             plan_bytes(g->plan) + 4 * npairs + 16 * (int64_t)g->nb + 4 + 32 + 8 * (int64_t)V;
+  g->bytes = 4 * (npairs + 1) + 4 * npairs + 4 * (int64_t)k * (g->nb + 1) +
+             seg_plan_bytes(g->plan) + 4 * npairs + 16 * (int64_t)g->nb + 4 + 32 + 8 * (int64_t)V;
   return CG_OK;
 }
 
 void free_segmented(cg_segmented* g) {
   cudaFree(g->row_ptr);
-  cudaFree(g->col);
   cudaFree(g->idx_map);
   cudaFree(g->blk);
-  free_plan(&g->plan);
+  seg_plan_free(&g->plan);
   cudaFree(g->interm);
   cudaFree(g->partials);
   cudaFree(g->counter);
@@ -495,23 +494,21 @@ int cg_segmented_get_info(const cg_segmented* g, cg_segmented_info* info) {
   info->rows = g->rows;
   info->q = g->V ? (double)g->rows / (double)g->V : 0.0;
   info->device_bytes = g->bytes;
-  info->gather_tiles = g->plan.ntiles;
+  info->gather_tiles = g->plan.nchunks;
   info->table_vertices = g->plan.tab_cap;
   info->ctas_per_sm = g->plan.ctas_per_sm;
+  info->gather_threads = g->plan.threads;
   return CG_OK;
 }
 
-int pr_set_gather_config(cg_segmented* g, int32_t table_vertices, int32_t ctas_per_sm,
-                         cudaStream_t stream) {
+int pr_set_gather_config(cg_segmented* g, int32_t threads, int32_t ctas_per_sm,
+                         int32_t table_vertices, cudaStream_t stream) {
   CG_ARG(g != nullptr, "pr_set_gather_config: null handle");
-  CG_ARG(ctas_per_sm >= 1 && ctas_per_sm <= 32, "pr_set_gather_config: ctas_per_sm in [1, 32]");
   CG_ARG(table_vertices >= -1, "pr_set_gather_config: table_vertices must be >= -1");
-  return configure_gather(&g->plan, table_vertices, ctas_per_sm, stream);
+  return seg_plan_configure(&g->plan, threads, ctas_per_sm, table_vertices, stream);
 }
 
-int pr_gather_table_capacity(int32_t ctas_per_sm) {
-  return gather_table_capacity(ctas_per_sm);
-}
+int pr_gather_table_capacity(int32_t ctas_per_sm) { return seg_table_capacity(ctas_per_sm); }
 
 int pr_plan_bounds(const int32_t* dev_outdeg, int32_t V, int32_t smem_vertices,
                    double min_avg_degree, int32_t max_global_vertices, int32_t k_max,
@@ -520,7 +517,7 @@ int pr_plan_bounds(const int32_t* dev_outdeg, int32_t V, int32_t smem_vertices,
   CG_ARG(k_max >= 1 && k_max <= kMaxSegments, "pr_plan_bounds: k_max must be in [1, %d]",
          kMaxSegments);
   CG_ARG(max_global_vertices >= 1, "pr_plan_bounds: max_global_vertices must be >= 1");
-  if (smem_vertices < 0) smem_vertices = gather_table_capacity(2);
+  if (smem_vertices < 0) smem_vertices = seg_table_capacity(1);
   std::vector<int32_t> deg(V);
   CG_CUDA(cudaMemcpyAsync(deg.data(), dev_outdeg, sizeof(int32_t) * (size_t)V,
                           cudaMemcpyDeviceToHost, stream));
@@ -566,8 +563,7 @@ int cg_segmented_export(const cg_segmented* g, int64_t* h_bounds, int64_t* h_row
     to_i64_kernel<<<grid_for(g->rows + 1, 256), 256, 0, s>>>(g->row_ptr, g->rows + 1, d_row_ptr);
     CG_LAUNCH_CHECK();
   }
-  if (d_col && g->E > 0)
-    CG_CUDA(cudaMemcpyAsync(d_col, g->col, sizeof(int32_t) * g->E, cudaMemcpyDeviceToDevice, s));
+  if (d_col && g->E > 0) CG_TRY(seg_plan_export_col(g->plan, g->row_ptr, d_col, s));
   if (d_idx_map && g->rows > 0)
     CG_CUDA(cudaMemcpyAsync(d_idx_map, g->idx_map, sizeof(int32_t) * g->rows,
                             cudaMemcpyDeviceToDevice, s));

@@ -76,7 +76,7 @@ class _PageRankBase:
         return self.g.to_original(self.rank[1]), resid
 
 
-def plan_bounds(graph: Graph, ctas_per_sm: int = 2, min_avg_degree: float = 64.0,
+def plan_bounds(graph: Graph, ctas_per_sm: int = 1, min_avg_degree: float = 64.0,
                 max_global_vertices: int = 1 << 24):
     """Segment bounds for this GPU: shared-memory-sized segments over the hot
     (clustered) head, L2-sized segments over the cold rest."""
@@ -84,19 +84,23 @@ def plan_bounds(graph: Graph, ctas_per_sm: int = 2, min_avg_degree: float = 64.0
     return C.pr_plan_bounds(graph.outdeg, H, min_avg_degree, max_global_vertices)
 
 
+GATHER_SHAPES = ((1024, 1), (1024, 2), (512, 4))  # (threads, blocks per SM)
+
+
 class SegmentedPageRank(_PageRankBase):
     """PageRank through CSR segmenting (Algorithms 2-5)."""
 
     def __init__(self, graph: Graph, num_segments: int | None = None, merge_block: int = 4096,
-                 bounds=None, table_vertices: int = -1, ctas_per_sm: int = 2):
+                 bounds=None, threads: int = 1024, ctas_per_sm: int = 1,
+                 table_vertices: int = -1):
         super().__init__(graph)
         if bounds is not None:
             bounds = np.asarray(bounds, dtype=np.int64)
             num_segments = len(bounds) - 1
         self.seg = C.pr_build_segments(graph.offsets, graph.src, num_segments, bounds=bounds,
                                        merge_block=merge_block)
-        if (table_vertices, ctas_per_sm) != (-1, 2):
-            C.pr_set_gather_config(self.seg, table_vertices, ctas_per_sm)
+        if (threads, ctas_per_sm, table_vertices) != (1024, 1, -1):
+            C.pr_set_gather_config(self.seg, threads, ctas_per_sm, table_vertices)
 
     @property
     def info(self):
@@ -136,21 +140,25 @@ def time_iterations(pr, iterations: int = 3, damping: float = 0.85, reps: int = 
     return times[len(times) // 2]
 
 
-def default_candidates(uniform_k=(1, 2, 4, 8, 16), ctas=(2, 3, 4), min_deg=(16.0, 64.0, 256.0)):
+def default_candidates(uniform_k=(1, 4, 16), shapes=GATHER_SHAPES,
+                       min_deg=(16.0, 64.0, 256.0)):
     """Autotuner search space: the paper's uniform split into k segments, and
     the GPU plan (shared-memory segments over the hot head, L2 segments over
-    the rest) at several blocks-per-SM / staging thresholds."""
-    out = [{"kind": "uniform", "k": k, "ctas": c} for k in uniform_k for c in (2, 4)]
-    out += [{"kind": "plan", "ctas": c, "min_avg_degree": m} for c in ctas for m in min_deg]
+    the rest), each at several gather launch shapes / staging thresholds."""
+    out = [{"kind": "uniform", "k": k, "threads": t, "ctas": c}
+           for k in uniform_k for (t, c) in shapes]
+    out += [{"kind": "plan", "threads": t, "ctas": c, "min_avg_degree": m}
+            for (t, c) in shapes for m in min_deg]
     return out
 
 
 def _build(graph, cand, merge_block):
+    t, c = cand.get("threads", 1024), cand.get("ctas", 1)
     if cand["kind"] == "uniform":
-        return SegmentedPageRank(graph, cand["k"], merge_block=merge_block,
-                                 ctas_per_sm=cand["ctas"])
-    b = plan_bounds(graph, cand["ctas"], cand["min_avg_degree"])
-    return SegmentedPageRank(graph, bounds=b, merge_block=merge_block, ctas_per_sm=cand["ctas"])
+        return SegmentedPageRank(graph, cand["k"], merge_block=merge_block, threads=t,
+                                 ctas_per_sm=c)
+    b = plan_bounds(graph, c, cand["min_avg_degree"])
+    return SegmentedPageRank(graph, bounds=b, merge_block=merge_block, threads=t, ctas_per_sm=c)
 
 
 def autotune_segments(graph: Graph, candidates=None, merge_block: int = 4096,

@@ -294,19 +294,32 @@ def test_deterministic_repeat(C, torch_mod, rmat16):
 
 # ------------------------------------------------------------------ shared-table / planned segments
 
-@pytest.mark.parametrize("table,ctas", [(0, 1), (100, 2), (-1, 2), (-1, 3), (512, 4), (-1, 8)])
-def test_gather_table_configs(C, torch_mod, rmat16, rmat16_oracle, table, ctas):
-    """The shared-memory table (whole segment or its hot head) changes where
-    values are read from, not the result."""
+@pytest.mark.parametrize("threads,ctas,table", [(1024, 1, 0), (1024, 1, 100), (1024, 1, -1),
+                                               (1024, 2, -1), (512, 1, 5000), (512, 4, -1)])
+def test_gather_table_configs(C, torch_mod, rmat16, rmat16_oracle, threads, ctas, table):
+    """The shared-memory table (whole segment or its hot head) and the launch
+    shape change where values are read from, not the result."""
     from paper_1608_01362_gb300 import pipeline as P
     graph = P.Graph(rmat16.offsets, rmat16.src, cluster_mode=0)
     for k in (1, 3, 40):
-        pr = P.SegmentedPageRank(graph, k, table_vertices=table, ctas_per_sm=ctas)
+        pr = P.SegmentedPageRank(graph, k, threads=threads, ctas_per_sm=ctas,
+                                 table_vertices=table)
         info = pr.info
-        assert info["ctas_per_sm"] == ctas
-        assert info["table_vertices"] == (0 if table == 0 else info["table_vertices"])
+        assert info["ctas_per_sm"] == ctas and info["gather_threads"] == threads
+        if table >= 0:
+            assert info["table_vertices"] == table
         rank, resid = pr.run(20)
-        assert rel_l1(rank.cpu().numpy(), rmat16_oracle[0]) <= TOL_L1, (table, ctas, k)
+        assert rel_l1(rank.cpu().numpy(), rmat16_oracle[0]) <= TOL_L1, (threads, ctas, table, k)
+
+
+def test_gather_config_rejects_bad_shape(C, torch_mod, rmat16):
+    from paper_1608_01362_gb300 import pipeline as P
+    graph = P.Graph(rmat16.offsets, rmat16.src, cluster_mode=0)
+    pr = P.SegmentedPageRank(graph, 2)
+    with pytest.raises(C.CagraError, match="threads"):
+        C.pr_set_gather_config(pr.seg, 256, 1, -1)
+    with pytest.raises(C.CagraError, match="ctas_per_sm"):
+        C.pr_set_gather_config(pr.seg, 1024, 3, -1)
 
 
 def test_planned_bounds(C, torch_mod, rmat16, rmat16_oracle):
@@ -325,6 +338,7 @@ def test_planned_bounds(C, torch_mod, rmat16, rmat16_oracle):
     if b[m] + 2048 <= graph.V:
         assert od[b[m]:b[m] + 2048].sum() < 8 * 2048
     pr = P.SegmentedPageRank(graph, bounds=b, table_vertices=2048, ctas_per_sm=2)
+    assert pr.info["table_vertices"] == 2048
     rank, _ = pr.run(20)
     assert rel_l1(rank.cpu().numpy(), rmat16_oracle[0]) <= TOL_L1
     # segment build on planned bounds is still bit-exact
@@ -335,7 +349,7 @@ def test_planned_bounds(C, torch_mod, rmat16, rmat16_oracle):
 def test_autotuner_returns_valid_choice(C, torch_mod, rmat16):
     from paper_1608_01362_gb300 import pipeline as P
     graph = P.Graph(rmat16.offsets, rmat16.src, cluster_mode=0)
-    cands = P.default_candidates(uniform_k=(1, 4), ctas=(2,), min_deg=(16.0,))
+    cands = P.default_candidates(uniform_k=(1, 4), shapes=((1024, 1), (512, 2)), min_deg=(16.0,))
     best, results = P.autotune_segments(graph, cands, iterations=2, reps=1)
     assert best in cands and len(results) == len(cands)
     assert all(r["s_per_iter"] > 0 for r in results)
