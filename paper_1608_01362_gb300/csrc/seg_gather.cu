@@ -70,7 +70,7 @@ __global__ void first_row_kernel(const int64_t* __restrict__ rp,
 }
 
 template <class Op, int THREADS>
-__global__ void __launch_bounds__(THREADS)
+__global__ void __launch_bounds__(THREADS, 2048 / THREADS)
 seg_gather_kernel(const uint32_t* __restrict__ colf, const typename Op::T* __restrict__ x,
                   int32_t nx, const int32_t* __restrict__ first_row,
                   const int64_t* __restrict__ seg_cstart, const int32_t* __restrict__ seg_E,
@@ -84,11 +84,10 @@ seg_gather_kernel(const uint32_t* __restrict__ colf, const typename Op::T* __res
   T* tab = reinterpret_cast<T*>(smem_raw);
   const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
   int cur = -1;
-  int32_t lo = 0, tn = 0, Es = 0;
-  int64_t cstart = 0, cbase = 0;
-  int32_t ctbase = 0;
+  // per-segment state in 32 bits (colf entries and chunks stay below 2^31)
+  int32_t lo = 0, tn = 0, Es = 0, cstart = 0, cbase = 0, ctbase = 0;
 
-  for (int64_t ct = blockIdx.x; ct < n_ctiles; ct += gridDim.x) {
+  for (int32_t ct = blockIdx.x; ct < (int32_t)n_ctiles; ct += gridDim.x) {
     // segment of this block-group (the same for every thread of the block)
     int a = 0, b = k + 1;
     while (a < b) {
@@ -102,17 +101,18 @@ seg_gather_kernel(const uint32_t* __restrict__ colf, const typename Op::T* __res
       lo = seg_lo[s];
       tn = seg_tab[s] < tab_cap ? seg_tab[s] : tab_cap;
       Es = seg_E[s];
-      cstart = seg_cstart[s];
-      cbase = seg_chunk[s];
+      cstart = (int32_t)seg_cstart[s];
+      cbase = (int32_t)seg_chunk[s];
       ctbase = seg_ctile[s];
       for (int i = tid; i < tn; i += THREADS) tab[i] = x[lo + i];
       __syncthreads();
     }
-    const int64_t j = (ct - ctbase) * WARPS + w;  // chunk of this warp within the segment
-    const int64_t e0 = j * kChunkEdges;
+    const int32_t j = (ct - ctbase) * WARPS + w;  // chunk of this warp within the segment
+    const int32_t e0 = j * kChunkEdges;
     if (e0 >= Es) continue;  // warp-uniform
-    const int n = (int)(Es - e0 < kChunkEdges ? Es - e0 : kChunkEdges);
-    const int64_t c = cbase + j;
+    const int n = Es - e0 < kChunkEdges ? Es - e0 : kChunkEdges;
+    const int32_t c = cbase + j;
+    const int32_t frow = first_row[c];
 
     // 1. this lane's 8 edges (two 16-byte streaming loads; colf is padded)
     const uint4* p = reinterpret_cast<const uint4*>(colf + cstart + e0 + lane * 8);
@@ -144,7 +144,7 @@ seg_gather_kernel(const uint32_t* __restrict__ colf, const typename Op::T* __res
       const int y = __shfl_up_sync(0xffffffffu, incl, o);
       if (lane >= o) incl += y;
     }
-    const int32_t row0 = first_row[c] + (incl - F);
+    const int32_t row0 = frow + (incl - F);
 
     // 3. sequential fold; rows that start and end in this lane are final
     T acc = Op::identity(), first_val = Op::identity();
@@ -183,7 +183,7 @@ seg_gather_kernel(const uint32_t* __restrict__ colf, const typename Op::T* __res
     if (lane == 31) {
       const bool closed = (lf >> ((n - 1) & 7)) & 1u;
       carry[c] = closed ? Op::identity() : S;
-      carry_row[c] = closed ? -1 : first_row[c] + total;
+      carry_row[c] = closed ? -1 : frow + total;
     }
   }
 }
@@ -222,6 +222,10 @@ int seg_plan_build(const int32_t* col, const int64_t* rp, int64_t rows, int64_t 
   }
   p->nchunks = p->h_chunk[k];
   p->colf_len = p->h_cstart[k] + kChunkEdges;  // chunks may read past their segment's end
+  if (p->colf_len >= 0x7FFFFFFFLL) {
+    set_error("segmented gather: padded edge array exceeds 2^31 entries");
+    return CG_ERR_UNSUPPORTED;
+  }
   CG_CUDA(cudaMalloc((void**)&p->colf, sizeof(uint32_t) * p->colf_len));
   CG_CUDA(cudaMemsetAsync(p->colf, 0, sizeof(uint32_t) * p->colf_len, s));
   const size_t kk = (size_t)(k > 0 ? k : 1);

@@ -140,25 +140,28 @@ def time_iterations(pr, iterations: int = 3, damping: float = 0.85, reps: int = 
     return times[len(times) // 2]
 
 
-def default_candidates(uniform_k=(1, 4, 16), shapes=GATHER_SHAPES,
-                       min_deg=(16.0, 64.0, 256.0)):
+def default_candidates(uniform_k=(1, 4), shapes=GATHER_SHAPES, min_deg=(64.0, 256.0, 1024.0),
+                       tables=(-1, 8192, 0)):
     """Autotuner search space: the paper's uniform split into k segments, and
     the GPU plan (shared-memory segments over the hot head, L2 segments over
-    the rest), each at several gather launch shapes / staging thresholds."""
-    out = [{"kind": "uniform", "k": k, "threads": t, "ctas": c}
-           for k in uniform_k for (t, c) in shapes]
-    out += [{"kind": "plan", "threads": t, "ctas": c, "min_avg_degree": m}
+    the rest), at several gather launch shapes, shared-table sizes and
+    staging thresholds.  A smaller table leaves more of the SM's on-chip
+    memory to the L1 cache, which serves the reads the table does not."""
+    out = [{"kind": "uniform", "k": k, "threads": 1024, "ctas": 2, "table": tb}
+           for k in uniform_k for tb in tables]
+    out += [{"kind": "plan", "threads": t, "ctas": c, "min_avg_degree": m, "table": -1}
             for (t, c) in shapes for m in min_deg]
     return out
 
 
 def _build(graph, cand, merge_block):
-    t, c = cand.get("threads", 1024), cand.get("ctas", 1)
+    t, c, tb = cand.get("threads", 1024), cand.get("ctas", 1), cand.get("table", -1)
     if cand["kind"] == "uniform":
         return SegmentedPageRank(graph, cand["k"], merge_block=merge_block, threads=t,
-                                 ctas_per_sm=c)
+                                 ctas_per_sm=c, table_vertices=tb)
     b = plan_bounds(graph, c, cand["min_avg_degree"])
-    return SegmentedPageRank(graph, bounds=b, merge_block=merge_block, threads=t, ctas_per_sm=c)
+    return SegmentedPageRank(graph, bounds=b, merge_block=merge_block, threads=t, ctas_per_sm=c,
+                             table_vertices=tb)
 
 
 def autotune_segments(graph: Graph, candidates=None, merge_block: int = 4096,

@@ -349,7 +349,8 @@ def test_planned_bounds(C, torch_mod, rmat16, rmat16_oracle):
 def test_autotuner_returns_valid_choice(C, torch_mod, rmat16):
     from paper_1608_01362_gb300 import pipeline as P
     graph = P.Graph(rmat16.offsets, rmat16.src, cluster_mode=0)
-    cands = P.default_candidates(uniform_k=(1, 4), shapes=((1024, 1), (512, 2)), min_deg=(16.0,))
+    cands = P.default_candidates(uniform_k=(1, 4), shapes=((1024, 1), (512, 2)), min_deg=(16.0,),
+                                 tables=(-1, 0))
     best, results = P.autotune_segments(graph, cands, iterations=2, reps=1)
     assert best in cands and len(results) == len(cands)
     assert all(r["s_per_iter"] > 0 for r in results)
