@@ -184,7 +184,10 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--scale", type=int, default=25)
-    ap.add_argument("--k", type=int, default=0, help="segments (0: autotune)")
+    ap.add_argument("--k", type=int, default=0, help="uniform segments (0: autotune)")
+    ap.add_argument("--threads", type=int, default=1024, help="gather threads (with --k)")
+    ap.add_argument("--ctas", type=int, default=2, help="gather blocks per SM (with --k)")
+    ap.add_argument("--table", type=int, default=0, help="shared table entries (with --k)")
     ap.add_argument("--merge-block", type=int, default=4096)
     ap.add_argument("--sweep", action="store_true", help="k = 1..64 sweep table")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -217,7 +220,9 @@ def main():
     cluster_s = time.time() - t0
 
     if args.k:
-        best, table = {"kind": "uniform", "k": args.k, "ctas": 2}, []
+        best = {"kind": "uniform", "k": args.k, "threads": args.threads, "ctas": args.ctas,
+                "table": args.table}
+        table = []
     else:
         uk = (1, 2, 4, 8, 16, 32, 64) if args.sweep else (1, 4, 16)
         best, table = P.autotune_segments(graph, P.default_candidates(uniform_k=uk),

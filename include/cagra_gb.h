@@ -120,9 +120,10 @@ typedef struct {
   double q;              /* expansion factor rows / V (Section III-D) */
   int64_t device_bytes;  /* device memory held by the handle */
   int64_t gather_tiles;  /* 256-edge chunks of one segment-processing pass */
-  int32_t table_vertices; /* shared-memory table entries per block */
-  int32_t ctas_per_sm;   /* gather blocks per SM */
-  int32_t gather_threads; /* threads per gather block */
+  int32_t table_vertices; /* shared-memory table entries per staged block */
+  int32_t ctas_per_sm;   /* staged-gather blocks per SM */
+  int32_t gather_threads; /* threads per staged-gather block */
+  int32_t staged_segments; /* leading segments served from shared memory */
 } cg_segmented_info;
 
 /*
@@ -166,13 +167,15 @@ int pr_plan_bounds(const int32_t *dev_outdeg, int32_t V, int32_t smem_vertices,
                    cudaStream_t stream);
 
 /*
- * Launch shape of the segment-processing gather of `seg`: `threads` (512 or
- * 1024) per block, `ctas_per_sm` persistent blocks per SM (at most
- * 2048/threads); each block keeps the first `table_vertices` source values of
- * its current segment in shared memory (-1: as many as fit; 0: none) when
- * the segment has enough edges to repay loading them.  Results do not depend
- * on it.  Default after pr_build_segments: 1024 threads, 1 block/SM, -1.
- * Synchronizes the stream.
+ * Launch shape of the segment-processing gather of `seg`.  The leading
+ * segments of at most `table_vertices` sources (-1: as many as fit in shared
+ * memory at `ctas_per_sm` blocks of `threads` threads per SM; 0: none) that
+ * carry at least 4 edges per source are "staged": a block copies the
+ * segment's source values into shared memory and serves every read of the
+ * segment from there.  The other segments are read through L1/L2 by a
+ * second launch (1024 threads, 2 blocks per SM, no shared memory).  threads:
+ * 512 or 1024; ctas_per_sm <= 2048/threads.  Results do not depend on it.
+ * Default after pr_build_segments: 1024, 1, -1.  Synchronizes the stream.
  */
 int pr_set_gather_config(cg_segmented *seg, int32_t threads, int32_t ctas_per_sm,
                          int32_t table_vertices, cudaStream_t stream);

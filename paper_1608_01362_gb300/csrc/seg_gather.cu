@@ -76,7 +76,7 @@ seg_gather_kernel(const uint32_t* __restrict__ colf, const typename Op::T* __res
                   const int64_t* __restrict__ seg_cstart, const int32_t* __restrict__ seg_E,
                   const int64_t* __restrict__ seg_chunk, const int32_t* __restrict__ seg_ctile,
                   const int32_t* __restrict__ seg_lo, const int32_t* __restrict__ seg_tab, int k,
-                  int64_t n_ctiles, int tab_cap, typename Op::T* __restrict__ out,
+                  int32_t ct_begin, int32_t ct_end, int tab_cap, typename Op::T* __restrict__ out,
                   typename Op::T* __restrict__ carry, int32_t* __restrict__ carry_row) {
   using T = typename Op::T;
   constexpr int WARPS = THREADS / 32;
@@ -87,7 +87,12 @@ seg_gather_kernel(const uint32_t* __restrict__ colf, const typename Op::T* __res
   // per-segment state in 32 bits (colf entries and chunks stay below 2^31)
   int32_t lo = 0, tn = 0, Es = 0, cstart = 0, cbase = 0, ctbase = 0;
 
-  for (int32_t ct = blockIdx.x; ct < (int32_t)n_ctiles; ct += gridDim.x) {
+  // this block's contiguous share of the block-groups [ct_begin, ct_end): a
+  // block meets at most a few segments, so it stages at most a few tables
+  const int32_t per = (ct_end - ct_begin + (int32_t)gridDim.x - 1) / (int32_t)gridDim.x;
+  const int32_t my_lo = ct_begin + (int32_t)blockIdx.x * per;
+  const int32_t my_hi = my_lo + per < ct_end ? my_lo + per : ct_end;
+  for (int32_t ct = my_lo; ct < my_hi; ++ct) {
     // segment of this block-group (the same for every thread of the block)
     int a = 0, b = k + 1;
     while (a < b) {
@@ -289,25 +294,30 @@ int seg_plan_configure(SegPlan* p, int threads, int ctas_per_sm, int tab_vertice
   }
   DeviceInfo di{};
   CG_TRY(device_info(&di));
-  const int warps = threads / 32;
   const int cap = seg_table_capacity(ctas_per_sm);
   int tab = tab_vertices < 0 ? cap : std::min(tab_vertices, cap);
   tab &= ~3;
   const int k = p->k;
+  const int64_t grid_a = (int64_t)di.sm_count * ctas_per_sm;
+  // staged prefix: leading segments that fit the table and carry enough edges
+  // for every block that stages them to read each entry a few times on average
+  int m = 0;
+  int64_t tabmax = 0;
+  while (m < k && tab > 0) {
+    const int64_t size = p->src_bounds[m + 1] - p->src_bounds[m];
+    const int64_t Eq = p->edge_base[m + 1] - p->edge_base[m];
+    if (size > tab || (double)Eq < 4.0 * (double)size) break;
+    tabmax = std::max(tabmax, size);
+    ++m;
+  }
+  const int warps_a = threads / 32, warps_b = 1024 / 32;
   std::vector<int32_t> ctile(k + 1, 0), lo(k > 0 ? k : 1, 0), tn(k > 0 ? k : 1, 0);
   for (int q = 0; q < k; ++q)
-    ctile[q + 1] = ctile[q] + (int32_t)ceil_div(p->h_chunk[q + 1] - p->h_chunk[q], warps);
-  p->n_ctiles = ctile[k];
-  p->grid = (int)std::max<int64_t>(1, std::min<int64_t>(p->n_ctiles, (int64_t)di.sm_count *
-                                                                         ctas_per_sm));
+    ctile[q + 1] = ctile[q] + (int32_t)ceil_div(p->h_chunk[q + 1] - p->h_chunk[q],
+                                                q < m ? warps_a : warps_b);
   for (int q = 0; q < k; ++q) {
     lo[q] = (int32_t)p->src_bounds[q];
-    const int64_t size = p->src_bounds[q + 1] - p->src_bounds[q];
-    const int64_t Eq = p->edge_base[q + 1] - p->edge_base[q];
-    int64_t t = std::min<int64_t>(tab, size);
-    // stage a table only when every block reads it at least ~t/4 times
-    if ((double)Eq < 0.25 * (double)p->grid * (double)t) t = 0;
-    tn[q] = (int32_t)t;
+    tn[q] = q < m ? (int32_t)(p->src_bounds[q + 1] - p->src_bounds[q]) : 0;
   }
   CG_CUDA(cudaMemcpyAsync(p->seg_ctile, ctile.data(), sizeof(int32_t) * (k + 1),
                           cudaMemcpyHostToDevice, s));
@@ -319,7 +329,14 @@ int seg_plan_configure(SegPlan* p, int threads, int ctas_per_sm, int tab_vertice
   CG_CUDA(cudaStreamSynchronize(s));
   p->threads = threads;
   p->ctas_per_sm = ctas_per_sm;
-  p->tab_cap = tab;
+  p->tab_cap = (int)((tabmax + 3) & ~3LL);
+  p->m = m;
+  p->ct_split = ctile[m];
+  p->n_ctiles = ctile[k];
+  p->grid = (int)std::max<int64_t>(1, std::min<int64_t>(p->ct_split, grid_a));
+  p->grid_l2 = (int)std::max<int64_t>(
+      1, std::min<int64_t>(p->n_ctiles - p->ct_split, (int64_t)di.sm_count * 2));
+  p->table_request = tab;
   return CG_OK;
 }
 
@@ -363,25 +380,39 @@ int seg_plan_export_col(const SegPlan& p, const int32_t* rp, int32_t* col, cudaS
   return CG_OK;
 }
 
+template <class Op, int THREADS>
+static int launch_seg_gather(const SegPlan& p, const typename Op::T* x, int32_t nx,
+                             typename Op::T* out, int32_t ct_begin, int32_t ct_end, int grid,
+                             int tab_cap, cudaStream_t s) {
+  if (ct_end <= ct_begin) return CG_OK;
+  using T = typename Op::T;
+  const size_t smem = (size_t)tab_cap * sizeof(T);
+  auto fn = seg_gather_kernel<Op, THREADS>;
+  if (smem > 48 * 1024)
+    CG_CUDA(cudaFuncSetAttribute((const void*)fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)smem));
+  fn<<<grid, THREADS, smem, s>>>(p.colf, x, nx, p.first_row, p.seg_cstart, p.seg_E, p.seg_chunk,
+                                 p.seg_ctile, p.seg_lo, p.seg_tab, p.k, ct_begin, ct_end, tab_cap,
+                                 out, reinterpret_cast<T*>(p.carry), p.carry_row);
+  CG_LAUNCH_CHECK();
+  return CG_OK;
+}
+
 template <class Op>
 int run_seg_gather(const SegPlan& p, const typename Op::T* x, int32_t nx, typename Op::T* out,
                    cudaStream_t s) {
   if (p.nchunks == 0) return CG_OK;
-  const size_t smem = (size_t)p.tab_cap * 4;
-  const void* fn = p.threads == 1024 ? (const void*)seg_gather_kernel<Op, 1024>
-                                     : (const void*)seg_gather_kernel<Op, 512>;
-  if (smem > 48 * 1024)
-    CG_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   using T = typename Op::T;
-  if (p.threads == 1024)
-    seg_gather_kernel<Op, 1024><<<p.grid, 1024, smem, s>>>(
-        p.colf, x, nx, p.first_row, p.seg_cstart, p.seg_E, p.seg_chunk, p.seg_ctile, p.seg_lo,
-        p.seg_tab, p.k, p.n_ctiles, p.tab_cap, out, reinterpret_cast<T*>(p.carry), p.carry_row);
-  else
-    seg_gather_kernel<Op, 512><<<p.grid, 512, smem, s>>>(
-        p.colf, x, nx, p.first_row, p.seg_cstart, p.seg_E, p.seg_chunk, p.seg_ctile, p.seg_lo,
-        p.seg_tab, p.k, p.n_ctiles, p.tab_cap, out, reinterpret_cast<T*>(p.carry), p.carry_row);
-  CG_LAUNCH_CHECK();
+  // staged segments [0, m): table in shared memory, the launch shape chosen
+  if (p.m > 0) {
+    if (p.threads == 1024)
+      CG_TRY((launch_seg_gather<Op, 1024>(p, x, nx, out, 0, p.ct_split, p.grid, p.tab_cap, s)));
+    else
+      CG_TRY((launch_seg_gather<Op, 512>(p, x, nx, out, 0, p.ct_split, p.grid, p.tab_cap, s)));
+  }
+  // the rest through L1/L2: no shared memory, so the whole on-chip store is L1
+  CG_TRY((launch_seg_gather<Op, 1024>(p, x, nx, out, p.ct_split, (int32_t)p.n_ctiles, p.grid_l2,
+                                      0, s)));
   carry_fixup_kernel<Op><<<grid_for(p.nchunks, 256, 4), 256, 0, s>>>(
       reinterpret_cast<const T*>(p.carry), p.carry_row, p.nchunks, p.rows, out);
   CG_LAUNCH_CHECK();

@@ -14,12 +14,15 @@
 // goes to carry[chunk], folded in afterwards in chunk order.  No shared
 // staging of edges and no block barriers between chunks.
 //
-// Source values come from a per-block shared-memory copy of the first
-// `tab` sources of the current segment (the whole segment when it fits:
-// the paper's cache-sized segment, sized to an SM's shared memory), and
-// through L1/L2 otherwise.  Blocks are persistent and take block-sized
-// groups of chunks round-robin, so the grid moves through the segments in
-// order; a block reloads its table when its segment changes.
+// Two launches per pass.  The leading segments that fit an SM's shared
+// memory (after clustering, the hot head: the paper's cache-sized segment,
+// sized here to on-chip shared memory) are "staged": each block copies its
+// current segment's source values into shared memory and every read of the
+// segment is served from there.  The remaining segments are read through
+// L1/L2 by a second launch that uses no shared memory, leaving the whole
+// on-chip store to the L1 cache.  In both, a block owns a contiguous run of
+// block-sized groups of chunks (so it meets at most a few segments and
+// stages at most a few tables), in segment order.
 #pragma once
 
 #include <vector>
@@ -46,11 +49,15 @@ struct SegPlan {
   void* carry = nullptr;           // [nchunks] 4-byte values
   int32_t* carry_row = nullptr;    // [nchunks]
   std::vector<int64_t> h_cstart, h_chunk, src_bounds, edge_base, row_base;
-  int threads = 1024;
+  int threads = 1024;       // staged-segment launch shape
   int ctas_per_sm = 1;
-  int tab_cap = 0;
+  int tab_cap = 0;          // table entries of the staged launch (its largest segment)
+  int table_request = 0;    // the capacity asked for
+  int m = 0;                // segments [0, m) are staged in shared memory
+  int32_t ct_split = 0;     // first block-group of the unstaged segments
   int64_t n_ctiles = 0;
-  int grid = 0;
+  int grid = 0;             // staged launch blocks
+  int grid_l2 = 0;          // unstaged launch blocks (1024 threads, 2 per SM)
 };
 
 // Largest shared table (entries, multiple of 32) for `ctas` blocks per SM.

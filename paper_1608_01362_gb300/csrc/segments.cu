@@ -496,6 +496,7 @@ int cg_segmented_get_info(const cg_segmented* g, cg_segmented_info* info) {
   info->device_bytes = g->bytes;
   info->gather_tiles = g->plan.nchunks;
   info->table_vertices = g->plan.tab_cap;
+  info->staged_segments = g->plan.m;
   info->ctas_per_sm = g->plan.ctas_per_sm;
   info->gather_threads = g->plan.threads;
   return CG_OK;
