@@ -188,6 +188,8 @@ def main():
     ap.add_argument("--threads", type=int, default=1024, help="gather threads (with --k)")
     ap.add_argument("--ctas", type=int, default=2, help="gather blocks per SM (with --k)")
     ap.add_argument("--table", type=int, default=0, help="shared table entries (with --k)")
+    ap.add_argument("--plan", type=float, default=0.0,
+                    help="use planned bounds with this min_avg_degree (skips the autotuner)")
     ap.add_argument("--merge-block", type=int, default=4096)
     ap.add_argument("--sweep", action="store_true", help="k = 1..64 sweep table")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -219,7 +221,11 @@ def main():
     torch.cuda.synchronize()
     cluster_s = time.time() - t0
 
-    if args.k:
+    if args.plan:
+        best = {"kind": "plan", "threads": args.threads, "ctas": args.ctas,
+                "min_avg_degree": args.plan, "table": -1}
+        table = []
+    elif args.k:
         best = {"kind": "uniform", "k": args.k, "threads": args.threads, "ctas": args.ctas,
                 "table": args.table}
         table = []

@@ -76,7 +76,8 @@ seg_gather_kernel(const uint32_t* __restrict__ colf, const typename Op::T* __res
                   const int64_t* __restrict__ seg_cstart, const int32_t* __restrict__ seg_E,
                   const int64_t* __restrict__ seg_chunk, const int32_t* __restrict__ seg_ctile,
                   const int32_t* __restrict__ seg_lo, const int32_t* __restrict__ seg_tab, int k,
-                  int32_t ct_begin, int32_t ct_end, int tab_cap, typename Op::T* __restrict__ out,
+                  int32_t ct_begin, int32_t ct_end, int contiguous, int tab_cap,
+                  typename Op::T* __restrict__ out,
                   typename Op::T* __restrict__ carry, int32_t* __restrict__ carry_row) {
   using T = typename Op::T;
   constexpr int WARPS = THREADS / 32;
@@ -87,12 +88,16 @@ seg_gather_kernel(const uint32_t* __restrict__ colf, const typename Op::T* __res
   // per-segment state in 32 bits (colf entries and chunks stay below 2^31)
   int32_t lo = 0, tn = 0, Es = 0, cstart = 0, cbase = 0, ctbase = 0;
 
-  // this block's contiguous share of the block-groups [ct_begin, ct_end): a
-  // block meets at most a few segments, so it stages at most a few tables
-  const int32_t per = (ct_end - ct_begin + (int32_t)gridDim.x - 1) / (int32_t)gridDim.x;
+  // Block-groups [ct_begin, ct_end): with `contiguous`, each block takes one
+  // contiguous share (it meets at most a few segments, so it stages at most
+  // a few tables); otherwise round-robin (the grid sweeps the groups in
+  // order, which balances blocks when the cost per group varies).
+  const int32_t per = contiguous
+      ? (ct_end - ct_begin + (int32_t)gridDim.x - 1) / (int32_t)gridDim.x : 1;
+  const int32_t step = contiguous ? 1 : (int32_t)gridDim.x;
   const int32_t my_lo = ct_begin + (int32_t)blockIdx.x * per;
-  const int32_t my_hi = my_lo + per < ct_end ? my_lo + per : ct_end;
-  for (int32_t ct = my_lo; ct < my_hi; ++ct) {
+  const int32_t my_hi = contiguous ? (my_lo + per < ct_end ? my_lo + per : ct_end) : ct_end;
+  for (int32_t ct = my_lo; ct < my_hi; ct += step) {
     // segment of this block-group (the same for every thread of the block)
     int a = 0, b = k + 1;
     while (a < b) {
@@ -383,7 +388,7 @@ int seg_plan_export_col(const SegPlan& p, const int32_t* rp, int32_t* col, cudaS
 template <class Op, int THREADS>
 static int launch_seg_gather(const SegPlan& p, const typename Op::T* x, int32_t nx,
                              typename Op::T* out, int32_t ct_begin, int32_t ct_end, int grid,
-                             int tab_cap, cudaStream_t s) {
+                             int contiguous, int tab_cap, cudaStream_t s) {
   if (ct_end <= ct_begin) return CG_OK;
   using T = typename Op::T;
   const size_t smem = (size_t)tab_cap * sizeof(T);
@@ -392,8 +397,9 @@ static int launch_seg_gather(const SegPlan& p, const typename Op::T* x, int32_t 
     CG_CUDA(cudaFuncSetAttribute((const void*)fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)smem));
   fn<<<grid, THREADS, smem, s>>>(p.colf, x, nx, p.first_row, p.seg_cstart, p.seg_E, p.seg_chunk,
-                                 p.seg_ctile, p.seg_lo, p.seg_tab, p.k, ct_begin, ct_end, tab_cap,
-                                 out, reinterpret_cast<T*>(p.carry), p.carry_row);
+                                 p.seg_ctile, p.seg_lo, p.seg_tab, p.k, ct_begin, ct_end,
+                                 contiguous, tab_cap, out, reinterpret_cast<T*>(p.carry),
+                                 p.carry_row);
   CG_LAUNCH_CHECK();
   return CG_OK;
 }
@@ -406,13 +412,15 @@ int run_seg_gather(const SegPlan& p, const typename Op::T* x, int32_t nx, typena
   // staged segments [0, m): table in shared memory, the launch shape chosen
   if (p.m > 0) {
     if (p.threads == 1024)
-      CG_TRY((launch_seg_gather<Op, 1024>(p, x, nx, out, 0, p.ct_split, p.grid, p.tab_cap, s)));
+      CG_TRY((launch_seg_gather<Op, 1024>(p, x, nx, out, 0, p.ct_split, p.grid, 1, p.tab_cap,
+                                          s)));
     else
-      CG_TRY((launch_seg_gather<Op, 512>(p, x, nx, out, 0, p.ct_split, p.grid, p.tab_cap, s)));
+      CG_TRY((launch_seg_gather<Op, 512>(p, x, nx, out, 0, p.ct_split, p.grid, 1, p.tab_cap,
+                                         s)));
   }
   // the rest through L1/L2: no shared memory, so the whole on-chip store is L1
   CG_TRY((launch_seg_gather<Op, 1024>(p, x, nx, out, p.ct_split, (int32_t)p.n_ctiles, p.grid_l2,
-                                      0, s)));
+                                      0, 0, s)));
   carry_fixup_kernel<Op><<<grid_for(p.nchunks, 256, 4), 256, 0, s>>>(
       reinterpret_cast<const T*>(p.carry), p.carry_row, p.nchunks, p.rows, out);
   CG_LAUNCH_CHECK();
