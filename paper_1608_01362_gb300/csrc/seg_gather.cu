@@ -69,53 +69,66 @@ __global__ void first_row_kernel(const int64_t* __restrict__ rp,
   }
 }
 
-template <class Op, int THREADS>
+// STAGED: every segment of [ct_begin, ct_end) is read from a shared-memory
+// copy (each block takes one contiguous run of block-groups); otherwise all
+// reads go through L1/L2 (round-robin over the groups).
+template <class Op, int THREADS, bool STAGED>
 __global__ void __launch_bounds__(THREADS, 2048 / THREADS)
 seg_gather_kernel(const uint32_t* __restrict__ colf, const typename Op::T* __restrict__ x,
                   int32_t nx, const int32_t* __restrict__ first_row,
                   const int64_t* __restrict__ seg_cstart, const int32_t* __restrict__ seg_E,
                   const int64_t* __restrict__ seg_chunk, const int32_t* __restrict__ seg_ctile,
                   const int32_t* __restrict__ seg_lo, const int32_t* __restrict__ seg_tab, int k,
-                  int32_t ct_begin, int32_t ct_end, int contiguous, int tab_cap,
-                  typename Op::T* __restrict__ out,
+                  int32_t ct_begin, int32_t ct_end, typename Op::T* __restrict__ out,
                   typename Op::T* __restrict__ carry, int32_t* __restrict__ carry_row) {
   using T = typename Op::T;
   constexpr int WARPS = THREADS / 32;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* tab = reinterpret_cast<T*>(smem_raw);
   const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
-  int cur = -1;
-  // per-segment state in 32 bits (colf entries and chunks stay below 2^31)
-  int32_t lo = 0, tn = 0, Es = 0, cstart = 0, cbase = 0, ctbase = 0;
 
-  // Block-groups [ct_begin, ct_end): with `contiguous`, each block takes one
-  // contiguous share (it meets at most a few segments, so it stages at most
-  // a few tables); otherwise round-robin (the grid sweeps the groups in
-  // order, which balances blocks when the cost per group varies).
-  const int32_t per = contiguous
-      ? (ct_end - ct_begin + (int32_t)gridDim.x - 1) / (int32_t)gridDim.x : 1;
-  const int32_t step = contiguous ? 1 : (int32_t)gridDim.x;
-  const int32_t my_lo = ct_begin + (int32_t)blockIdx.x * per;
-  const int32_t my_hi = contiguous ? (my_lo + per < ct_end ? my_lo + per : ct_end) : ct_end;
-  for (int32_t ct = my_lo; ct < my_hi; ct += step) {
-    // segment of this block-group (the same for every thread of the block)
+  int32_t my_lo, my_hi, step;
+  if (STAGED) {  // one contiguous run: a block meets few segments, stages few tables
+    const int32_t per = (ct_end - ct_begin + (int32_t)gridDim.x - 1) / (int32_t)gridDim.x;
+    my_lo = ct_begin + (int32_t)blockIdx.x * per;
+    my_hi = my_lo + per < ct_end ? my_lo + per : ct_end;
+    step = 1;
+  } else {  // round-robin: the grid sweeps the groups in order, balancing blocks
+    my_lo = ct_begin + (int32_t)blockIdx.x;
+    my_hi = ct_end;
+    step = (int32_t)gridDim.x;
+  }
+  if (my_lo >= my_hi) return;
+  // segment of the first group; groups only move forward, so later segments
+  // are found by stepping
+  int s;
+  {
     int a = 0, b = k + 1;
     while (a < b) {
       const int mid = (a + b) >> 1;
-      if (seg_ctile[mid] <= ct) a = mid + 1; else b = mid;
+      if (seg_ctile[mid] <= my_lo) a = mid + 1; else b = mid;
     }
-    const int s = a - 1;
-    if (s != cur) {
-      __syncthreads();  // every warp is done reading the previous table
-      cur = s;
+    s = a - 1;
+  }
+  int32_t lo = 0, tn = 0, Es = 0, cstart = 0, cbase = 0, ctbase = 0, ctnext = 0;
+  bool fresh = true;
+
+  for (int32_t ct = my_lo; ct < my_hi; ct += step) {
+    if (fresh || ct >= ctnext) {
+      while (ct >= seg_ctile[s + 1]) ++s;
       lo = seg_lo[s];
-      tn = seg_tab[s] < tab_cap ? seg_tab[s] : tab_cap;
       Es = seg_E[s];
       cstart = (int32_t)seg_cstart[s];
       cbase = (int32_t)seg_chunk[s];
       ctbase = seg_ctile[s];
-      for (int i = tid; i < tn; i += THREADS) tab[i] = x[lo + i];
-      __syncthreads();
+      ctnext = seg_ctile[s + 1];
+      fresh = false;
+      if (STAGED) {  // (uniform across the block: every thread sees the same groups)
+        __syncthreads();  // every warp is done reading the previous table
+        tn = seg_tab[s];
+        for (int i = tid; i < tn; i += THREADS) tab[i] = x[lo + i];
+        __syncthreads();
+      }
     }
     const int32_t j = (ct - ctbase) * WARPS + w;  // chunk of this warp within the segment
     const int32_t e0 = j * kChunkEdges;
@@ -130,18 +143,18 @@ seg_gather_kernel(const uint32_t* __restrict__ colf, const typename Op::T* __res
     const uint32_t cf[8] = {qa.x, qa.y, qa.z, qa.w, qb.x, qb.y, qb.z, qb.w};
     T v[8];
     uint32_t fl = 0;
+    const int nl = n - lane * 8;  // valid edges of this lane (may be <= 0 or > 8)
 #pragma unroll
     for (int u = 0; u < 8; ++u) {
-      const bool ok = lane * 8 + u < n;
+      const bool ok = u < nl;
       const int32_t src = (int32_t)(cf[u] & ~kRowEndFlag);
       if (ok && (cf[u] & kRowEndFlag)) fl |= 1u << u;
-      const uint32_t off = (uint32_t)(src - lo);
       T val = Op::identity();
-      if (ok) {
-        if (off < (uint32_t)tn)
-          val = tab[off];
-        else if (src < nx)
-          val = __ldg(x + src);
+      if (STAGED) {
+        const uint32_t off = (uint32_t)(src - lo);
+        if (ok && off < (uint32_t)tn) val = tab[off];
+      } else {
+        if (ok && (uint32_t)src < (uint32_t)nx) val = __ldg(x + src);
       }
       v[u] = val;
     }
@@ -385,21 +398,20 @@ int seg_plan_export_col(const SegPlan& p, const int32_t* rp, int32_t* col, cudaS
   return CG_OK;
 }
 
-template <class Op, int THREADS>
+template <class Op, int THREADS, bool STAGED>
 static int launch_seg_gather(const SegPlan& p, const typename Op::T* x, int32_t nx,
                              typename Op::T* out, int32_t ct_begin, int32_t ct_end, int grid,
-                             int contiguous, int tab_cap, cudaStream_t s) {
+                             int tab_cap, cudaStream_t s) {
   if (ct_end <= ct_begin) return CG_OK;
   using T = typename Op::T;
-  const size_t smem = (size_t)tab_cap * sizeof(T);
-  auto fn = seg_gather_kernel<Op, THREADS>;
+  const size_t smem = STAGED ? (size_t)tab_cap * sizeof(T) : 0;
+  auto fn = seg_gather_kernel<Op, THREADS, STAGED>;
   if (smem > 48 * 1024)
     CG_CUDA(cudaFuncSetAttribute((const void*)fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)smem));
   fn<<<grid, THREADS, smem, s>>>(p.colf, x, nx, p.first_row, p.seg_cstart, p.seg_E, p.seg_chunk,
-                                 p.seg_ctile, p.seg_lo, p.seg_tab, p.k, ct_begin, ct_end,
-                                 contiguous, tab_cap, out, reinterpret_cast<T*>(p.carry),
-                                 p.carry_row);
+                                 p.seg_ctile, p.seg_lo, p.seg_tab, p.k, ct_begin, ct_end, out,
+                                 reinterpret_cast<T*>(p.carry), p.carry_row);
   CG_LAUNCH_CHECK();
   return CG_OK;
 }
@@ -412,15 +424,15 @@ int run_seg_gather(const SegPlan& p, const typename Op::T* x, int32_t nx, typena
   // staged segments [0, m): table in shared memory, the launch shape chosen
   if (p.m > 0) {
     if (p.threads == 1024)
-      CG_TRY((launch_seg_gather<Op, 1024>(p, x, nx, out, 0, p.ct_split, p.grid, 1, p.tab_cap,
-                                          s)));
+      CG_TRY((launch_seg_gather<Op, 1024, true>(p, x, nx, out, 0, p.ct_split, p.grid, p.tab_cap,
+                                                s)));
     else
-      CG_TRY((launch_seg_gather<Op, 512>(p, x, nx, out, 0, p.ct_split, p.grid, 1, p.tab_cap,
-                                         s)));
+      CG_TRY((launch_seg_gather<Op, 512, true>(p, x, nx, out, 0, p.ct_split, p.grid, p.tab_cap,
+                                               s)));
   }
   // the rest through L1/L2: no shared memory, so the whole on-chip store is L1
-  CG_TRY((launch_seg_gather<Op, 1024>(p, x, nx, out, p.ct_split, (int32_t)p.n_ctiles, p.grid_l2,
-                                      0, 0, s)));
+  CG_TRY((launch_seg_gather<Op, 1024, false>(p, x, nx, out, p.ct_split, (int32_t)p.n_ctiles,
+                                             p.grid_l2, 0, s)));
   carry_fixup_kernel<Op><<<grid_for(p.nchunks, 256, 4), 256, 0, s>>>(
       reinterpret_cast<const T*>(p.carry), p.carry_row, p.nchunks, p.rows, out);
   CG_LAUNCH_CHECK();
