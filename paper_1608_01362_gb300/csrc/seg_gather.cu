@@ -50,16 +50,17 @@ __global__ void export_col_kernel(const uint32_t* __restrict__ colf,
   }
 }
 
-// Subgraph row of each chunk's first edge.
-__global__ void first_row_kernel(const int64_t* __restrict__ rp,
+// Subgraph row of each chunk's first edge (segments [0, m) use chunks of
+// chunk_a edges, the others chunks of chunk_b).
+__global__ void first_row_kernel(const int32_t* __restrict__ rp,
                                  const int64_t* __restrict__ row_base,
                                  const int64_t* __restrict__ edge_base,
-                                 const int64_t* __restrict__ chunk_base, int k, int64_t nchunks,
-                                 int32_t* __restrict__ first_row) {
+                                 const int64_t* __restrict__ chunk_base, int k, int m, int chunk_a,
+                                 int chunk_b, int64_t nchunks, int32_t* __restrict__ first_row) {
   for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < nchunks;
        c += (int64_t)gridDim.x * blockDim.x) {
     const int s = last_le(chunk_base, k + 1, c);
-    const int64_t e = edge_base[s] + (c - chunk_base[s]) * kChunkEdges;
+    const int64_t e = edge_base[s] + (c - chunk_base[s]) * (s < m ? chunk_a : chunk_b);
     int64_t lo = row_base[s], hi = row_base[s + 1];  // last row with rp[row] <= e
     while (lo < hi) {
       const int64_t mid = (lo + hi) >> 1;
@@ -71,9 +72,10 @@ __global__ void first_row_kernel(const int64_t* __restrict__ rp,
 
 // STAGED: every segment of [ct_begin, ct_end) is read from a shared-memory
 // copy (each block takes one contiguous run of block-groups); otherwise all
-// reads go through L1/L2 (round-robin over the groups).
-template <class Op, int THREADS, bool STAGED>
-__global__ void __launch_bounds__(THREADS, 2048 / THREADS)
+// reads go through L1/L2 (round-robin over the groups).  A warp's chunk is
+// 32 * IPL edges; lane l holds edges [IPL*l, IPL*l + IPL).
+template <class Op, int THREADS, bool STAGED, int IPL>
+__global__ void __launch_bounds__(THREADS, IPL == 8 ? 2048 / THREADS : 1)
 seg_gather_kernel(const uint32_t* __restrict__ colf, const typename Op::T* __restrict__ x,
                   int32_t nx, const int32_t* __restrict__ first_row,
                   const int64_t* __restrict__ seg_cstart, const int32_t* __restrict__ seg_E,
@@ -83,6 +85,7 @@ seg_gather_kernel(const uint32_t* __restrict__ colf, const typename Op::T* __res
                   typename Op::T* __restrict__ carry, int32_t* __restrict__ carry_row) {
   using T = typename Op::T;
   constexpr int WARPS = THREADS / 32;
+  constexpr int CHUNK = 32 * IPL;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* tab = reinterpret_cast<T*>(smem_raw);
   const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
@@ -110,11 +113,10 @@ seg_gather_kernel(const uint32_t* __restrict__ colf, const typename Op::T* __res
     }
     s = a - 1;
   }
-  int32_t lo = 0, tn = 0, Es = 0, cstart = 0, cbase = 0, ctbase = 0, ctnext = 0;
-  bool fresh = true;
+  int32_t lo = 0, tn = 0, Es = 0, cstart = 0, cbase = 0, ctbase = 0, ctnext = -1;
 
   for (int32_t ct = my_lo; ct < my_hi; ct += step) {
-    if (fresh || ct >= ctnext) {
+    if (ct >= ctnext) {  // first group, or a new segment (uniform across the block)
       while (ct >= seg_ctile[s + 1]) ++s;
       lo = seg_lo[s];
       Es = seg_E[s];
@@ -122,8 +124,7 @@ seg_gather_kernel(const uint32_t* __restrict__ colf, const typename Op::T* __res
       cbase = (int32_t)seg_chunk[s];
       ctbase = seg_ctile[s];
       ctnext = seg_ctile[s + 1];
-      fresh = false;
-      if (STAGED) {  // (uniform across the block: every thread sees the same groups)
+      if (STAGED) {
         __syncthreads();  // every warp is done reading the previous table
         tn = seg_tab[s];
         for (int i = tid; i < tn; i += THREADS) tab[i] = x[lo + i];
@@ -131,32 +132,53 @@ seg_gather_kernel(const uint32_t* __restrict__ colf, const typename Op::T* __res
       }
     }
     const int32_t j = (ct - ctbase) * WARPS + w;  // chunk of this warp within the segment
-    const int32_t e0 = j * kChunkEdges;
+    const int32_t e0 = j * CHUNK;
     if (e0 >= Es) continue;  // warp-uniform
-    const int n = Es - e0 < kChunkEdges ? Es - e0 : kChunkEdges;
+    const int n = Es - e0 < CHUNK ? Es - e0 : CHUNK;
     const int32_t c = cbase + j;
     const int32_t frow = first_row[c];
 
-    // 1. this lane's 8 edges (two 16-byte streaming loads; colf is padded)
-    const uint4* p = reinterpret_cast<const uint4*>(colf + cstart + e0 + lane * 8);
-    const uint4 qa = __ldcs(p), qb = __ldcs(p + 1);
-    const uint32_t cf[8] = {qa.x, qa.y, qa.z, qa.w, qb.x, qb.y, qb.z, qb.w};
-    T v[8];
-    uint32_t fl = 0;
-    const int nl = n - lane * 8;  // valid edges of this lane (may be <= 0 or > 8)
+    // 1. this lane's IPL edges (16-byte streaming loads; colf is padded)
+    const uint4* p = reinterpret_cast<const uint4*>(colf + cstart + e0 + lane * IPL);
+    uint32_t cf[IPL];
 #pragma unroll
-    for (int u = 0; u < 8; ++u) {
-      const bool ok = u < nl;
-      const int32_t src = (int32_t)(cf[u] & ~kRowEndFlag);
-      if (ok && (cf[u] & kRowEndFlag)) fl |= 1u << u;
-      T val = Op::identity();
-      if (STAGED) {
-        const uint32_t off = (uint32_t)(src - lo);
-        if (ok && off < (uint32_t)tn) val = tab[off];
-      } else {
-        if (ok && (uint32_t)src < (uint32_t)nx) val = __ldg(x + src);
+    for (int q = 0; q < IPL / 4; ++q) {
+      const uint4 t4 = __ldcs(p + q);
+      cf[4 * q] = t4.x;
+      cf[4 * q + 1] = t4.y;
+      cf[4 * q + 2] = t4.z;
+      cf[4 * q + 3] = t4.w;
+    }
+    T v[IPL];
+    uint32_t fl = 0;
+    const int nl = n - lane * IPL;  // valid edges of this lane (may be <= 0 or > IPL)
+    if (nl >= IPL) {  // whole lane valid (every lane but the tail of a segment's last chunk)
+#pragma unroll
+      for (int u = 0; u < IPL; ++u) {
+        const int32_t src = (int32_t)(cf[u] & ~kRowEndFlag);
+        fl |= (cf[u] >> 31) << u;
+        if (STAGED) {
+          const uint32_t off = (uint32_t)(src - lo);
+          v[u] = tab[off < (uint32_t)tn ? off : 0u];
+        } else {
+          v[u] = (uint32_t)src < (uint32_t)nx ? __ldg(x + src) : Op::identity();
+        }
       }
-      v[u] = val;
+    } else {
+#pragma unroll
+      for (int u = 0; u < IPL; ++u) {
+        const bool ok = u < nl;
+        const int32_t src = (int32_t)(cf[u] & ~kRowEndFlag);
+        if (ok) fl |= (cf[u] >> 31) << u;
+        T val = Op::identity();
+        if (STAGED) {
+          const uint32_t off = (uint32_t)(src - lo);
+          if (ok && off < (uint32_t)tn) val = tab[off];
+        } else {
+          if (ok && (uint32_t)src < (uint32_t)nx) val = __ldg(x + src);
+        }
+        v[u] = val;
+      }
     }
 
     // 2. rows ended before this lane (exclusive warp prefix of flag counts)
@@ -171,18 +193,13 @@ seg_gather_kernel(const uint32_t* __restrict__ colf, const typename Op::T* __res
 
     // 3. sequential fold; rows that start and end in this lane are final
     T acc = Op::identity(), first_val = Op::identity();
-    int nf = 0;
+    const int f0 = __ffs(fl) - 1;  // first row end in this lane (-1: none)
 #pragma unroll
-    for (int u = 0; u < 8; ++u) {
+    for (int u = 0; u < IPL; ++u) {
       acc = Op::op(acc, v[u]);
-      if (fl & (1u << u)) {
-        if (nf == 0)
-          first_val = acc;
-        else
-          out[row0 + nf] = acc;
-        ++nf;
-        acc = Op::identity();
-      }
+      if (u == f0) first_val = acc;
+      if (((fl >> u) & 1u) && u != f0) out[row0 + __popc(fl & ((1u << u) - 1u))] = acc;
+      if ((fl >> u) & 1u) acc = Op::identity();
     }
 
     // 4. segmented scan of the open-row parts; completes each lane's first row
@@ -202,9 +219,9 @@ seg_gather_kernel(const uint32_t* __restrict__ colf, const typename Op::T* __res
 
     // 5. the row open at the chunk's end
     const int total = __shfl_sync(0xffffffffu, incl, 31);
-    const uint32_t lf = __shfl_sync(0xffffffffu, fl, (n - 1) >> 3);
+    const uint32_t lf = __shfl_sync(0xffffffffu, fl, (n - 1) / IPL);
     if (lane == 31) {
-      const bool closed = (lf >> ((n - 1) & 7)) & 1u;
+      const bool closed = (lf >> ((n - 1) % IPL)) & 1u;
       carry[c] = closed ? Op::identity() : S;
       carry_row[c] = closed ? -1 : frow + total;
     }
@@ -227,24 +244,23 @@ int seg_table_capacity(int ctas) {
   return (int)((per / 4) & ~31LL);
 }
 
-int seg_plan_build(const int32_t* col, const int64_t* rp, int64_t rows, int64_t E, int k,
-                   const std::vector<int64_t>& row_base, const std::vector<int64_t>& edge_base,
-                   const std::vector<int64_t>& src_bounds, SegPlan* p, cudaStream_t s) {
+int seg_plan_build(const int32_t* col, const int64_t* rp, const int32_t* rp32, int64_t rows,
+                   int64_t E, int k, const std::vector<int64_t>& row_base,
+                   const std::vector<int64_t>& edge_base, const std::vector<int64_t>& src_bounds,
+                   SegPlan* p, cudaStream_t s) {
   p->k = k;
   p->E = E;
   p->rows = rows;
+  p->rp32 = rp32;
   p->row_base = row_base;
   p->edge_base = edge_base;
   p->src_bounds = src_bounds;
   p->h_cstart.assign(k + 1, 0);
-  p->h_chunk.assign(k + 1, 0);
   for (int q = 0; q < k; ++q) {
     const int64_t Eq = edge_base[q + 1] - edge_base[q];
     p->h_cstart[q + 1] = p->h_cstart[q] + ((Eq + 7) & ~7LL);
-    p->h_chunk[q + 1] = p->h_chunk[q] + ceil_div(Eq, kChunkEdges);
   }
-  p->nchunks = p->h_chunk[k];
-  p->colf_len = p->h_cstart[k] + kChunkEdges;  // chunks may read past their segment's end
+  p->colf_len = p->h_cstart[k] + kMaxChunkEdges;  // chunks may read past their segment's end
   if (p->colf_len >= 0x7FFFFFFFLL) {
     set_error("segmented gather: padded edge array exceeds 2^31 entries");
     return CG_ERR_UNSUPPORTED;
@@ -254,48 +270,34 @@ int seg_plan_build(const int32_t* col, const int64_t* rp, int64_t rows, int64_t 
   const size_t kk = (size_t)(k > 0 ? k : 1);
   CG_CUDA(cudaMalloc((void**)&p->seg_cstart, sizeof(int64_t) * kk));
   CG_CUDA(cudaMalloc((void**)&p->seg_E, sizeof(int32_t) * kk));
-  CG_CUDA(cudaMalloc((void**)&p->seg_chunk, sizeof(int64_t) * kk));
+  CG_CUDA(cudaMalloc((void**)&p->seg_chunk, sizeof(int64_t) * (kk + 1)));
   CG_CUDA(cudaMalloc((void**)&p->seg_ctile, sizeof(int32_t) * (kk + 1)));
   CG_CUDA(cudaMalloc((void**)&p->seg_lo, sizeof(int32_t) * kk));
   CG_CUDA(cudaMalloc((void**)&p->seg_tab, sizeof(int32_t) * kk));
-  const size_t nc = (size_t)(p->nchunks > 0 ? p->nchunks : 1);
-  CG_CUDA(cudaMalloc((void**)&p->first_row, sizeof(int32_t) * nc));
-  CG_CUDA(cudaMalloc(&p->carry, sizeof(int32_t) * nc));
-  CG_CUDA(cudaMalloc((void**)&p->carry_row, sizeof(int32_t) * nc));
+  CG_CUDA(cudaMalloc((void**)&p->meta, sizeof(int64_t) * 3 * (kk + 1)));
 
-  std::vector<int32_t> segE(kk, 0);
-  for (int q = 0; q < k; ++q) segE[q] = (int32_t)(edge_base[q + 1] - edge_base[q]);
+  std::vector<int32_t> segE(kk, 0), lo(kk, 0);
+  for (int q = 0; q < k; ++q) {
+    segE[q] = (int32_t)(edge_base[q + 1] - edge_base[q]);
+    lo[q] = (int32_t)src_bounds[q];
+  }
   CG_CUDA(cudaMemcpyAsync(p->seg_cstart, p->h_cstart.data(), sizeof(int64_t) * k,
                           cudaMemcpyHostToDevice, s));
   CG_CUDA(cudaMemcpyAsync(p->seg_E, segE.data(), sizeof(int32_t) * k, cudaMemcpyHostToDevice, s));
-  CG_CUDA(cudaMemcpyAsync(p->seg_chunk, p->h_chunk.data(), sizeof(int64_t) * k,
+  CG_CUDA(cudaMemcpyAsync(p->seg_lo, lo.data(), sizeof(int32_t) * k, cudaMemcpyHostToDevice, s));
+  // meta: row_base, edge_base, cstart (k+1 each), kept for chunk indexing and export
+  CG_CUDA(cudaMemcpyAsync(p->meta, row_base.data(), sizeof(int64_t) * (k + 1),
                           cudaMemcpyHostToDevice, s));
-  int64_t* meta = nullptr;  // row_base, edge_base, cstart, chunk_base: 4 x (k+1)
-  CG_CUDA(cudaMallocAsync((void**)&meta, sizeof(int64_t) * 4 * (k + 1), s));
-  cudaError_t e = cudaMemcpyAsync(meta, row_base.data(), sizeof(int64_t) * (k + 1),
-                                  cudaMemcpyHostToDevice, s);
-  if (e == cudaSuccess)
-    e = cudaMemcpyAsync(meta + (k + 1), edge_base.data(), sizeof(int64_t) * (k + 1),
-                        cudaMemcpyHostToDevice, s);
-  if (e == cudaSuccess)
-    e = cudaMemcpyAsync(meta + 2 * (k + 1), p->h_cstart.data(), sizeof(int64_t) * (k + 1),
-                        cudaMemcpyHostToDevice, s);
-  if (e == cudaSuccess)
-    e = cudaMemcpyAsync(meta + 3 * (k + 1), p->h_chunk.data(), sizeof(int64_t) * (k + 1),
-                        cudaMemcpyHostToDevice, s);
-  if (e == cudaSuccess && rows > 0) {
+  CG_CUDA(cudaMemcpyAsync(p->meta + (k + 1), edge_base.data(), sizeof(int64_t) * (k + 1),
+                          cudaMemcpyHostToDevice, s));
+  CG_CUDA(cudaMemcpyAsync(p->meta + 2 * (k + 1), p->h_cstart.data(), sizeof(int64_t) * (k + 1),
+                          cudaMemcpyHostToDevice, s));
+  if (rows > 0) {
     colf_fill_kernel<<<grid_for(rows * 32, 256, 16), 256, 0, s>>>(
-        col, rp, rows, meta, meta + (k + 1), meta + 2 * (k + 1), k, p->colf);
-    e = cudaGetLastError();
+        col, rp, rows, p->meta, p->meta + (k + 1), p->meta + 2 * (k + 1), k, p->colf);
+    CG_LAUNCH_CHECK();
   }
-  if (e == cudaSuccess && p->nchunks > 0) {
-    first_row_kernel<<<grid_for(p->nchunks, 256), 256, 0, s>>>(
-        rp, meta, meta + (k + 1), meta + 3 * (k + 1), k, p->nchunks, p->first_row);
-    e = cudaGetLastError();
-  }
-  cudaFreeAsync(meta, s);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(s);  // host vectors above go out of scope
-  if (e != cudaSuccess) return cuda_fail(e, "seg_plan_build", __FILE__, __LINE__);
+  CG_CUDA(cudaStreamSynchronize(s));  // host vectors above go out of scope
   return seg_plan_configure(p, 1024, 1, -1, s);
 }
 
@@ -316,9 +318,8 @@ int seg_plan_configure(SegPlan* p, int threads, int ctas_per_sm, int tab_vertice
   int tab = tab_vertices < 0 ? cap : std::min(tab_vertices, cap);
   tab &= ~3;
   const int k = p->k;
-  const int64_t grid_a = (int64_t)di.sm_count * ctas_per_sm;
-  // staged prefix: leading segments that fit the table and carry enough edges
-  // for every block that stages them to read each entry a few times on average
+  // staged prefix: leading segments that fit the table and carry enough
+  // edges (>= 4 per source) for staging them in shared memory to pay
   int m = 0;
   int64_t tabmax = 0;
   while (m < k && tab > 0) {
@@ -328,38 +329,67 @@ int seg_plan_configure(SegPlan* p, int threads, int ctas_per_sm, int tab_vertice
     tabmax = std::max(tabmax, size);
     ++m;
   }
+  // one block per SM of 1024 threads has registers for 16 edges per lane
+  const int ipl_a = (threads == 1024 && ctas_per_sm == 1) ? 16 : 8;
+  const int chunk_a = 32 * ipl_a, chunk_b = 32 * 8;
   const int warps_a = threads / 32, warps_b = 1024 / 32;
-  std::vector<int32_t> ctile(k + 1, 0), lo(k > 0 ? k : 1, 0), tn(k > 0 ? k : 1, 0);
-  for (int q = 0; q < k; ++q)
-    ctile[q + 1] = ctile[q] + (int32_t)ceil_div(p->h_chunk[q + 1] - p->h_chunk[q],
-                                                q < m ? warps_a : warps_b);
+  std::vector<int64_t> chunk(k + 1, 0);
+  std::vector<int32_t> ctile(k + 1, 0), tn(k > 0 ? k : 1, 0);
   for (int q = 0; q < k; ++q) {
-    lo[q] = (int32_t)p->src_bounds[q];
+    const int64_t Eq = p->edge_base[q + 1] - p->edge_base[q];
+    const int64_t nch = ceil_div(Eq, q < m ? chunk_a : chunk_b);
+    chunk[q + 1] = chunk[q] + nch;
+    ctile[q + 1] = ctile[q] + (int32_t)ceil_div(nch, q < m ? warps_a : warps_b);
     tn[q] = q < m ? (int32_t)(p->src_bounds[q + 1] - p->src_bounds[q]) : 0;
   }
+  const int64_t nchunks = chunk[k];
+  if (nchunks > p->chunk_cap) {
+    cudaFree(p->first_row);
+    cudaFree(p->carry);
+    cudaFree(p->carry_row);
+    p->first_row = nullptr;
+    p->carry = nullptr;
+    p->carry_row = nullptr;
+    p->chunk_cap = 0;
+    const size_t nc = (size_t)(nchunks > 0 ? nchunks : 1);
+    CG_CUDA(cudaMalloc((void**)&p->first_row, sizeof(int32_t) * nc));
+    CG_CUDA(cudaMalloc(&p->carry, sizeof(int32_t) * nc));
+    CG_CUDA(cudaMalloc((void**)&p->carry_row, sizeof(int32_t) * nc));
+    p->chunk_cap = nchunks;
+  }
+  CG_CUDA(cudaMemcpyAsync(p->seg_chunk, chunk.data(), sizeof(int64_t) * (k + 1),
+                          cudaMemcpyHostToDevice, s));
   CG_CUDA(cudaMemcpyAsync(p->seg_ctile, ctile.data(), sizeof(int32_t) * (k + 1),
                           cudaMemcpyHostToDevice, s));
-  if (k > 0) {
-    CG_CUDA(cudaMemcpyAsync(p->seg_lo, lo.data(), sizeof(int32_t) * k, cudaMemcpyHostToDevice, s));
+  if (k > 0)
     CG_CUDA(cudaMemcpyAsync(p->seg_tab, tn.data(), sizeof(int32_t) * k, cudaMemcpyHostToDevice,
                             s));
+  if (nchunks > 0) {
+    first_row_kernel<<<grid_for(nchunks, 256), 256, 0, s>>>(
+        p->rp32, p->meta, p->meta + (k + 1), p->seg_chunk, k, m, chunk_a, chunk_b, nchunks,
+        p->first_row);
+    CG_LAUNCH_CHECK();
   }
-  CG_CUDA(cudaStreamSynchronize(s));
+  CG_CUDA(cudaStreamSynchronize(s));  // host vectors go out of scope
   p->threads = threads;
   p->ctas_per_sm = ctas_per_sm;
+  p->ipl_a = ipl_a;
   p->tab_cap = (int)((tabmax + 3) & ~3LL);
+  p->table_request = tab;
   p->m = m;
+  p->nchunks = nchunks;
   p->ct_split = ctile[m];
   p->n_ctiles = ctile[k];
-  p->grid = (int)std::max<int64_t>(1, std::min<int64_t>(p->ct_split, grid_a));
+  p->grid = (int)std::max<int64_t>(
+      1, std::min<int64_t>(p->ct_split, (int64_t)di.sm_count * ctas_per_sm));
   p->grid_l2 = (int)std::max<int64_t>(
       1, std::min<int64_t>(p->n_ctiles - p->ct_split, (int64_t)di.sm_count * 2));
-  p->table_request = tab;
   return CG_OK;
 }
 
 void seg_plan_free(SegPlan* p) {
   cudaFree(p->colf);
+  cudaFree(p->meta);
   cudaFree(p->seg_cstart);
   cudaFree(p->seg_E);
   cudaFree(p->seg_chunk);
@@ -377,35 +407,21 @@ int64_t seg_plan_bytes(const SegPlan& p) { return 4 * p.colf_len + 12 * p.nchunk
 int seg_plan_export_col(const SegPlan& p, const int32_t* rp, int32_t* col, cudaStream_t s) {
   if (p.rows == 0) return CG_OK;
   const int k = p.k;
-  int64_t* meta = nullptr;
-  CG_CUDA(cudaMallocAsync((void**)&meta, sizeof(int64_t) * 3 * (k + 1), s));
-  cudaError_t e = cudaMemcpyAsync(meta, p.row_base.data(), sizeof(int64_t) * (k + 1),
-                                  cudaMemcpyHostToDevice, s);
-  if (e == cudaSuccess)
-    e = cudaMemcpyAsync(meta + (k + 1), p.edge_base.data(), sizeof(int64_t) * (k + 1),
-                        cudaMemcpyHostToDevice, s);
-  if (e == cudaSuccess)
-    e = cudaMemcpyAsync(meta + 2 * (k + 1), p.h_cstart.data(), sizeof(int64_t) * (k + 1),
-                        cudaMemcpyHostToDevice, s);
-  if (e == cudaSuccess) {
-    export_col_kernel<<<grid_for(p.rows * 32, 256, 16), 256, 0, s>>>(
-        p.colf, rp, p.rows, meta, meta + (k + 1), meta + 2 * (k + 1), k, col);
-    e = cudaGetLastError();
-  }
-  cudaFreeAsync(meta, s);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-  if (e != cudaSuccess) return cuda_fail(e, "seg_plan_export_col", __FILE__, __LINE__);
+  export_col_kernel<<<grid_for(p.rows * 32, 256, 16), 256, 0, s>>>(
+      p.colf, rp, p.rows, p.meta, p.meta + (k + 1), p.meta + 2 * (k + 1), k, col);
+  CG_LAUNCH_CHECK();
+  CG_CUDA(cudaStreamSynchronize(s));
   return CG_OK;
 }
 
-template <class Op, int THREADS, bool STAGED>
+template <class Op, int THREADS, bool STAGED, int IPL>
 static int launch_seg_gather(const SegPlan& p, const typename Op::T* x, int32_t nx,
                              typename Op::T* out, int32_t ct_begin, int32_t ct_end, int grid,
                              int tab_cap, cudaStream_t s) {
   if (ct_end <= ct_begin) return CG_OK;
   using T = typename Op::T;
   const size_t smem = STAGED ? (size_t)tab_cap * sizeof(T) : 0;
-  auto fn = seg_gather_kernel<Op, THREADS, STAGED>;
+  auto fn = seg_gather_kernel<Op, THREADS, STAGED, IPL>;
   if (smem > 48 * 1024)
     CG_CUDA(cudaFuncSetAttribute((const void*)fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)smem));
@@ -421,18 +437,21 @@ int run_seg_gather(const SegPlan& p, const typename Op::T* x, int32_t nx, typena
                    cudaStream_t s) {
   if (p.nchunks == 0) return CG_OK;
   using T = typename Op::T;
-  // staged segments [0, m): table in shared memory, the launch shape chosen
+  // staged segments [0, m): read from a shared-memory copy
   if (p.m > 0) {
-    if (p.threads == 1024)
-      CG_TRY((launch_seg_gather<Op, 1024, true>(p, x, nx, out, 0, p.ct_split, p.grid, p.tab_cap,
-                                                s)));
+    if (p.threads == 1024 && p.ipl_a == 16)
+      CG_TRY((launch_seg_gather<Op, 1024, true, 16>(p, x, nx, out, 0, p.ct_split, p.grid,
+                                                    p.tab_cap, s)));
+    else if (p.threads == 1024)
+      CG_TRY((launch_seg_gather<Op, 1024, true, 8>(p, x, nx, out, 0, p.ct_split, p.grid,
+                                                   p.tab_cap, s)));
     else
-      CG_TRY((launch_seg_gather<Op, 512, true>(p, x, nx, out, 0, p.ct_split, p.grid, p.tab_cap,
-                                               s)));
+      CG_TRY((launch_seg_gather<Op, 512, true, 8>(p, x, nx, out, 0, p.ct_split, p.grid,
+                                                  p.tab_cap, s)));
   }
   // the rest through L1/L2: no shared memory, so the whole on-chip store is L1
-  CG_TRY((launch_seg_gather<Op, 1024, false>(p, x, nx, out, p.ct_split, (int32_t)p.n_ctiles,
-                                             p.grid_l2, 0, s)));
+  CG_TRY((launch_seg_gather<Op, 1024, false, 8>(p, x, nx, out, p.ct_split, (int32_t)p.n_ctiles,
+                                                p.grid_l2, 0, s)));
   carry_fixup_kernel<Op><<<grid_for(p.nchunks, 256, 4), 256, 0, s>>>(
       reinterpret_cast<const T*>(p.carry), p.carry_row, p.nchunks, p.rows, out);
   CG_LAUNCH_CHECK();

@@ -6,8 +6,9 @@
 // one edge, so row i is the (i+1)-th flagged edge: the gather needs no row
 // pointers at all.
 //
-// Work unit: a warp owns a chunk of 256 consecutive edges of one segment;
-// lane l holds edges [8l, 8l+8) of it (two 16-byte streaming loads).  Lanes
+// Work unit: a warp owns a chunk of 32*IPL consecutive edges of one segment
+// (IPL = 8, or 16 in the staged launch at one block per SM); lane l holds
+// edges [IPL*l, IPL*l + IPL) of it (16-byte streaming loads).  Lanes
 // fold their 8 values sequentially, emit every row that starts and ends
 // inside them, and a warp-wide segmented scan over the lanes' open-row parts
 // completes each lane's first row.  The row still open at the chunk's end
@@ -32,7 +33,7 @@
 namespace cg {
 
 constexpr uint32_t kRowEndFlag = 0x80000000u;
-constexpr int kChunkEdges = 256;  // 32 lanes x 8 edges
+constexpr int kMaxChunkEdges = 512;  // 32 lanes x 16 edges (staged launch, 1 block/SM)
 
 struct SegPlan {
   int k = 0;
@@ -41,16 +42,20 @@ struct SegPlan {
   int64_t colf_len = 0;
   int64_t* seg_cstart = nullptr;   // [k]   first colf entry of each segment
   int32_t* seg_E = nullptr;        // [k]   edges of each segment
-  int64_t* seg_chunk = nullptr;    // [k]   first global chunk of each segment
+  int64_t* seg_chunk = nullptr;    // [k+1] first global chunk of each segment
   int32_t* seg_ctile = nullptr;    // [k+1] first block-group of each segment
   int32_t* seg_lo = nullptr;       // [k]   first source of each segment
   int32_t* seg_tab = nullptr;      // [k]   table entries used for each segment
   int32_t* first_row = nullptr;    // [nchunks] subgraph row of each chunk's first edge
   void* carry = nullptr;           // [nchunks] 4-byte values
   int32_t* carry_row = nullptr;    // [nchunks]
-  std::vector<int64_t> h_cstart, h_chunk, src_bounds, edge_base, row_base;
+  int64_t* meta = nullptr;         // [3(k+1)] row_base, edge_base, cstart on the device
+  const int32_t* rp32 = nullptr;   // subgraph row starts (owned by the handle)
+  int64_t chunk_cap = 0;           // capacity of first_row / carry / carry_row
+  std::vector<int64_t> h_cstart, src_bounds, edge_base, row_base;
   int threads = 1024;       // staged-segment launch shape
   int ctas_per_sm = 1;
+  int ipl_a = 8;            // edges per lane of the staged launch
   int tab_cap = 0;          // table entries of the staged launch (its largest segment)
   int table_request = 0;    // the capacity asked for
   int m = 0;                // segments [0, m) are staged in shared memory
@@ -64,11 +69,12 @@ struct SegPlan {
 int seg_table_capacity(int ctas);
 
 // Build colf, the chunk index and the carry buffers from the unpadded
-// segmented CSR (col[E] int32 global sources, rp[rows+1] int64 row starts).
-// Synchronizes the stream.
-int seg_plan_build(const int32_t* col, const int64_t* rp, int64_t rows, int64_t E, int k,
-                   const std::vector<int64_t>& row_base, const std::vector<int64_t>& edge_base,
-                   const std::vector<int64_t>& src_bounds, SegPlan* p, cudaStream_t s);
+// segmented CSR (col[E] int32 global sources, rp[rows+1] int64 row starts;
+// rp32: the same row starts in int32, kept by the handle).  Synchronizes.
+int seg_plan_build(const int32_t* col, const int64_t* rp, const int32_t* rp32, int64_t rows,
+                   int64_t E, int k, const std::vector<int64_t>& row_base,
+                   const std::vector<int64_t>& edge_base, const std::vector<int64_t>& src_bounds,
+                   SegPlan* p, cudaStream_t s);
 
 // Launch shape: threads per block (512 or 1024), blocks per SM, table size
 // (-1: the capacity; 0: none).  Synchronizes the stream.

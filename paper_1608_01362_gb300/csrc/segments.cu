@@ -384,7 +384,8 @@ int build_impl(const int64_t* offsets, const int32_t* src, int32_t V, int64_t E,
 
   // F
   CG_CUDA(cudaStreamSynchronize(s));  // edge_base copies have landed
-  CG_TRY(seg_plan_build(col, rp, npairs, E, k, g->row_base, g->edge_base, bounds, &g->plan, s));
+  CG_TRY(seg_plan_build(col, rp, g->row_ptr, npairs, E, k, g->row_base, g->edge_base, bounds,
+                        &g->plan, s));
   CG_CUDA(cudaMalloc(&g->interm, sizeof(float) * (size_t)(npairs > 0 ? npairs : 1)));
   CG_CUDA(cudaMalloc((void**)&g->partials, sizeof(double) * 2 * (size_t)g->nb));
   CG_CUDA(cudaMalloc((void**)&g->counter, sizeof(unsigned)));
