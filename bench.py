@@ -186,7 +186,7 @@ def main():
     ap.add_argument("--scale", type=int, default=25)
     ap.add_argument("--k", type=int, default=0, help="uniform segments (0: autotune)")
     ap.add_argument("--threads", type=int, default=1024, help="gather threads (with --k)")
-    ap.add_argument("--ctas", type=int, default=2, help="gather blocks per SM (with --k)")
+    ap.add_argument("--ctas", type=int, default=1, help="gather blocks per SM (with --k)")
     ap.add_argument("--table", type=int, default=0, help="shared table entries (with --k)")
     ap.add_argument("--plan", type=float, default=0.0,
                     help="use planned bounds with this min_avg_degree (skips the autotuner)")

@@ -16,12 +16,13 @@ __device__ __forceinline__ int last_le(const int64_t* a, int n, int64_t v) {
   return lo - 1;
 }
 
-// One warp per subgraph row: copy its sources into the padded layout and
-// flag the last one.
+// One warp per subgraph row: copy its sources, as indices local to their
+// segment, into the padded layout and flag the last one.
 __global__ void colf_fill_kernel(const int32_t* __restrict__ col, const int64_t* __restrict__ rp,
                                  int64_t rows, const int64_t* __restrict__ row_base,
                                  const int64_t* __restrict__ edge_base,
-                                 const int64_t* __restrict__ cstart, int k,
+                                 const int64_t* __restrict__ cstart,
+                                 const int64_t* __restrict__ bounds, int k,
                                  uint32_t* __restrict__ colf) {
   const int lane = threadIdx.x & 31;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -29,8 +30,9 @@ __global__ void colf_fill_kernel(const int32_t* __restrict__ col, const int64_t*
     const int s = last_le(row_base, k + 1, i);
     const int64_t lo = rp[i], hi = rp[i + 1];
     const int64_t shift = cstart[s] - edge_base[s];
+    const int32_t src0 = (int32_t)bounds[s];
     for (int64_t e = lo + lane; e < hi; e += 32)
-      colf[e + shift] = (uint32_t)col[e] | (e == hi - 1 ? kRowEndFlag : 0u);
+      colf[e + shift] = (uint32_t)(col[e] - src0) | (e == hi - 1 ? kRowEndFlag : 0u);
   }
 }
 
@@ -38,15 +40,17 @@ __global__ void export_col_kernel(const uint32_t* __restrict__ colf,
                                   const int32_t* __restrict__ rp, int64_t rows,
                                   const int64_t* __restrict__ row_base,
                                   const int64_t* __restrict__ edge_base,
-                                  const int64_t* __restrict__ cstart, int k,
+                                  const int64_t* __restrict__ cstart,
+                                  const int64_t* __restrict__ bounds, int k,
                                   int32_t* __restrict__ col) {
   const int lane = threadIdx.x & 31;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
   for (int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < rows; i += nw) {
     const int s = last_le(row_base, k + 1, i);
     const int64_t shift = cstart[s] - edge_base[s];
+    const int32_t src0 = (int32_t)bounds[s];
     for (int64_t e = rp[i] + lane; e < rp[i + 1]; e += 32)
-      col[e] = (int32_t)(colf[e + shift] & ~kRowEndFlag);
+      col[e] = src0 + (int32_t)(colf[e + shift] & ~kRowEndFlag);
   }
 }
 
@@ -70,41 +74,28 @@ __global__ void first_row_kernel(const int32_t* __restrict__ rp,
   }
 }
 
-// STAGED: every segment of [ct_begin, ct_end) is read from a shared-memory
-// copy (each block takes one contiguous run of block-groups); otherwise all
-// reads go through L1/L2 (round-robin over the groups).  A warp's chunk is
-// 32 * IPL edges; lane l holds edges [IPL*l, IPL*l + IPL).
-template <class Op, int THREADS, bool STAGED, int IPL>
-__global__ void __launch_bounds__(THREADS, IPL == 8 ? 2048 / THREADS : 1)
+// The L1/L2 launch: every read of a segment in [ct_begin, ct_end) goes
+// through L1/L2.  Blocks take block-groups round-robin (the grid sweeps the
+// groups in order, which balances blocks when the cost per group varies).
+// A warp's chunk is 256 edges; lane l holds edges [8l, 8l + 8).
+template <class Op, int THREADS>
+__global__ void __launch_bounds__(THREADS, 2048 / THREADS)
 seg_gather_kernel(const uint32_t* __restrict__ colf, const typename Op::T* __restrict__ x,
                   int32_t nx, const int32_t* __restrict__ first_row,
                   const int64_t* __restrict__ seg_cstart, const int32_t* __restrict__ seg_E,
                   const int64_t* __restrict__ seg_chunk, const int32_t* __restrict__ seg_ctile,
-                  const int32_t* __restrict__ seg_lo, const int32_t* __restrict__ seg_tab, int k,
-                  int32_t ct_begin, int32_t ct_end, typename Op::T* __restrict__ out,
-                  typename Op::T* __restrict__ carry, int32_t* __restrict__ carry_row) {
+                  const int32_t* __restrict__ seg_lo, int k, int32_t ct_begin, int32_t ct_end,
+                  typename Op::T* __restrict__ out, typename Op::T* __restrict__ carry,
+                  int32_t* __restrict__ carry_row) {
   using T = typename Op::T;
   constexpr int WARPS = THREADS / 32;
+  constexpr int IPL = 8;
   constexpr int CHUNK = 32 * IPL;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  T* tab = reinterpret_cast<T*>(smem_raw);
   const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
-
-  int32_t my_lo, my_hi, step;
-  if (STAGED) {  // one contiguous run: a block meets few segments, stages few tables
-    const int32_t per = (ct_end - ct_begin + (int32_t)gridDim.x - 1) / (int32_t)gridDim.x;
-    my_lo = ct_begin + (int32_t)blockIdx.x * per;
-    my_hi = my_lo + per < ct_end ? my_lo + per : ct_end;
-    step = 1;
-  } else {  // round-robin: the grid sweeps the groups in order, balancing blocks
-    my_lo = ct_begin + (int32_t)blockIdx.x;
-    my_hi = ct_end;
-    step = (int32_t)gridDim.x;
-  }
-  if (my_lo >= my_hi) return;
-  // segment of the first group; groups only move forward, so later segments
-  // are found by stepping
-  int s;
+  const int32_t my_lo = ct_begin + (int32_t)blockIdx.x;
+  const int32_t step = (int32_t)gridDim.x;
+  if (my_lo >= ct_end) return;
+  int s;  // segment of the first group; later ones are found by stepping forward
   {
     int a = 0, b = k + 1;
     while (a < b) {
@@ -113,10 +104,10 @@ seg_gather_kernel(const uint32_t* __restrict__ colf, const typename Op::T* __res
     }
     s = a - 1;
   }
-  int32_t lo = 0, tn = 0, Es = 0, cstart = 0, cbase = 0, ctbase = 0, ctnext = -1;
+  int32_t lo = 0, Es = 0, cstart = 0, cbase = 0, ctbase = 0, ctnext = -1;
 
-  for (int32_t ct = my_lo; ct < my_hi; ct += step) {
-    if (ct >= ctnext) {  // first group, or a new segment (uniform across the block)
+  for (int32_t ct = my_lo; ct < ct_end; ct += step) {
+    if (ct >= ctnext) {
       while (ct >= seg_ctile[s + 1]) ++s;
       lo = seg_lo[s];
       Es = seg_E[s];
@@ -124,12 +115,6 @@ seg_gather_kernel(const uint32_t* __restrict__ colf, const typename Op::T* __res
       cbase = (int32_t)seg_chunk[s];
       ctbase = seg_ctile[s];
       ctnext = seg_ctile[s + 1];
-      if (STAGED) {
-        __syncthreads();  // every warp is done reading the previous table
-        tn = seg_tab[s];
-        for (int i = tid; i < tn; i += THREADS) tab[i] = x[lo + i];
-        __syncthreads();
-      }
     }
     const int32_t j = (ct - ctbase) * WARPS + w;  // chunk of this warp within the segment
     const int32_t e0 = j * CHUNK;
@@ -138,47 +123,19 @@ seg_gather_kernel(const uint32_t* __restrict__ colf, const typename Op::T* __res
     const int32_t c = cbase + j;
     const int32_t frow = first_row[c];
 
-    // 1. this lane's IPL edges (16-byte streaming loads; colf is padded)
+    // 1. this lane's 8 edges (two 16-byte streaming loads; colf is padded)
     const uint4* p = reinterpret_cast<const uint4*>(colf + cstart + e0 + lane * IPL);
-    uint32_t cf[IPL];
-#pragma unroll
-    for (int q = 0; q < IPL / 4; ++q) {
-      const uint4 t4 = __ldcs(p + q);
-      cf[4 * q] = t4.x;
-      cf[4 * q + 1] = t4.y;
-      cf[4 * q + 2] = t4.z;
-      cf[4 * q + 3] = t4.w;
-    }
+    const uint4 qa = __ldcs(p), qb = __ldcs(p + 1);
+    const uint32_t cf[8] = {qa.x, qa.y, qa.z, qa.w, qb.x, qb.y, qb.z, qb.w};
     T v[IPL];
     uint32_t fl = 0;
-    const int nl = n - lane * IPL;  // valid edges of this lane (may be <= 0 or > IPL)
-    if (nl >= IPL) {  // whole lane valid (every lane but the tail of a segment's last chunk)
+    const int nl = n - lane * IPL;  // valid edges of this lane
 #pragma unroll
-      for (int u = 0; u < IPL; ++u) {
-        const int32_t src = (int32_t)(cf[u] & ~kRowEndFlag);
-        fl |= (cf[u] >> 31) << u;
-        if (STAGED) {
-          const uint32_t off = (uint32_t)(src - lo);
-          v[u] = tab[off < (uint32_t)tn ? off : 0u];
-        } else {
-          v[u] = (uint32_t)src < (uint32_t)nx ? __ldg(x + src) : Op::identity();
-        }
-      }
-    } else {
-#pragma unroll
-      for (int u = 0; u < IPL; ++u) {
-        const bool ok = u < nl;
-        const int32_t src = (int32_t)(cf[u] & ~kRowEndFlag);
-        if (ok) fl |= (cf[u] >> 31) << u;
-        T val = Op::identity();
-        if (STAGED) {
-          const uint32_t off = (uint32_t)(src - lo);
-          if (ok && off < (uint32_t)tn) val = tab[off];
-        } else {
-          if (ok && (uint32_t)src < (uint32_t)nx) val = __ldg(x + src);
-        }
-        v[u] = val;
-      }
+    for (int u = 0; u < IPL; ++u) {
+      const bool ok = u < nl;
+      const int32_t src = lo + (int32_t)(cf[u] & ~kRowEndFlag);
+      if (ok) fl |= (cf[u] >> 31) << u;
+      v[u] = (ok && (uint32_t)src < (uint32_t)nx) ? __ldg(x + src) : Op::identity();
     }
 
     // 2. rows ended before this lane (exclusive warp prefix of flag counts)
@@ -193,16 +150,190 @@ seg_gather_kernel(const uint32_t* __restrict__ colf, const typename Op::T* __res
 
     // 3. sequential fold; rows that start and end in this lane are final
     T acc = Op::identity(), first_val = Op::identity();
-    const int f0 = __ffs(fl) - 1;  // first row end in this lane (-1: none)
+    int nf = 0;
 #pragma unroll
     for (int u = 0; u < IPL; ++u) {
       acc = Op::op(acc, v[u]);
-      if (u == f0) first_val = acc;
-      if (((fl >> u) & 1u) && u != f0) out[row0 + __popc(fl & ((1u << u) - 1u))] = acc;
-      if ((fl >> u) & 1u) acc = Op::identity();
+      if (fl & (1u << u)) {
+        if (nf == 0)
+          first_val = acc;
+        else
+          out[row0 + nf] = acc;
+        ++nf;
+        acc = Op::identity();
+      }
     }
 
     // 4. segmented scan of the open-row parts; completes each lane's first row
+    T S = acc;
+    int h = F > 0;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const T y = __shfl_up_sync(0xffffffffu, S, o);
+      const int g = __shfl_up_sync(0xffffffffu, h, o);
+      if (lane >= o) {
+        if (!h) S = Op::op(y, S);
+        h |= g;
+      }
+    }
+    const T P = __shfl_up_sync(0xffffffffu, S, 1);
+    if (F > 0) out[row0] = lane > 0 ? Op::op(P, first_val) : first_val;
+
+    // 5. the row open at the chunk's end
+    const int total = __shfl_sync(0xffffffffu, incl, 31);
+    const uint32_t lf = __shfl_sync(0xffffffffu, fl, (n - 1) / IPL);
+    if (lane == 31) {
+      const bool closed = (lf >> ((n - 1) % IPL)) & 1u;
+      carry[c] = closed ? Op::identity() : S;
+      carry_row[c] = closed ? -1 : frow + total;
+    }
+  }
+}
+
+// Staged chunk stream: per 512-edge chunk, 512 uint16 segment-local source
+// indices (lane l's 16 edges at bytes [32l, 32l + 32)) then 32 uint16 row-end
+// masks (lane l's at byte 1024 + 2l).
+constexpr int kStagedIPL = 16;
+constexpr int kStagedChunk = 32 * kStagedIPL;  // 512 edges
+constexpr int kStagedChunkBytes = 2 * kStagedChunk + 64;  // 1088
+
+// One thread per (staged chunk, lane): pack its 16 edges.
+__global__ void staged_fill_kernel(const uint32_t* __restrict__ colf,
+                                   const int64_t* __restrict__ seg_chunk,
+                                   const int64_t* __restrict__ seg_cstart,
+                                   const int32_t* __restrict__ seg_E, int m, int64_t nchunks_a,
+                                   uint8_t* __restrict__ cs) {
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < nchunks_a * 32;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t c = t >> 5;
+    const int lane = (int)(t & 31);
+    const int s = last_le(seg_chunk, m + 1, c);
+    const int64_t e_begin = (c - seg_chunk[s]) * kStagedChunk + lane * kStagedIPL;
+    uint32_t packed[kStagedIPL / 2];
+    uint32_t fl = 0;
+#pragma unroll
+    for (int u = 0; u < kStagedIPL; ++u) {
+      const int64_t e = e_begin + u;
+      uint32_t idx = 0;
+      if (e < seg_E[s]) {
+        const uint32_t wv = colf[seg_cstart[s] + e];
+        idx = wv & 0xFFFFu;  // segment-local index (< 65536 for staged segments)
+        fl |= (wv >> 31) << u;
+      }
+      if (u & 1) packed[u >> 1] |= idx << 16; else packed[u >> 1] = idx;
+    }
+    uint8_t* base = cs + c * kStagedChunkBytes;
+    uint4* dst = reinterpret_cast<uint4*>(base + lane * 32);
+    dst[0] = make_uint4(packed[0], packed[1], packed[2], packed[3]);
+    dst[1] = make_uint4(packed[4], packed[5], packed[6], packed[7]);
+    reinterpret_cast<uint16_t*>(base + 2 * kStagedChunk)[lane] = (uint16_t)fl;
+  }
+}
+
+// The staged launch: segments [0, m) are read from a shared-memory copy of
+// their source values.  Each block takes one contiguous run of block-groups
+// (it meets at most a few segments, so it stages at most a few tables).  A
+// warp's chunk is 512 edges from the compressed stream; lane l holds 16.
+template <class Op, int THREADS>
+__global__ void __launch_bounds__(THREADS, 1024 / THREADS)
+staged_gather_kernel(const uint8_t* __restrict__ cs, const typename Op::T* __restrict__ x,
+                     const int32_t* __restrict__ first_row, const int32_t* __restrict__ seg_E,
+                     const int64_t* __restrict__ seg_chunk, const int32_t* __restrict__ seg_ctile,
+                     const int32_t* __restrict__ seg_lo, const int32_t* __restrict__ seg_tab,
+                     int m, int32_t ct_end, typename Op::T* __restrict__ out,
+                     typename Op::T* __restrict__ carry, int32_t* __restrict__ carry_row) {
+  using T = typename Op::T;
+  constexpr int WARPS = THREADS / 32;
+  constexpr int IPL = kStagedIPL;
+  constexpr int CHUNK = kStagedChunk;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* tab = reinterpret_cast<T*>(smem_raw);
+  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  const int32_t per = (ct_end + (int32_t)gridDim.x - 1) / (int32_t)gridDim.x;
+  const int32_t my_lo = (int32_t)blockIdx.x * per;
+  const int32_t my_hi = my_lo + per < ct_end ? my_lo + per : ct_end;
+  if (my_lo >= my_hi) return;
+  int s;
+  {
+    int a = 0, b = m + 1;
+    while (a < b) {
+      const int mid = (a + b) >> 1;
+      if (seg_ctile[mid] <= my_lo) a = mid + 1; else b = mid;
+    }
+    s = a - 1;
+  }
+  int32_t tmax = 0, Es = 0, cbase = 0, ctbase = 0, ctnext = -1;
+
+  for (int32_t ct = my_lo; ct < my_hi; ++ct) {
+    if (ct >= ctnext) {  // first group or a new segment (uniform across the block)
+      while (ct >= seg_ctile[s + 1]) ++s;
+      Es = seg_E[s];
+      cbase = (int32_t)seg_chunk[s];
+      ctbase = seg_ctile[s];
+      ctnext = seg_ctile[s + 1];
+      const int32_t lo = seg_lo[s], tn = seg_tab[s];
+      tmax = tn > 0 ? tn - 1 : 0;
+      __syncthreads();  // every warp is done reading the previous table
+      for (int i = tid; i < tn; i += THREADS) tab[i] = x[lo + i];
+      __syncthreads();
+    }
+    const int32_t j = (ct - ctbase) * WARPS + w;
+    const int32_t e0 = j * CHUNK;
+    if (e0 >= Es) continue;  // warp-uniform
+    const int n = Es - e0 < CHUNK ? Es - e0 : CHUNK;
+    const int32_t c = cbase + j;
+    const int32_t frow = first_row[c];
+
+    // 1. 16 local indices (two 16-byte loads) and the lane's row-end mask
+    const uint8_t* base = cs + (int64_t)c * kStagedChunkBytes;
+    const uint4 qa = __ldcs(reinterpret_cast<const uint4*>(base + lane * 32));
+    const uint4 qb = __ldcs(reinterpret_cast<const uint4*>(base + lane * 32 + 16));
+    uint32_t fl = __ldcs(reinterpret_cast<const unsigned short*>(base + 2 * CHUNK) + lane);
+    const uint32_t pk[8] = {qa.x, qa.y, qa.z, qa.w, qb.x, qb.y, qb.z, qb.w};
+    T v[IPL];
+    if (n == CHUNK) {
+#pragma unroll
+      for (int u = 0; u < IPL; ++u) {
+        const uint32_t idx = (u & 1) ? (pk[u >> 1] >> 16) : (pk[u >> 1] & 0xFFFFu);
+        v[u] = tab[idx < (uint32_t)tmax ? idx : (uint32_t)tmax];
+      }
+    } else {  // a segment's last chunk: lanes past its end hold nothing
+      const int nl = n - lane * IPL;
+#pragma unroll
+      for (int u = 0; u < IPL; ++u) {
+        const uint32_t idx = (u & 1) ? (pk[u >> 1] >> 16) : (pk[u >> 1] & 0xFFFFu);
+        v[u] = u < nl ? tab[idx < (uint32_t)tmax ? idx : (uint32_t)tmax] : Op::identity();
+      }
+      fl &= nl >= IPL ? 0xFFFFu : (nl <= 0 ? 0u : ((1u << nl) - 1u));
+    }
+
+    // 2. rows ended before this lane
+    const int F = __popc(fl);
+    int incl = F;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += y;
+    }
+    const int32_t row0 = frow + (incl - F);
+
+    // 3. sequential fold
+    T acc = Op::identity(), first_val = Op::identity();
+    int nf = 0;
+#pragma unroll
+    for (int u = 0; u < IPL; ++u) {
+      acc = Op::op(acc, v[u]);
+      if (fl & (1u << u)) {
+        if (nf == 0)
+          first_val = acc;
+        else
+          out[row0 + nf] = acc;
+        ++nf;
+        acc = Op::identity();
+      }
+    }
+
+    // 4. segmented scan of the open-row parts
     T S = acc;
     int h = F > 0;
 #pragma unroll
@@ -274,7 +405,7 @@ int seg_plan_build(const int32_t* col, const int64_t* rp, const int32_t* rp32, i
   CG_CUDA(cudaMalloc((void**)&p->seg_ctile, sizeof(int32_t) * (kk + 1)));
   CG_CUDA(cudaMalloc((void**)&p->seg_lo, sizeof(int32_t) * kk));
   CG_CUDA(cudaMalloc((void**)&p->seg_tab, sizeof(int32_t) * kk));
-  CG_CUDA(cudaMalloc((void**)&p->meta, sizeof(int64_t) * 3 * (kk + 1)));
+  CG_CUDA(cudaMalloc((void**)&p->meta, sizeof(int64_t) * 4 * (kk + 1)));
 
   std::vector<int32_t> segE(kk, 0), lo(kk, 0);
   for (int q = 0; q < k; ++q) {
@@ -285,16 +416,19 @@ int seg_plan_build(const int32_t* col, const int64_t* rp, const int32_t* rp32, i
                           cudaMemcpyHostToDevice, s));
   CG_CUDA(cudaMemcpyAsync(p->seg_E, segE.data(), sizeof(int32_t) * k, cudaMemcpyHostToDevice, s));
   CG_CUDA(cudaMemcpyAsync(p->seg_lo, lo.data(), sizeof(int32_t) * k, cudaMemcpyHostToDevice, s));
-  // meta: row_base, edge_base, cstart (k+1 each), kept for chunk indexing and export
+  // meta: row_base, edge_base, cstart, bounds (k+1 each), for chunk indexing and export
   CG_CUDA(cudaMemcpyAsync(p->meta, row_base.data(), sizeof(int64_t) * (k + 1),
                           cudaMemcpyHostToDevice, s));
   CG_CUDA(cudaMemcpyAsync(p->meta + (k + 1), edge_base.data(), sizeof(int64_t) * (k + 1),
                           cudaMemcpyHostToDevice, s));
   CG_CUDA(cudaMemcpyAsync(p->meta + 2 * (k + 1), p->h_cstart.data(), sizeof(int64_t) * (k + 1),
                           cudaMemcpyHostToDevice, s));
+  CG_CUDA(cudaMemcpyAsync(p->meta + 3 * (k + 1), src_bounds.data(), sizeof(int64_t) * (k + 1),
+                          cudaMemcpyHostToDevice, s));
   if (rows > 0) {
     colf_fill_kernel<<<grid_for(rows * 32, 256, 16), 256, 0, s>>>(
-        col, rp, rows, p->meta, p->meta + (k + 1), p->meta + 2 * (k + 1), k, p->colf);
+        col, rp, rows, p->meta, p->meta + (k + 1), p->meta + 2 * (k + 1), p->meta + 3 * (k + 1),
+        k, p->colf);
     CG_LAUNCH_CHECK();
   }
   CG_CUDA(cudaStreamSynchronize(s));  // host vectors above go out of scope
@@ -307,7 +441,7 @@ int seg_plan_configure(SegPlan* p, int threads, int ctas_per_sm, int tab_vertice
     set_error("gather threads must be 512 or 1024 (got %d)", threads);
     return CG_ERR_INVALID_ARG;
   }
-  const int max_ctas = 2048 / threads;
+  const int max_ctas = 1024 / threads;  // the staged kernel holds 64 registers per thread
   if (ctas_per_sm < 1 || ctas_per_sm > max_ctas) {
     set_error("ctas_per_sm must be in [1, %d] for %d threads", max_ctas, threads);
     return CG_ERR_INVALID_ARG;
@@ -316,7 +450,7 @@ int seg_plan_configure(SegPlan* p, int threads, int ctas_per_sm, int tab_vertice
   CG_TRY(device_info(&di));
   const int cap = seg_table_capacity(ctas_per_sm);
   int tab = tab_vertices < 0 ? cap : std::min(tab_vertices, cap);
-  tab &= ~3;
+  tab = std::min(tab, 65536) & ~3;  // staged sources are 16-bit segment-local indices
   const int k = p->k;
   // staged prefix: leading segments that fit the table and carry enough
   // edges (>= 4 per source) for staging them in shared memory to pay
@@ -329,9 +463,7 @@ int seg_plan_configure(SegPlan* p, int threads, int ctas_per_sm, int tab_vertice
     tabmax = std::max(tabmax, size);
     ++m;
   }
-  // one block per SM of 1024 threads has registers for 16 edges per lane
-  const int ipl_a = (threads == 1024 && ctas_per_sm == 1) ? 16 : 8;
-  const int chunk_a = 32 * ipl_a, chunk_b = 32 * 8;
+  const int chunk_a = kStagedChunk, chunk_b = 256;
   const int warps_a = threads / 32, warps_b = 1024 / 32;
   std::vector<int64_t> chunk(k + 1, 0);
   std::vector<int32_t> ctile(k + 1, 0), tn(k > 0 ? k : 1, 0);
@@ -357,6 +489,14 @@ int seg_plan_configure(SegPlan* p, int threads, int ctas_per_sm, int tab_vertice
     CG_CUDA(cudaMalloc((void**)&p->carry_row, sizeof(int32_t) * nc));
     p->chunk_cap = nchunks;
   }
+  const int64_t cs_bytes = chunk[m] * kStagedChunkBytes;
+  if (cs_bytes > p->cs_cap) {
+    cudaFree(p->cs);
+    p->cs = nullptr;
+    p->cs_cap = 0;
+    CG_CUDA(cudaMalloc((void**)&p->cs, (size_t)cs_bytes));
+    p->cs_cap = cs_bytes;
+  }
   CG_CUDA(cudaMemcpyAsync(p->seg_chunk, chunk.data(), sizeof(int64_t) * (k + 1),
                           cudaMemcpyHostToDevice, s));
   CG_CUDA(cudaMemcpyAsync(p->seg_ctile, ctile.data(), sizeof(int32_t) * (k + 1),
@@ -370,10 +510,15 @@ int seg_plan_configure(SegPlan* p, int threads, int ctas_per_sm, int tab_vertice
         p->first_row);
     CG_LAUNCH_CHECK();
   }
+  if (chunk[m] > 0) {
+    staged_fill_kernel<<<grid_for(chunk[m] * 32, 256), 256, 0, s>>>(
+        p->colf, p->seg_chunk, p->seg_cstart, p->seg_E, m, chunk[m], p->cs);
+    CG_LAUNCH_CHECK();
+  }
   CG_CUDA(cudaStreamSynchronize(s));  // host vectors go out of scope
   p->threads = threads;
   p->ctas_per_sm = ctas_per_sm;
-  p->ipl_a = ipl_a;
+  p->ipl_a = kStagedIPL;
   p->tab_cap = (int)((tabmax + 3) & ~3LL);
   p->table_request = tab;
   p->m = m;
@@ -389,6 +534,7 @@ int seg_plan_configure(SegPlan* p, int threads, int ctas_per_sm, int tab_vertice
 
 void seg_plan_free(SegPlan* p) {
   cudaFree(p->colf);
+  cudaFree(p->cs);
   cudaFree(p->meta);
   cudaFree(p->seg_cstart);
   cudaFree(p->seg_E);
@@ -402,32 +548,33 @@ void seg_plan_free(SegPlan* p) {
   *p = SegPlan();
 }
 
-int64_t seg_plan_bytes(const SegPlan& p) { return 4 * p.colf_len + 12 * p.nchunks + 40 * p.k; }
+int64_t seg_plan_bytes(const SegPlan& p) {
+  return 4 * p.colf_len + p.cs_cap + 12 * p.chunk_cap + 72 * (int64_t)p.k;
+}
 
 int seg_plan_export_col(const SegPlan& p, const int32_t* rp, int32_t* col, cudaStream_t s) {
   if (p.rows == 0) return CG_OK;
   const int k = p.k;
   export_col_kernel<<<grid_for(p.rows * 32, 256, 16), 256, 0, s>>>(
-      p.colf, rp, p.rows, p.meta, p.meta + (k + 1), p.meta + 2 * (k + 1), k, col);
+      p.colf, rp, p.rows, p.meta, p.meta + (k + 1), p.meta + 2 * (k + 1), p.meta + 3 * (k + 1), k,
+      col);
   CG_LAUNCH_CHECK();
   CG_CUDA(cudaStreamSynchronize(s));
   return CG_OK;
 }
 
-template <class Op, int THREADS, bool STAGED, int IPL>
-static int launch_seg_gather(const SegPlan& p, const typename Op::T* x, int32_t nx,
-                             typename Op::T* out, int32_t ct_begin, int32_t ct_end, int grid,
-                             int tab_cap, cudaStream_t s) {
-  if (ct_end <= ct_begin) return CG_OK;
+template <class Op, int THREADS>
+static int launch_staged(const SegPlan& p, const typename Op::T* x, typename Op::T* out,
+                         cudaStream_t s) {
   using T = typename Op::T;
-  const size_t smem = STAGED ? (size_t)tab_cap * sizeof(T) : 0;
-  auto fn = seg_gather_kernel<Op, THREADS, STAGED, IPL>;
+  const size_t smem = (size_t)p.tab_cap * sizeof(T);
+  auto fn = staged_gather_kernel<Op, THREADS>;
   if (smem > 48 * 1024)
     CG_CUDA(cudaFuncSetAttribute((const void*)fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)smem));
-  fn<<<grid, THREADS, smem, s>>>(p.colf, x, nx, p.first_row, p.seg_cstart, p.seg_E, p.seg_chunk,
-                                 p.seg_ctile, p.seg_lo, p.seg_tab, p.k, ct_begin, ct_end, out,
-                                 reinterpret_cast<T*>(p.carry), p.carry_row);
+  fn<<<p.grid, THREADS, smem, s>>>(p.cs, x, p.first_row, p.seg_E, p.seg_chunk, p.seg_ctile,
+                                   p.seg_lo, p.seg_tab, p.m, p.ct_split, out,
+                                   reinterpret_cast<T*>(p.carry), p.carry_row);
   CG_LAUNCH_CHECK();
   return CG_OK;
 }
@@ -438,20 +585,19 @@ int run_seg_gather(const SegPlan& p, const typename Op::T* x, int32_t nx, typena
   if (p.nchunks == 0) return CG_OK;
   using T = typename Op::T;
   // staged segments [0, m): read from a shared-memory copy
-  if (p.m > 0) {
-    if (p.threads == 1024 && p.ipl_a == 16)
-      CG_TRY((launch_seg_gather<Op, 1024, true, 16>(p, x, nx, out, 0, p.ct_split, p.grid,
-                                                    p.tab_cap, s)));
-    else if (p.threads == 1024)
-      CG_TRY((launch_seg_gather<Op, 1024, true, 8>(p, x, nx, out, 0, p.ct_split, p.grid,
-                                                   p.tab_cap, s)));
+  if (p.m > 0 && p.ct_split > 0) {
+    if (p.threads == 1024)
+      CG_TRY((launch_staged<Op, 1024>(p, x, out, s)));
     else
-      CG_TRY((launch_seg_gather<Op, 512, true, 8>(p, x, nx, out, 0, p.ct_split, p.grid,
-                                                  p.tab_cap, s)));
+      CG_TRY((launch_staged<Op, 512>(p, x, out, s)));
   }
   // the rest through L1/L2: no shared memory, so the whole on-chip store is L1
-  CG_TRY((launch_seg_gather<Op, 1024, false, 8>(p, x, nx, out, p.ct_split, (int32_t)p.n_ctiles,
-                                                p.grid_l2, 0, s)));
+  if (p.n_ctiles > p.ct_split) {
+    seg_gather_kernel<Op, 1024><<<p.grid_l2, 1024, 0, s>>>(
+        p.colf, x, nx, p.first_row, p.seg_cstart, p.seg_E, p.seg_chunk, p.seg_ctile, p.seg_lo,
+        p.k, p.ct_split, (int32_t)p.n_ctiles, out, reinterpret_cast<T*>(p.carry), p.carry_row);
+    CG_LAUNCH_CHECK();
+  }
   carry_fixup_kernel<Op><<<grid_for(p.nchunks, 256, 4), 256, 0, s>>>(
       reinterpret_cast<const T*>(p.carry), p.carry_row, p.nchunks, p.rows, out);
   CG_LAUNCH_CHECK();

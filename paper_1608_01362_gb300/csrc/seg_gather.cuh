@@ -38,7 +38,9 @@ constexpr int kMaxChunkEdges = 512;  // 32 lanes x 16 edges (staged launch, 1 bl
 struct SegPlan {
   int k = 0;
   int64_t E = 0, rows = 0, nchunks = 0;
-  uint32_t* colf = nullptr;        // [colf_len] flagged, padded sources
+  uint32_t* colf = nullptr;        // [colf_len] flagged, padded segment-local sources
+  uint8_t* cs = nullptr;           // staged chunk stream (16-bit local indices + masks)
+  int64_t cs_cap = 0;
   int64_t colf_len = 0;
   int64_t* seg_cstart = nullptr;   // [k]   first colf entry of each segment
   int32_t* seg_E = nullptr;        // [k]   edges of each segment
@@ -49,7 +51,7 @@ struct SegPlan {
   int32_t* first_row = nullptr;    // [nchunks] subgraph row of each chunk's first edge
   void* carry = nullptr;           // [nchunks] 4-byte values
   int32_t* carry_row = nullptr;    // [nchunks]
-  int64_t* meta = nullptr;         // [3(k+1)] row_base, edge_base, cstart on the device
+  int64_t* meta = nullptr;         // [4(k+1)] row_base, edge_base, cstart, bounds (device)
   const int32_t* rp32 = nullptr;   // subgraph row starts (owned by the handle)
   int64_t chunk_cap = 0;           // capacity of first_row / carry / carry_row
   std::vector<int64_t> h_cstart, src_bounds, edge_base, row_base;

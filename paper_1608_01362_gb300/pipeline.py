@@ -84,7 +84,7 @@ def plan_bounds(graph: Graph, ctas_per_sm: int = 1, min_avg_degree: float = 64.0
     return C.pr_plan_bounds(graph.outdeg, H, min_avg_degree, max_global_vertices)
 
 
-GATHER_SHAPES = ((1024, 1), (1024, 2), (512, 4))  # (threads, blocks per SM)
+GATHER_SHAPES = ((1024, 1), (512, 2))  # staged gather (threads, blocks per SM)
 
 
 class SegmentedPageRank(_PageRankBase):
@@ -140,14 +140,14 @@ def time_iterations(pr, iterations: int = 3, damping: float = 0.85, reps: int = 
     return times[len(times) // 2]
 
 
-def default_candidates(uniform_k=(1, 4), shapes=GATHER_SHAPES, min_deg=(64.0, 256.0, 1024.0),
-                       tables=(-1, 8192, 0)):
+def default_candidates(uniform_k=(1, 4), shapes=GATHER_SHAPES, min_deg=(4.0, 16.0, 64.0, 256.0),
+                       tables=(-1, 0)):
     """Autotuner search space: the paper's uniform split into k segments, and
     the GPU plan (shared-memory segments over the hot head, L2 segments over
     the rest), at several gather launch shapes, shared-table sizes and
     staging thresholds.  A smaller table leaves more of the SM's on-chip
     memory to the L1 cache, which serves the reads the table does not."""
-    out = [{"kind": "uniform", "k": k, "threads": 1024, "ctas": 2, "table": tb}
+    out = [{"kind": "uniform", "k": k, "threads": 1024, "ctas": 1, "table": tb}
            for k in uniform_k for tb in tables]
     out += [{"kind": "plan", "threads": t, "ctas": c, "min_avg_degree": m, "table": -1}
             for (t, c) in shapes for m in min_deg]

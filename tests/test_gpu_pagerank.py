@@ -295,7 +295,7 @@ def test_deterministic_repeat(C, torch_mod, rmat16):
 # ------------------------------------------------------------------ shared-table / planned segments
 
 @pytest.mark.parametrize("threads,ctas,table", [(1024, 1, 0), (1024, 1, 100), (1024, 1, -1),
-                                               (1024, 2, -1), (512, 1, 5000), (512, 4, -1)])
+                                               (512, 2, -1), (512, 1, 5000), (512, 2, 300)])
 def test_gather_table_configs(C, torch_mod, rmat16, rmat16_oracle, threads, ctas, table):
     """The shared-memory table (whole segment or its hot head) and the launch
     shape change where values are read from, not the result."""
@@ -318,10 +318,11 @@ def test_gather_config_rejects_bad_shape(C, torch_mod, rmat16):
     from paper_1608_01362_gb300 import pipeline as P
     graph = P.Graph(rmat16.offsets, rmat16.src, cluster_mode=0)
     pr = P.SegmentedPageRank(graph, 2)
+    assert pr.info["gather_threads"] == 1024 and pr.info["ctas_per_sm"] == 1
     with pytest.raises(C.CagraError, match="threads"):
         C.pr_set_gather_config(pr.seg, 256, 1, -1)
     with pytest.raises(C.CagraError, match="ctas_per_sm"):
-        C.pr_set_gather_config(pr.seg, 1024, 3, -1)
+        C.pr_set_gather_config(pr.seg, 1024, 2, -1)
 
 
 def test_planned_bounds(C, torch_mod, rmat16, rmat16_oracle):
@@ -339,7 +340,7 @@ def test_planned_bounds(C, torch_mod, rmat16, rmat16_oracle):
     assert np.all(np.diff(b[m:]) <= 20000)
     if b[m] + 2048 <= graph.V:
         assert od[b[m]:b[m] + 2048].sum() < 8 * 2048
-    pr = P.SegmentedPageRank(graph, bounds=b, table_vertices=2048, ctas_per_sm=2)
+    pr = P.SegmentedPageRank(graph, bounds=b, threads=512, ctas_per_sm=2, table_vertices=2048)
     assert pr.info["table_vertices"] == 2048 and pr.info["staged_segments"] >= m
     rank, _ = pr.run(20)
     assert rel_l1(rank.cpu().numpy(), rmat16_oracle[0]) <= TOL_L1
