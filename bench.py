@@ -359,6 +359,8 @@ def main():
                    "V": V, "E": E, "iterations_per_step": ITERS, "damping": DAMPING,
                    "segments": best_k, "merge_block": args.merge_block, "q": info["q"],
                    "segmenting": best, "table_vertices": info["table_vertices"],
+                   "staged_segments": info["staged_segments"],
+                   "staged_edges": info["staged_edges"],
                    "ctas_per_sm": info["ctas_per_sm"],
                    "clustering": "descending out-degree (stable)",
                    "l2_policy": "inputs larger than L2 (2.1 GB edge stream per iteration)",

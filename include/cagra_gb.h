@@ -124,6 +124,7 @@ typedef struct {
   int32_t ctas_per_sm;   /* staged-gather blocks per SM */
   int32_t gather_threads; /* threads per staged-gather block */
   int32_t staged_segments; /* leading segments served from shared memory */
+  int64_t staged_edges;  /* edges of those segments */
 } cg_segmented_info;
 
 /*

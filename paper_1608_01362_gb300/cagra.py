@@ -42,7 +42,8 @@ class SegInfo(ctypes.Structure):
                 ("rows", ctypes.c_int64), ("q", ctypes.c_double),
                 ("device_bytes", ctypes.c_int64), ("gather_tiles", ctypes.c_int64),
                 ("table_vertices", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32),
-                ("gather_threads", ctypes.c_int32), ("staged_segments", ctypes.c_int32)]
+                ("gather_threads", ctypes.c_int32), ("staged_segments", ctypes.c_int32),
+                ("staged_edges", ctypes.c_int64)]
 
 
 def load(path: str | None = None):

@@ -190,6 +190,47 @@ seg_gather_kernel(const uint32_t* __restrict__ colf, const typename Op::T* __res
   }
 }
 
+// Copy n values into shared memory with many independent loads in flight per
+// thread (16-byte loads when the source is 16-byte aligned), so staging a
+// table costs a few memory round trips rather than one per element.
+template <typename T, int THREADS>
+__device__ __forceinline__ void stage_table(const T* __restrict__ src, int n, T* dst, int tid) {
+  static_assert(sizeof(T) == 4, "4-byte values");
+  if ((reinterpret_cast<uintptr_t>(src) & 15) == 0) {
+    const int n4 = n >> 2;
+    const uint4* s4 = reinterpret_cast<const uint4*>(src);
+    uint4* d4 = reinterpret_cast<uint4*>(dst);
+    for (int b = 0; b < n4; b += THREADS * 4) {
+      uint4 r[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int i = b + u * THREADS + tid;
+        if (i < n4) r[u] = __ldg(s4 + i);
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int i = b + u * THREADS + tid;
+        if (i < n4) d4[i] = r[u];
+      }
+    }
+    for (int i = (n4 << 2) + tid; i < n; i += THREADS) dst[i] = src[i];
+  } else {
+    for (int b = 0; b < n; b += THREADS * 8) {
+      T r[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int i = b + u * THREADS + tid;
+        if (i < n) r[u] = __ldg(src + i);
+      }
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int i = b + u * THREADS + tid;
+        if (i < n) dst[i] = r[u];
+      }
+    }
+  }
+}
+
 // Staged chunk stream: per 512-edge chunk, 512 uint16 segment-local source
 // indices (lane l's 16 edges at bytes [32l, 32l + 32)) then 32 uint16 row-end
 // masks (lane l's at byte 1024 + 2l).
@@ -274,7 +315,7 @@ staged_gather_kernel(const uint8_t* __restrict__ cs, const typename Op::T* __res
       const int32_t lo = seg_lo[s], tn = seg_tab[s];
       tmax = tn > 0 ? tn - 1 : 0;
       __syncthreads();  // every warp is done reading the previous table
-      for (int i = tid; i < tn; i += THREADS) tab[i] = x[lo + i];
+      stage_table<T, THREADS>(x + lo, tn, tab, tid);
       __syncthreads();
     }
     const int32_t j = (ct - ctbase) * WARPS + w;

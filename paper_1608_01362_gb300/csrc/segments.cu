@@ -498,6 +498,7 @@ int cg_segmented_get_info(const cg_segmented* g, cg_segmented_info* info) {
   info->gather_tiles = g->plan.nchunks;
   info->table_vertices = g->plan.tab_cap;
   info->staged_segments = g->plan.m;
+  info->staged_edges = g->plan.m > 0 ? g->edge_base[g->plan.m] : 0;
   info->ctas_per_sm = g->plan.ctas_per_sm;
   info->gather_threads = g->plan.threads;
   return CG_OK;
