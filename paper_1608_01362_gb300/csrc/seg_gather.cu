@@ -281,32 +281,33 @@ staged_gather_kernel(const uint8_t* __restrict__ cs, const typename Op::T* __res
                      const int32_t* __restrict__ first_row, const int32_t* __restrict__ seg_E,
                      const int64_t* __restrict__ seg_chunk, const int32_t* __restrict__ seg_ctile,
                      const int32_t* __restrict__ seg_lo, const int32_t* __restrict__ seg_tab,
-                     int m, int32_t ct_end, typename Op::T* __restrict__ out,
-                     typename Op::T* __restrict__ carry, int32_t* __restrict__ carry_row) {
+                     int m, int32_t ct_end, int32_t piece, unsigned* __restrict__ next_piece,
+                     typename Op::T* __restrict__ out, typename Op::T* __restrict__ carry,
+                     int32_t* __restrict__ carry_row) {
   using T = typename Op::T;
   constexpr int WARPS = THREADS / 32;
   constexpr int IPL = kStagedIPL;
   constexpr int CHUNK = kStagedChunk;
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ int32_t s_piece;
   T* tab = reinterpret_cast<T*>(smem_raw);
   const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
-  const int32_t per = (ct_end + (int32_t)gridDim.x - 1) / (int32_t)gridDim.x;
-  const int32_t my_lo = (int32_t)blockIdx.x * per;
-  const int32_t my_hi = my_lo + per < ct_end ? my_lo + per : ct_end;
-  if (my_lo >= my_hi) return;
-  int s;
-  {
-    int a = 0, b = m + 1;
-    while (a < b) {
-      const int mid = (a + b) >> 1;
-      if (seg_ctile[mid] <= my_lo) a = mid + 1; else b = mid;
-    }
-    s = a - 1;
-  }
+  int s = 0;
   int32_t tmax = 0, Es = 0, cbase = 0, ctbase = 0, ctnext = -1;
 
-  for (int32_t ct = my_lo; ct < my_hi; ++ct) {
-    if (ct >= ctnext) {  // first group or a new segment (uniform across the block)
+  // Pieces of `piece` consecutive block-groups are handed out in increasing
+  // order by an atomic counter: a block's groups only move forward (so it
+  // stages each segment's table at most once) and a slow block simply takes
+  // fewer pieces.
+  for (;;) {
+    __syncthreads();  // everyone is done with the previous piece's s_piece
+    if (tid == 0) s_piece = (int32_t)atomicAdd(next_piece, 1u);
+    __syncthreads();
+    const int32_t my_lo = s_piece * piece;
+    if (my_lo >= ct_end) break;
+    const int32_t my_hi = my_lo + piece < ct_end ? my_lo + piece : ct_end;
+    for (int32_t ct = my_lo; ct < my_hi; ++ct) {
+    if (ct >= ctnext) {  // a new segment (uniform across the block)
       while (ct >= seg_ctile[s + 1]) ++s;
       Es = seg_E[s];
       cbase = (int32_t)seg_chunk[s];
@@ -397,6 +398,7 @@ staged_gather_kernel(const uint8_t* __restrict__ cs, const typename Op::T* __res
       carry[c] = closed ? Op::identity() : S;
       carry_row[c] = closed ? -1 : frow + total;
     }
+    }
   }
 }
 
@@ -412,6 +414,7 @@ int seg_table_capacity(int ctas) {
   if (ctas < 1) ctas = 1;
   int64_t per = (int64_t)sm_smem / ctas - reserved;
   if (per > optin) per = optin;
+  per -= 128;  // the gather kernels' own static shared memory
   if (per <= 0) return 0;
   return (int)((per / 4) & ~31LL);
 }
@@ -568,12 +571,16 @@ int seg_plan_configure(SegPlan* p, int threads, int ctas_per_sm, int tab_vertice
   p->n_ctiles = ctile[k];
   p->grid = (int)std::max<int64_t>(
       1, std::min<int64_t>(p->ct_split, (int64_t)di.sm_count * ctas_per_sm));
+  // about eight pieces per block: balance without many table reloads
+  p->piece = (int32_t)std::max<int64_t>(1, ceil_div(p->ct_split, 8LL * p->grid));
+  if (!p->counter) CG_CUDA(cudaMalloc((void**)&p->counter, sizeof(unsigned)));
   p->grid_l2 = (int)std::max<int64_t>(
       1, std::min<int64_t>(p->n_ctiles - p->ct_split, (int64_t)di.sm_count * 2));
   return CG_OK;
 }
 
 void seg_plan_free(SegPlan* p) {
+  cudaFree(p->counter);
   cudaFree(p->colf);
   cudaFree(p->cs);
   cudaFree(p->meta);
@@ -610,11 +617,12 @@ static int launch_staged(const SegPlan& p, const typename Op::T* x, typename Op:
   using T = typename Op::T;
   const size_t smem = (size_t)p.tab_cap * sizeof(T);
   auto fn = staged_gather_kernel<Op, THREADS>;
+  CG_CUDA(cudaMemsetAsync(p.counter, 0, sizeof(unsigned), s));
   if (smem > 48 * 1024)
     CG_CUDA(cudaFuncSetAttribute((const void*)fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)smem));
   fn<<<p.grid, THREADS, smem, s>>>(p.cs, x, p.first_row, p.seg_E, p.seg_chunk, p.seg_ctile,
-                                   p.seg_lo, p.seg_tab, p.m, p.ct_split, out,
+                                   p.seg_lo, p.seg_tab, p.m, p.ct_split, p.piece, p.counter, out,
                                    reinterpret_cast<T*>(p.carry), p.carry_row);
   CG_LAUNCH_CHECK();
   return CG_OK;

@@ -64,6 +64,8 @@ struct SegPlan {
   int32_t ct_split = 0;     // first block-group of the unstaged segments
   int64_t n_ctiles = 0;
   int grid = 0;             // staged launch blocks
+  int32_t piece = 1;        // block-groups per work piece of the staged launch
+  unsigned* counter = nullptr;  // next staged work piece
   int grid_l2 = 0;          // unstaged launch blocks (1024 threads, 2 per SM)
 };
 
