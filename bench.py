@@ -190,7 +190,7 @@ def main():
     ap.add_argument("--table", type=int, default=0, help="shared table entries (with --k)")
     ap.add_argument("--plan", type=float, default=0.0,
                     help="use planned bounds with this min_avg_degree (skips the autotuner)")
-    ap.add_argument("--merge-block", type=int, default=4096)
+    ap.add_argument("--merge-block", type=int, default=512)
     ap.add_argument("--sweep", action="store_true", help="k = 1..64 sweep table")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()

@@ -138,7 +138,8 @@ typedef struct {
  * cache-aware merge for blocks of merge_block destinations (Algorithm 4).
  * The handle also owns the intermediate buffers (intermBuf) and the tiling
  * of the gather.  Inputs: device CSR as in the conventions; 1 <= k <= 1024;
- * 1 <= merge_block <= 12288.  The call synchronizes the stream (it reads
+ * 1 <= merge_block <= 6144 (a merge block's accumulator lives in one warp's
+ * share of shared memory; 512 is a good default).  The call synchronizes the stream (it reads
  * segment sizes on the host).  Errors: CG_ERR_INVALID_ARG, CG_ERR_OOM,
  * CG_ERR_CUDA.  Empty segments are legal.
  */
@@ -222,8 +223,9 @@ int cg_seg_gather(const cg_segmented *seg, int32_t op, const void *dev_x,
 
 /*
  * Cache-aware merge alone (Algorithm 4, Section III-C): for each block of
- * merge_block destinations, out[v] = identity (0 / INT32_MAX), then for each
- * segment in ascending order, for its rows i in the block,
+ * merge_block destinations (one warp per block, its accumulator in shared
+ * memory), out[v] = identity (0 / INT32_MAX), then for each segment in
+ * ascending order, for its rows i in the block,
  * out[idx_map[i]] = op(out[idx_map[i]], interm[i]).  dev_interm: rows
  * entries; dev_out: V entries.
  */

@@ -184,7 +184,7 @@ class Segmented:
         return {f: getattr(inf, f) for f, _ in SegInfo._fields_}
 
 
-def pr_build_segments(offsets, src, num_segments: int, bounds=None, merge_block: int = 4096,
+def pr_build_segments(offsets, src, num_segments: int, bounds=None, merge_block: int = 512,
                       stream=None) -> Segmented:
     import torch
     _dtype_check(offsets, torch.int64, "offsets"); _dtype_check(src, torch.int32, "src")

@@ -19,7 +19,6 @@
 namespace cg {
 namespace {
 
-constexpr int kMergeThreads = 256;
 
 struct PrArgs {
   const float* inv;
@@ -37,16 +36,85 @@ struct PrArgs {
   int32_t V;
 };
 
-// Vertex update for destinations [v0, v0+n) whose gathered sums sit in
-// acc[0..n); accumulates the FP64 partials and runs the last-block reduction.
-template <int THREADS>
-__device__ __forceinline__ void vertex_update_block(const float* acc, int64_t v0, int n,
-                                                    const PrArgs& a, double D) {
-  __shared__ double sh[32];
-  __shared__ bool s_last;
-  const float Dv = (float)(D * a.inv_V);
-  float dpart = 0.0f, rpart = 0.0f;  // <= B/THREADS terms per thread, then FP64
-  for (int i = threadIdx.x; i < n; i += THREADS) {
+// ---------------------------------------------------------------------------
+// Cache-aware merge (Algorithm 4).  Each warp owns one merge block of B
+// destinations (a shared-memory accumulator of B values) and walks the
+// segments in ascending order: for segment s it adds the block's rows
+// [blk[s][b], blk[s][b+1]) of intermBuf into acc[idx_map[i] - b*B].  Inside
+// one segment the destinations are distinct, so lanes never collide; the
+// warp synchronises between segments, which keeps the per-destination order
+// fixed (deterministic).  The loads of segment s+1 are issued before the
+// adds of segment s, and no block-wide barrier is involved, so the k segments
+// do not serialise k memory round trips per block.
+// ---------------------------------------------------------------------------
+constexpr int kMergeWarps = 8;
+
+template <class Op>
+__device__ __forceinline__ void warp_merge(const int32_t* __restrict__ blk,
+                                           const int32_t* __restrict__ idx_map,
+                                           const typename Op::T* __restrict__ interm, int k,
+                                           int nb, int64_t mb, int64_t v0, int n,
+                                           typename Op::T* acc) {
+  using T = typename Op::T;
+  const int lane = threadIdx.x & 31;
+  for (int i = lane; i < n; i += 32) acc[i] = Op::identity();
+  __syncwarp();
+  for (int s0 = 0; s0 < k; s0 += 32) {
+    const int ls = s0 + lane;
+    int32_t lo = 0, hi = 0;
+    if (ls < k) {
+      lo = __ldg(blk + (int64_t)ls * (nb + 1) + mb);
+      hi = __ldg(blk + (int64_t)ls * (nb + 1) + mb + 1);
+    }
+    const int cnt = k - s0 < 32 ? k - s0 : 32;
+    int32_t i0 = __shfl_sync(0xffffffffu, lo, 0) + lane;
+    int32_t h0 = __shfl_sync(0xffffffffu, hi, 0);
+    int32_t d0 = 0;
+    T x0 = Op::identity();
+    if (i0 < h0) {
+      d0 = __ldcs(idx_map + i0);
+      x0 = __ldcs(interm + i0);
+    }
+    for (int t = 0; t < cnt; ++t) {
+      // issue segment t+1's first loads before applying segment t
+      int32_t i1 = 0, h1 = 0, d1 = 0;
+      T x1 = Op::identity();
+      if (t + 1 < cnt) {
+        i1 = __shfl_sync(0xffffffffu, lo, t + 1) + lane;
+        h1 = __shfl_sync(0xffffffffu, hi, t + 1);
+        if (i1 < h1) {
+          d1 = __ldcs(idx_map + i1);
+          x1 = __ldcs(interm + i1);
+        }
+      }
+      if (i0 < h0) {
+        const int64_t lv = (int64_t)d0 - v0;
+        if ((uint64_t)lv < (uint64_t)n) acc[lv] = Op::op(acc[lv], x0);
+      }
+      for (int32_t i = i0 + 32; i < h0; i += 32) {  // segments with more than 32 rows here
+        const int64_t lv = (int64_t)__ldcs(idx_map + i) - v0;
+        const T x = __ldcs(interm + i);
+        if ((uint64_t)lv < (uint64_t)n) acc[lv] = Op::op(acc[lv], x);
+      }
+      __syncwarp();
+      i0 = i1;
+      h0 = h1;
+      d0 = d1;
+      x0 = x1;
+    }
+  }
+  __syncwarp();
+}
+
+// Vertex update (Algorithm 5's VertexUpdate, normalised) for one warp's
+// destinations [v0, v0+n) with sums in acc; returns the warp's FP64 partial
+// sums of the dangling mass and of the L1 residual (valid in lane 0).
+__device__ __forceinline__ void warp_vertex_update(const float* acc, int64_t v0, int n,
+                                                   const PrArgs& a, float Dv, double* dsum,
+                                                   double* rsum) {
+  const int lane = threadIdx.x & 31;
+  float dpart = 0.0f, rpart = 0.0f;  // <= B/32 terms per lane, then FP64
+  for (int i = lane; i < n; i += 32) {
     const int64_t v = v0 + i;
     const float r = a.base + a.d * (acc[i] + Dv);
     const float iv = __ldcs(a.inv + v);
@@ -56,9 +124,28 @@ __device__ __forceinline__ void vertex_update_block(const float* acc, int64_t v0
     if (iv == 0.0f) dpart += r;
     rpart += fabsf(r - old);
   }
-  const double bd = block_sum<double, THREADS>((double)dpart, sh);
-  const double br = block_sum<double, THREADS>((double)rpart, sh);
+  *dsum = warp_sum((double)dpart);
+  *rsum = warp_sum((double)rpart);
+}
+
+// Per-block FP64 partials, then the last block to finish reduces all
+// partials in a fixed order (no float atomics: deterministic).
+__device__ __forceinline__ void block_finish(double dsum, double rsum, const PrArgs& a) {
+  __shared__ double s_d[kMergeWarps], s_r[kMergeWarps];
+  __shared__ double sh[32];
+  __shared__ bool s_last;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  if (lane == 0) {
+    s_d[w] = dsum;
+    s_r[w] = rsum;
+  }
+  __syncthreads();
   if (threadIdx.x == 0) {
+    double bd = 0.0, br = 0.0;
+    for (int q = 0; q < kMergeWarps; ++q) {
+      bd += s_d[q];
+      br += s_r[q];
+    }
     a.partials[2 * blockIdx.x] = bd;
     a.partials[2 * blockIdx.x + 1] = br;
     __threadfence();
@@ -69,12 +156,12 @@ __device__ __forceinline__ void vertex_update_block(const float* acc, int64_t v0
   if (s_last) {
     __threadfence();
     double sd = 0.0, sr = 0.0;
-    for (int q = threadIdx.x; q < (int)gridDim.x; q += THREADS) {
+    for (int q = threadIdx.x; q < (int)gridDim.x; q += kMergeWarps * 32) {
       sd += __ldcg(a.partials + 2 * q);
       sr += __ldcg(a.partials + 2 * q + 1);
     }
-    sd = block_sum<double, THREADS>(sd, sh);
-    sr = block_sum<double, THREADS>(sr, sh);
+    sd = block_sum<double, kMergeWarps * 32>(sd, sh);
+    sr = block_sum<double, kMergeWarps * 32>(sr, sh);
     if (threadIdx.x == 0) {
       *a.D_out = sd;
       if (a.resid_out) *a.resid_out = sr;
@@ -84,65 +171,59 @@ __device__ __forceinline__ void vertex_update_block(const float* acc, int64_t v0
 }
 
 // Cache-aware merge (Algorithm 4) fused with the vertex update.
-template <int THREADS>
-__global__ void __launch_bounds__(THREADS)
+__global__ void __launch_bounds__(kMergeWarps * 32)
 merge_update_kernel(const int32_t* __restrict__ blk, const int32_t* __restrict__ idx_map,
                     const float* __restrict__ interm, int k, int nb, int B, PrArgs a) {
-  extern __shared__ float acc[];
+  extern __shared__ float acc_all[];
   const double D = *a.D_in;
-  const int64_t v0 = (int64_t)blockIdx.x * B;
-  const int n = (int)((a.V - v0) < B ? (a.V - v0) : B);
-  for (int i = threadIdx.x; i < n; i += THREADS) acc[i] = 0.0f;
-  __syncthreads();
-  for (int s = 0; s < k; ++s) {
-    const int32_t lo = blk[(int64_t)s * (nb + 1) + blockIdx.x];
-    const int32_t hi = blk[(int64_t)s * (nb + 1) + blockIdx.x + 1];
-    for (int32_t i = lo + threadIdx.x; i < hi; i += THREADS) {
-      const int64_t lv = (int64_t)__ldcs(idx_map + i) - v0;
-      const float x = __ldcs(interm + i);
-      if ((uint64_t)lv < (uint64_t)n) acc[lv] += x;  // distinct destinations inside a segment
-    }
-    __syncthreads();
+  const int w = threadIdx.x >> 5;
+  const int64_t mb = (int64_t)blockIdx.x * kMergeWarps + w;
+  double dsum = 0.0, rsum = 0.0;
+  if (mb < nb) {
+    float* acc = acc_all + (int64_t)w * B;
+    const int64_t v0 = mb * B;
+    const int n = (int)((a.V - v0) < B ? (a.V - v0) : B);
+    warp_merge<SumF32>(blk, idx_map, interm, k, nb, mb, v0, n, acc);
+    warp_vertex_update(acc, v0, n, a, (float)(D * a.inv_V), &dsum, &rsum);
   }
-  vertex_update_block<THREADS>(acc, v0, n, a, D);
+  block_finish(dsum, rsum, a);
 }
 
 // Plain path: the gathered sums are already dense.
-template <int THREADS>
-__global__ void __launch_bounds__(THREADS)
-dense_update_kernel(const float* __restrict__ sums, int B, PrArgs a) {
-  extern __shared__ float acc[];
+__global__ void __launch_bounds__(kMergeWarps * 32)
+dense_update_kernel(const float* __restrict__ sums, int B, int nb, PrArgs a) {
+  extern __shared__ float acc_all[];
   const double D = *a.D_in;
-  const int64_t v0 = (int64_t)blockIdx.x * B;
-  const int n = (int)((a.V - v0) < B ? (a.V - v0) : B);
-  for (int i = threadIdx.x; i < n; i += THREADS) acc[i] = __ldcs(sums + v0 + i);
-  __syncthreads();
-  vertex_update_block<THREADS>(acc, v0, n, a, D);
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t mb = (int64_t)blockIdx.x * kMergeWarps + w;
+  double dsum = 0.0, rsum = 0.0;
+  if (mb < nb) {
+    float* acc = acc_all + (int64_t)w * B;
+    const int64_t v0 = mb * B;
+    const int n = (int)((a.V - v0) < B ? (a.V - v0) : B);
+    for (int i = lane; i < n; i += 32) acc[i] = __ldcs(sums + v0 + i);
+    __syncwarp();
+    warp_vertex_update(acc, v0, n, a, (float)(D * a.inv_V), &dsum, &rsum);
+  }
+  block_finish(dsum, rsum, a);
 }
 
 // Generic merge (Algorithm 4 alone) with identity fill.
-template <class Op, int THREADS>
-__global__ void __launch_bounds__(THREADS)
+template <class Op>
+__global__ void __launch_bounds__(kMergeWarps * 32)
 merge_only_kernel(const int32_t* __restrict__ blk, const int32_t* __restrict__ idx_map,
                   const typename Op::T* __restrict__ interm, int k, int nb, int B, int32_t V,
                   typename Op::T* __restrict__ out) {
   using T = typename Op::T;
   extern __shared__ unsigned char raw[];
-  T* acc = reinterpret_cast<T*>(raw);
-  const int64_t v0 = (int64_t)blockIdx.x * B;
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t mb = (int64_t)blockIdx.x * kMergeWarps + w;
+  if (mb >= nb) return;
+  T* acc = reinterpret_cast<T*>(raw) + (int64_t)w * B;
+  const int64_t v0 = mb * B;
   const int n = (int)((V - v0) < B ? (V - v0) : B);
-  for (int i = threadIdx.x; i < n; i += THREADS) acc[i] = Op::identity();
-  __syncthreads();
-  for (int s = 0; s < k; ++s) {
-    const int32_t lo = blk[(int64_t)s * (nb + 1) + blockIdx.x];
-    const int32_t hi = blk[(int64_t)s * (nb + 1) + blockIdx.x + 1];
-    for (int32_t i = lo + threadIdx.x; i < hi; i += THREADS) {
-      const int64_t lv = (int64_t)idx_map[i] - v0;
-      if ((uint64_t)lv < (uint64_t)n) acc[lv] = Op::op(acc[lv], interm[i]);
-    }
-    __syncthreads();
-  }
-  for (int i = threadIdx.x; i < n; i += THREADS) out[v0 + i] = acc[i];
+  warp_merge<Op>(blk, idx_map, interm, k, nb, mb, v0, n, acc);
+  for (int i = lane; i < n; i += 32) out[v0 + i] = acc[i];
 }
 
 __global__ void pr_init_kernel(const float* __restrict__ inv, int32_t V, float* __restrict__ rank,
@@ -190,9 +271,8 @@ __global__ void sum_partials_kernel(const double* __restrict__ partials, int n,
   if (threadIdx.x == 0) *out = d;
 }
 
-int set_merge_smem(const void* fn, int B, size_t elem) {
+int set_merge_smem(const void* fn, size_t bytes) {
   // the kernels also hold a little static shared memory, so opt in above 32 KB
-  const size_t bytes = (size_t)B * elem;
   if (bytes > 32 * 1024)
     CG_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
   return CG_OK;
@@ -305,18 +385,18 @@ int cg_seg_gather(const cg_segmented* g, int32_t op, const void* x, void* interm
 
 int merge(const cg_segmented* g, int32_t op, const void* interm, void* out, cudaStream_t stream) {
   CG_ARG(g && out && (interm || g->rows == 0), "merge: null argument");
+  const unsigned grid = (unsigned)ceil_div(g->nb, kMergeWarps);
+  const size_t smem = (size_t)kMergeWarps * g->B * 4;
   if (op == CG_OP_SUM_F32) {
-    auto fn = merge_only_kernel<SumF32, kMergeThreads>;
-    CG_TRY(set_merge_smem((const void*)fn, g->B, 4));
-    fn<<<g->nb, kMergeThreads, (size_t)g->B * 4, stream>>>(g->blk, g->idx_map,
-                                                           (const float*)interm, g->k, g->nb,
-                                                           g->B, g->V, (float*)out);
+    auto fn = merge_only_kernel<SumF32>;
+    CG_TRY(set_merge_smem((const void*)fn, smem));
+    fn<<<grid, kMergeWarps * 32, smem, stream>>>(g->blk, g->idx_map, (const float*)interm, g->k,
+                                                 g->nb, g->B, g->V, (float*)out);
   } else if (op == CG_OP_MIN_I32) {
-    auto fn = merge_only_kernel<MinI32, kMergeThreads>;
-    CG_TRY(set_merge_smem((const void*)fn, g->B, 4));
-    fn<<<g->nb, kMergeThreads, (size_t)g->B * 4, stream>>>(g->blk, g->idx_map,
-                                                           (const int32_t*)interm, g->k, g->nb,
-                                                           g->B, g->V, (int32_t*)out);
+    auto fn = merge_only_kernel<MinI32>;
+    CG_TRY(set_merge_smem((const void*)fn, smem));
+    fn<<<grid, kMergeWarps * 32, smem, stream>>>(g->blk, g->idx_map, (const int32_t*)interm,
+                                                 g->k, g->nb, g->B, g->V, (int32_t*)out);
   } else {
     set_error("merge: unknown op %d", op);
     return CG_ERR_INVALID_ARG;
@@ -333,8 +413,8 @@ int pr_merge_update(const cg_segmented* g, const float* inv, const float* rank_i
   CG_ARG(damping >= 0.0 && damping <= 1.0, "pr_merge_update: damping must be in [0, 1]");
   CG_ARG(rank_out != rank_in && (const float*)contrib_out != rank_in && rank_out != contrib_out,
          "pr_merge_update: outputs must not alias the inputs or each other");
-  auto fn = merge_update_kernel<kMergeThreads>;
-  CG_TRY(set_merge_smem((const void*)fn, g->B, 4));
+  const size_t smem = (size_t)kMergeWarps * g->B * 4;
+  CG_TRY(set_merge_smem((const void*)merge_update_kernel, smem));
   PrArgs a;
   a.inv = inv;
   a.rank_in = rank_in;
@@ -349,9 +429,9 @@ int pr_merge_update(const cg_segmented* g, const float* inv, const float* rank_i
   a.partials = g->partials;
   a.counter = g->counter;
   a.V = g->V;
-  fn<<<g->nb, kMergeThreads, (size_t)g->B * 4, stream>>>(g->blk, g->idx_map,
-                                                         (const float*)g->interm, g->k, g->nb,
-                                                         g->B, a);
+  merge_update_kernel<<<(unsigned)ceil_div(g->nb, kMergeWarps), kMergeWarps * 32, smem,
+                        stream>>>(g->blk, g->idx_map, (const float*)g->interm, g->k, g->nb,
+                                  g->B, a);
   CG_LAUNCH_CHECK();
   return CG_OK;
 }
@@ -387,7 +467,7 @@ int pr_plain_create(const int64_t* offsets, const int32_t* src, int32_t V, int64
   p->E = E;
   p->offsets = offsets;
   p->src = src;
-  p->nb = (int32_t)ceil_div(V, 4096);
+  p->nb = (int32_t)ceil_div(ceil_div(V, 512), kMergeWarps);  // update blocks
   int st = plan_tiles<int64_t>(offsets + 1, V, E, &p->plan, stream);
   cudaError_t e = cudaSuccess;
   if (st == CG_OK) e = cudaMalloc((void**)&p->acc, sizeof(float) * (size_t)V);
@@ -435,9 +515,10 @@ int pr_iterate_plain(const cg_plain* p, const float* inv, const float* rank_in,
   CG_ARG(p != nullptr, "pr_iterate_plain: null handle");
   CG_TRY(check_pr_args(p->V, inv, rank_in, contrib_in, rank_out, contrib_out, damping,
                        iterations, D_io));
-  const int B = 4096;
-  auto fn = dense_update_kernel<kMergeThreads>;
-  CG_TRY(set_merge_smem((const void*)fn, B, 4));
+  const int B = 512;
+  const int nb = (int)ceil_div(p->V, B);
+  const size_t smem = (size_t)kMergeWarps * B * 4;
+  CG_TRY(set_merge_smem((const void*)dense_update_kernel, smem));
   for (int t = 0; t < iterations; ++t) {
     IterBufs b = iter_bufs(t, iterations, rank_in, contrib_in, rank_out, contrib_out,
                            p->rank_tmp, p->contrib_tmp, D_io, p->dslot, resid);
@@ -461,7 +542,8 @@ int pr_iterate_plain(const cg_plain* p, const float* inv, const float* rank_in,
     a.partials = p->partials;
     a.counter = p->counter;
     a.V = p->V;
-    fn<<<p->nb, kMergeThreads, (size_t)B * 4, stream>>>(p->acc, B, a);
+    dense_update_kernel<<<(unsigned)ceil_div(nb, kMergeWarps), kMergeWarps * 32, smem,
+                          stream>>>(p->acc, B, nb, a);
     CG_LAUNCH_CHECK();
   }
   return CG_OK;

@@ -455,7 +455,7 @@ int pr_build_segments(const int64_t* offsets, const int32_t* src, int32_t V, int
   CG_ARG(offsets && (E == 0 || src), "pr_build_segments: null CSR pointer");
   CG_ARG(k >= 1 && k <= kMaxSegments, "pr_build_segments: num_segments must be in [1, %d]",
          kMaxSegments);
-  CG_ARG(B >= 1 && B <= 12288, "pr_build_segments: merge_block must be in [1, 12288]");
+  CG_ARG(B >= 1 && B <= 6144, "pr_build_segments: merge_block must be in [1, 6144]");
   std::vector<int64_t> bounds(k + 1);
   if (host_bounds) {
     for (int q = 0; q <= k; ++q) bounds[q] = host_bounds[q];

@@ -90,7 +90,7 @@ GATHER_SHAPES = ((1024, 1), (512, 2))  # staged gather (threads, blocks per SM)
 class SegmentedPageRank(_PageRankBase):
     """PageRank through CSR segmenting (Algorithms 2-5)."""
 
-    def __init__(self, graph: Graph, num_segments: int | None = None, merge_block: int = 4096,
+    def __init__(self, graph: Graph, num_segments: int | None = None, merge_block: int = 512,
                  bounds=None, threads: int = 1024, ctas_per_sm: int = 1,
                  table_vertices: int = -1):
         super().__init__(graph)
@@ -164,7 +164,7 @@ def _build(graph, cand, merge_block):
                              table_vertices=tb)
 
 
-def autotune_segments(graph: Graph, candidates=None, merge_block: int = 4096,
+def autotune_segments(graph: Graph, candidates=None, merge_block: int = 512,
                       iterations: int = 3, reps: int = 3):
     """Pick the segmenting by measuring a few iterations of each candidate
     (Section III-D's trade-off: smaller segments confine the random reads to
@@ -191,5 +191,5 @@ def autotune_segments(graph: Graph, candidates=None, merge_block: int = 4096,
     return best[0], results
 
 
-def build_candidate(graph: Graph, cand: dict, merge_block: int = 4096) -> SegmentedPageRank:
+def build_candidate(graph: Graph, cand: dict, merge_block: int = 512) -> SegmentedPageRank:
     return _build(graph, cand, merge_block)

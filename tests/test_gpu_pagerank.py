@@ -119,7 +119,7 @@ def _check_segments(C, torch, offsets, src, k, B, bounds=None):
 
 
 @pytest.mark.parametrize("k,B", [(1, 4096), (2, 1024), (4, 4096), (7, 333), (16, 4096),
-                                 (64, 12288), (1024, 64)])
+                                 (64, 6144), (1024, 64)])
 def test_segments_bitexact_rmat16(C, torch_mod, rmat16, k, B):
     _check_segments(C, torch_mod, rmat16.offsets, rmat16.src, k, B)
 
@@ -221,7 +221,7 @@ def test_plain_pagerank_parity(C, torch_mod, rmat16, rmat16_oracle, cluster):
 
 
 @pytest.mark.parametrize("k,cluster,B", [(1, None, 4096), (2, None, 4096), (4, 0, 4096),
-                                         (8, 0, 1024), (16, 1, 4096), (64, 0, 12288),
+                                         (8, 0, 1024), (16, 1, 4096), (64, 0, 6144),
                                          (1024, 0, 256)])
 def test_segmented_pagerank_parity(C, torch_mod, rmat16, rmat16_oracle, k, cluster, B):
     rank, resid, pr = _pagerank_gpu(torch_mod, rmat16, k, cluster, B=B)
