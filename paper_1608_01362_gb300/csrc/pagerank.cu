@@ -43,9 +43,9 @@ struct PrArgs {
 // [blk[s][b], blk[s][b+1]) of intermBuf into acc[idx_map[i] - b*B].  Inside
 // one segment the destinations are distinct, so lanes never collide; the
 // warp synchronises between segments, which keeps the per-destination order
-// fixed (deterministic).  The loads of segment s+1 are issued before the
-// adds of segment s, and no block-wide barrier is involved, so the k segments
-// do not serialise k memory round trips per block.
+// fixed (deterministic).  The first rows of eight segments are loaded
+// together before they are applied in order, and no block-wide barrier is
+// involved, so the k segments do not serialise k memory round trips.
 // ---------------------------------------------------------------------------
 constexpr int kMergeWarps = 8;
 
@@ -56,6 +56,7 @@ __device__ __forceinline__ void warp_merge(const int32_t* __restrict__ blk,
                                            int nb, int64_t mb, int64_t v0, int n,
                                            typename Op::T* acc) {
   using T = typename Op::T;
+  constexpr int G = 8;  // segments whose first rows are loaded together
   const int lane = threadIdx.x & 31;
   for (int i = lane; i < n; i += 32) acc[i] = Op::identity();
   __syncwarp();
@@ -67,40 +68,34 @@ __device__ __forceinline__ void warp_merge(const int32_t* __restrict__ blk,
       hi = __ldg(blk + (int64_t)ls * (nb + 1) + mb + 1);
     }
     const int cnt = k - s0 < 32 ? k - s0 : 32;
-    int32_t i0 = __shfl_sync(0xffffffffu, lo, 0) + lane;
-    int32_t h0 = __shfl_sync(0xffffffffu, hi, 0);
-    int32_t d0 = 0;
-    T x0 = Op::identity();
-    if (i0 < h0) {
-      d0 = __ldcs(idx_map + i0);
-      x0 = __ldcs(interm + i0);
-    }
-    for (int t = 0; t < cnt; ++t) {
-      // issue segment t+1's first loads before applying segment t
-      int32_t i1 = 0, h1 = 0, d1 = 0;
-      T x1 = Op::identity();
-      if (t + 1 < cnt) {
-        i1 = __shfl_sync(0xffffffffu, lo, t + 1) + lane;
-        h1 = __shfl_sync(0xffffffffu, hi, t + 1);
-        if (i1 < h1) {
-          d1 = __ldcs(idx_map + i1);
-          x1 = __ldcs(interm + i1);
+    for (int t0 = 0; t0 < cnt; t0 += G) {
+      int32_t ii[G], hh[G], dd[G];
+      T xx[G];
+#pragma unroll
+      for (int u = 0; u < G; ++u) {  // first (up to 32) rows of G segments in flight
+        const int t = t0 + u < 31 ? t0 + u : 31;
+        ii[u] = __shfl_sync(0xffffffffu, lo, t) + lane;
+        hh[u] = t0 + u < cnt ? __shfl_sync(0xffffffffu, hi, t) : 0;
+        dd[u] = 0;
+        xx[u] = Op::identity();
+        if (ii[u] < hh[u]) {
+          dd[u] = __ldcs(idx_map + ii[u]);
+          xx[u] = __ldcs(interm + ii[u]);
         }
       }
-      if (i0 < h0) {
-        const int64_t lv = (int64_t)d0 - v0;
-        if ((uint64_t)lv < (uint64_t)n) acc[lv] = Op::op(acc[lv], x0);
+#pragma unroll
+      for (int u = 0; u < G; ++u) {  // apply in segment order
+        if (ii[u] < hh[u]) {
+          const int64_t lv = (int64_t)dd[u] - v0;
+          if ((uint64_t)lv < (uint64_t)n) acc[lv] = Op::op(acc[lv], xx[u]);
+        }
+        for (int32_t i = ii[u] + 32; i < hh[u]; i += 32) {  // segments with > 32 rows here
+          const int64_t lv = (int64_t)__ldcs(idx_map + i) - v0;
+          const T x = __ldcs(interm + i);
+          if ((uint64_t)lv < (uint64_t)n) acc[lv] = Op::op(acc[lv], x);
+        }
+        __syncwarp();
       }
-      for (int32_t i = i0 + 32; i < h0; i += 32) {  // segments with more than 32 rows here
-        const int64_t lv = (int64_t)__ldcs(idx_map + i) - v0;
-        const T x = __ldcs(interm + i);
-        if ((uint64_t)lv < (uint64_t)n) acc[lv] = Op::op(acc[lv], x);
-      }
-      __syncwarp();
-      i0 = i1;
-      h0 = h1;
-      d0 = d1;
-      x0 = x1;
     }
   }
   __syncwarp();

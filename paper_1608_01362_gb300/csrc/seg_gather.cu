@@ -271,10 +271,106 @@ __global__ void staged_fill_kernel(const uint32_t* __restrict__ colf,
   }
 }
 
+// One staged chunk whose stream words (pk, fl) are already loaded: fold,
+// complete the rows and record the open row.
+template <class Op>
+__device__ __forceinline__ void staged_chunk(const uint32_t (&pk)[8], uint32_t fl, int n,
+                                             int32_t c, int32_t frow,
+                                             const typename Op::T* tab, uint32_t tmax,
+                                             typename Op::T* __restrict__ out,
+                                             typename Op::T* __restrict__ carry,
+                                             int32_t* __restrict__ carry_row) {
+  using T = typename Op::T;
+  constexpr int IPL = kStagedIPL;
+  constexpr int CHUNK = kStagedChunk;
+  const int lane = threadIdx.x & 31;
+  T v[IPL];
+  if (n == CHUNK) {
+#pragma unroll
+    for (int u = 0; u < IPL; ++u) {
+      const uint32_t idx = (u & 1) ? (pk[u >> 1] >> 16) : (pk[u >> 1] & 0xFFFFu);
+      v[u] = tab[idx < tmax ? idx : tmax];
+    }
+  } else {  // a segment's last chunk: lanes past its end hold nothing
+    const int nl = n - lane * IPL;
+#pragma unroll
+    for (int u = 0; u < IPL; ++u) {
+      const uint32_t idx = (u & 1) ? (pk[u >> 1] >> 16) : (pk[u >> 1] & 0xFFFFu);
+      v[u] = u < nl ? tab[idx < tmax ? idx : tmax] : Op::identity();
+    }
+    fl &= nl >= IPL ? 0xFFFFu : (nl <= 0 ? 0u : ((1u << nl) - 1u));
+  }
+  // rows ended before this lane
+  const int F = __popc(fl);
+  int incl = F;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int y = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += y;
+  }
+  const int32_t row0 = frow + (incl - F);
+  // sequential fold
+  T acc = Op::identity(), first_val = Op::identity();
+  int nf = 0;
+#pragma unroll
+  for (int u = 0; u < IPL; ++u) {
+    acc = Op::op(acc, v[u]);
+    if (fl & (1u << u)) {
+      if (nf == 0)
+        first_val = acc;
+      else
+        out[row0 + nf] = acc;
+      ++nf;
+      acc = Op::identity();
+    }
+  }
+  // segmented scan of the open-row parts
+  T S = acc;
+  int h = F > 0;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const T y = __shfl_up_sync(0xffffffffu, S, o);
+    const int g = __shfl_up_sync(0xffffffffu, h, o);
+    if (lane >= o) {
+      if (!h) S = Op::op(y, S);
+      h |= g;
+    }
+  }
+  const T P = __shfl_up_sync(0xffffffffu, S, 1);
+  if (F > 0) out[row0] = lane > 0 ? Op::op(P, first_val) : first_val;
+  // the row open at the chunk's end
+  const int total = __shfl_sync(0xffffffffu, incl, 31);
+  const uint32_t lf = __shfl_sync(0xffffffffu, fl, (n - 1) / IPL);
+  if (lane == 31) {
+    const bool closed = (lf >> ((n - 1) % IPL)) & 1u;
+    carry[c] = closed ? Op::identity() : S;
+    carry_row[c] = closed ? -1 : frow + total;
+  }
+}
+
+// Bulk prefetch of [p, p + bytes) into L2 (TMA; p and bytes 16-byte aligned).
+__device__ __forceinline__ void prefetch_l2(const void* p, uint32_t bytes) {
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ void staged_load(const uint8_t* __restrict__ cs, int32_t c,
+                                            uint32_t (&pk)[8], uint32_t& fl) {
+  const int lane = threadIdx.x & 31;
+  const uint8_t* base = cs + (int64_t)c * kStagedChunkBytes;
+  const uint4 qa = __ldcs(reinterpret_cast<const uint4*>(base + lane * 32));
+  const uint4 qb = __ldcs(reinterpret_cast<const uint4*>(base + lane * 32 + 16));
+  fl = __ldcs(reinterpret_cast<const unsigned short*>(base + 2 * kStagedChunk) + lane);
+  pk[0] = qa.x; pk[1] = qa.y; pk[2] = qa.z; pk[3] = qa.w;
+  pk[4] = qb.x; pk[5] = qb.y; pk[6] = qb.z; pk[7] = qb.w;
+}
+
 // The staged launch: segments [0, m) are read from a shared-memory copy of
-// their source values.  Each block takes one contiguous run of block-groups
-// (it meets at most a few segments, so it stages at most a few tables).  A
-// warp's chunk is 512 edges from the compressed stream; lane l holds 16.
+// their source values.  Work pieces of `piece` consecutive block-groups are
+// handed out in increasing order by an atomic counter: a block's groups only
+// move forward (so it stages each segment's table at most once) and a slow
+// block simply takes fewer pieces.  A warp's chunk is 512 edges of the
+// compressed stream (lane l holds 16); while it works on one chunk the TMA
+// unit prefetches its next one into L2.
 template <class Op, int THREADS>
 __global__ void __launch_bounds__(THREADS, 1024 / THREADS)
 staged_gather_kernel(const uint8_t* __restrict__ cs, const typename Op::T* __restrict__ x,
@@ -286,19 +382,15 @@ staged_gather_kernel(const uint8_t* __restrict__ cs, const typename Op::T* __res
                      int32_t* __restrict__ carry_row) {
   using T = typename Op::T;
   constexpr int WARPS = THREADS / 32;
-  constexpr int IPL = kStagedIPL;
   constexpr int CHUNK = kStagedChunk;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ int32_t s_piece;
   T* tab = reinterpret_cast<T*>(smem_raw);
-  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  const int tid = threadIdx.x, w = tid >> 5;
   int s = 0;
-  int32_t tmax = 0, Es = 0, cbase = 0, ctbase = 0, ctnext = -1;
+  int32_t Es = 0, cbase = 0, ctbase = 0, ctnext = -1;
+  uint32_t tmax = 0;
 
-  // Pieces of `piece` consecutive block-groups are handed out in increasing
-  // order by an atomic counter: a block's groups only move forward (so it
-  // stages each segment's table at most once) and a slow block simply takes
-  // fewer pieces.
   for (;;) {
     __syncthreads();  // everyone is done with the previous piece's s_piece
     if (tid == 0) s_piece = (int32_t)atomicAdd(next_piece, 1u);
@@ -306,98 +398,32 @@ staged_gather_kernel(const uint8_t* __restrict__ cs, const typename Op::T* __res
     const int32_t my_lo = s_piece * piece;
     if (my_lo >= ct_end) break;
     const int32_t my_hi = my_lo + piece < ct_end ? my_lo + piece : ct_end;
-    for (int32_t ct = my_lo; ct < my_hi; ++ct) {
-    if (ct >= ctnext) {  // a new segment (uniform across the block)
-      while (ct >= seg_ctile[s + 1]) ++s;
-      Es = seg_E[s];
-      cbase = (int32_t)seg_chunk[s];
-      ctbase = seg_ctile[s];
-      ctnext = seg_ctile[s + 1];
-      const int32_t lo = seg_lo[s], tn = seg_tab[s];
-      tmax = tn > 0 ? tn - 1 : 0;
-      __syncthreads();  // every warp is done reading the previous table
-      stage_table<T, THREADS>(x + lo, tn, tab, tid);
-      __syncthreads();
-    }
-    const int32_t j = (ct - ctbase) * WARPS + w;
-    const int32_t e0 = j * CHUNK;
-    if (e0 >= Es) continue;  // warp-uniform
-    const int n = Es - e0 < CHUNK ? Es - e0 : CHUNK;
-    const int32_t c = cbase + j;
-    const int32_t frow = first_row[c];
-
-    // 1. 16 local indices (two 16-byte loads) and the lane's row-end mask
-    const uint8_t* base = cs + (int64_t)c * kStagedChunkBytes;
-    const uint4 qa = __ldcs(reinterpret_cast<const uint4*>(base + lane * 32));
-    const uint4 qb = __ldcs(reinterpret_cast<const uint4*>(base + lane * 32 + 16));
-    uint32_t fl = __ldcs(reinterpret_cast<const unsigned short*>(base + 2 * CHUNK) + lane);
-    const uint32_t pk[8] = {qa.x, qa.y, qa.z, qa.w, qb.x, qb.y, qb.z, qb.w};
-    T v[IPL];
-    if (n == CHUNK) {
-#pragma unroll
-      for (int u = 0; u < IPL; ++u) {
-        const uint32_t idx = (u & 1) ? (pk[u >> 1] >> 16) : (pk[u >> 1] & 0xFFFFu);
-        v[u] = tab[idx < (uint32_t)tmax ? idx : (uint32_t)tmax];
+    for (int32_t ct = my_lo; ct < my_hi;) {
+      if (ct >= ctnext) {  // a new segment (uniform across the block)
+        while (ct >= seg_ctile[s + 1]) ++s;
+        Es = seg_E[s];
+        cbase = (int32_t)seg_chunk[s];
+        ctbase = seg_ctile[s];
+        ctnext = seg_ctile[s + 1];
+        const int32_t lo = seg_lo[s], tn = seg_tab[s];
+        tmax = tn > 0 ? (uint32_t)(tn - 1) : 0u;
+        __syncthreads();  // every warp is done reading the previous table
+        stage_table<T, THREADS>(x + lo, tn, tab, tid);
+        __syncthreads();
       }
-    } else {  // a segment's last chunk: lanes past its end hold nothing
-      const int nl = n - lane * IPL;
-#pragma unroll
-      for (int u = 0; u < IPL; ++u) {
-        const uint32_t idx = (u & 1) ? (pk[u >> 1] >> 16) : (pk[u >> 1] & 0xFFFFu);
-        v[u] = u < nl ? tab[idx < (uint32_t)tmax ? idx : (uint32_t)tmax] : Op::identity();
+      const int32_t j = (ct - ctbase) * WARPS + w;
+      if (j * CHUNK < Es) {  // warp-uniform
+        const int32_t c = cbase + j;
+        // ask the TMA unit to pull this warp's next chunk into L2 meanwhile
+        if ((threadIdx.x & 31) == 0 && ct + 1 < my_hi && (j + WARPS) * CHUNK < Es)
+          prefetch_l2(cs + (int64_t)(c + WARPS) * kStagedChunkBytes, kStagedChunkBytes);
+        uint32_t pk[8], fl;
+        staged_load(cs, c, pk, fl);
+        const int32_t frow = first_row[c];
+        staged_chunk<Op>(pk, fl, Es - j * CHUNK < CHUNK ? Es - j * CHUNK : CHUNK, c, frow, tab,
+                         tmax, out, carry, carry_row);
       }
-      fl &= nl >= IPL ? 0xFFFFu : (nl <= 0 ? 0u : ((1u << nl) - 1u));
-    }
-
-    // 2. rows ended before this lane
-    const int F = __popc(fl);
-    int incl = F;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const int y = __shfl_up_sync(0xffffffffu, incl, o);
-      if (lane >= o) incl += y;
-    }
-    const int32_t row0 = frow + (incl - F);
-
-    // 3. sequential fold
-    T acc = Op::identity(), first_val = Op::identity();
-    int nf = 0;
-#pragma unroll
-    for (int u = 0; u < IPL; ++u) {
-      acc = Op::op(acc, v[u]);
-      if (fl & (1u << u)) {
-        if (nf == 0)
-          first_val = acc;
-        else
-          out[row0 + nf] = acc;
-        ++nf;
-        acc = Op::identity();
-      }
-    }
-
-    // 4. segmented scan of the open-row parts
-    T S = acc;
-    int h = F > 0;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const T y = __shfl_up_sync(0xffffffffu, S, o);
-      const int g = __shfl_up_sync(0xffffffffu, h, o);
-      if (lane >= o) {
-        if (!h) S = Op::op(y, S);
-        h |= g;
-      }
-    }
-    const T P = __shfl_up_sync(0xffffffffu, S, 1);
-    if (F > 0) out[row0] = lane > 0 ? Op::op(P, first_val) : first_val;
-
-    // 5. the row open at the chunk's end
-    const int total = __shfl_sync(0xffffffffu, incl, 31);
-    const uint32_t lf = __shfl_sync(0xffffffffu, fl, (n - 1) / IPL);
-    if (lane == 31) {
-      const bool closed = (lf >> ((n - 1) % IPL)) & 1u;
-      carry[c] = closed ? Op::identity() : S;
-      carry_row[c] = closed ? -1 : frow + total;
-    }
+      ++ct;
     }
   }
 }
