@@ -43,7 +43,7 @@ struct PrArgs {
 // [blk[s][b], blk[s][b+1]) of intermBuf into acc[idx_map[i] - b*B].  Inside
 // one segment the destinations are distinct, so lanes never collide; the
 // warp synchronises between segments, which keeps the per-destination order
-// fixed (deterministic).  The first rows of eight segments are loaded
+// fixed (deterministic).  The first rows of four segments are loaded
 // together before they are applied in order, and no block-wide barrier is
 // involved, so the k segments do not serialise k memory round trips.
 // ---------------------------------------------------------------------------
@@ -56,7 +56,7 @@ __device__ __forceinline__ void warp_merge(const int32_t* __restrict__ blk,
                                            int nb, int64_t mb, int64_t v0, int n,
                                            typename Op::T* acc) {
   using T = typename Op::T;
-  constexpr int G = 8;  // segments whose first rows are loaded together
+  constexpr int G = 4;  // segments whose first rows are loaded together
   const int lane = threadIdx.x & 31;
   for (int i = lane; i < n; i += 32) acc[i] = Op::identity();
   __syncwarp();
@@ -166,7 +166,7 @@ __device__ __forceinline__ void block_finish(double dsum, double rsum, const PrA
 }
 
 // Cache-aware merge (Algorithm 4) fused with the vertex update.
-__global__ void __launch_bounds__(kMergeWarps * 32)
+__global__ void __launch_bounds__(kMergeWarps * 32, 6)
 merge_update_kernel(const int32_t* __restrict__ blk, const int32_t* __restrict__ idx_map,
                     const float* __restrict__ interm, int k, int nb, int B, PrArgs a) {
   extern __shared__ float acc_all[];

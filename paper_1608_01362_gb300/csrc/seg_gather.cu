@@ -231,23 +231,28 @@ __device__ __forceinline__ void stage_table(const T* __restrict__ src, int n, T*
   }
 }
 
-// Staged chunk stream: per 512-edge chunk, 512 uint16 segment-local source
-// indices (lane l's 16 edges at bytes [32l, 32l + 32)) then 32 uint16 row-end
-// masks (lane l's at byte 1024 + 2l).
+// Staged chunk stream, per 512-edge chunk (1168 bytes):
+//   [0, 1024)     512 uint16 segment-local source indices, lane l's 16 edges
+//                 at bytes [32l, 32l + 32)
+//   [1024, 1088)  32 uint16 row-end masks (bit u: lane l's edge u ends a row)
+//   [1088, 1152)  32 uint16 row ends in lanes before lane l
+//   [1152, 1156)  int32 subgraph row of the chunk's first edge
 constexpr int kStagedIPL = 16;
 constexpr int kStagedChunk = 32 * kStagedIPL;  // 512 edges
-constexpr int kStagedChunkBytes = 2 * kStagedChunk + 64;  // 1088
+constexpr int kStagedChunkBytes = 2 * kStagedChunk + 64 + 64 + 16;  // 1168
 
-// One thread per (staged chunk, lane): pack its 16 edges.
+// One warp per staged chunk: pack its 512 edges, the lanes' row-end masks and
+// their exclusive prefix, and the chunk's first subgraph row.
 __global__ void staged_fill_kernel(const uint32_t* __restrict__ colf,
                                    const int64_t* __restrict__ seg_chunk,
                                    const int64_t* __restrict__ seg_cstart,
-                                   const int32_t* __restrict__ seg_E, int m, int64_t nchunks_a,
-                                   uint8_t* __restrict__ cs) {
-  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < nchunks_a * 32;
-       t += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t c = t >> 5;
-    const int lane = (int)(t & 31);
+                                   const int32_t* __restrict__ seg_E,
+                                   const int32_t* __restrict__ first_row, int m,
+                                   int64_t nchunks_a, uint8_t* __restrict__ cs) {
+  const int lane = threadIdx.x & 31;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t c = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; c < nchunks_a;
+       c += nw) {
     const int s = last_le(seg_chunk, m + 1, c);
     const int64_t e_begin = (c - seg_chunk[s]) * kStagedChunk + lane * kStagedIPL;
     uint32_t packed[kStagedIPL / 2];
@@ -263,19 +268,32 @@ __global__ void staged_fill_kernel(const uint32_t* __restrict__ colf,
       }
       if (u & 1) packed[u >> 1] |= idx << 16; else packed[u >> 1] = idx;
     }
+    const int F = __popc(fl);
+    int incl = F;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += y;
+    }
     uint8_t* base = cs + c * kStagedChunkBytes;
     uint4* dst = reinterpret_cast<uint4*>(base + lane * 32);
     dst[0] = make_uint4(packed[0], packed[1], packed[2], packed[3]);
     dst[1] = make_uint4(packed[4], packed[5], packed[6], packed[7]);
     reinterpret_cast<uint16_t*>(base + 2 * kStagedChunk)[lane] = (uint16_t)fl;
+    reinterpret_cast<uint16_t*>(base + 2 * kStagedChunk + 64)[lane] = (uint16_t)(incl - F);
+    if (lane == 0) {
+      int32_t* tail = reinterpret_cast<int32_t*>(base + 2 * kStagedChunk + 128);
+      tail[0] = first_row[c];
+      tail[1] = tail[2] = tail[3] = 0;
+    }
   }
 }
 
-// One staged chunk whose stream words (pk, fl) are already loaded: fold,
-// complete the rows and record the open row.
+// One staged chunk whose stream words are loaded: pk (16 indices), fl (row
+// ends), pre (row ends before this lane), frow (first subgraph row).
 template <class Op>
-__device__ __forceinline__ void staged_chunk(const uint32_t (&pk)[8], uint32_t fl, int n,
-                                             int32_t c, int32_t frow,
+__device__ __forceinline__ void staged_chunk(const uint32_t (&pk)[8], uint32_t fl, int pre,
+                                             int n, int32_t c, int32_t frow,
                                              const typename Op::T* tab, uint32_t tmax,
                                              typename Op::T* __restrict__ out,
                                              typename Op::T* __restrict__ carry,
@@ -300,16 +318,9 @@ __device__ __forceinline__ void staged_chunk(const uint32_t (&pk)[8], uint32_t f
     }
     fl &= nl >= IPL ? 0xFFFFu : (nl <= 0 ? 0u : ((1u << nl) - 1u));
   }
-  // rows ended before this lane
   const int F = __popc(fl);
-  int incl = F;
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    const int y = __shfl_up_sync(0xffffffffu, incl, o);
-    if (lane >= o) incl += y;
-  }
-  const int32_t row0 = frow + (incl - F);
-  // sequential fold
+  const int32_t row0 = frow + pre;
+  // sequential fold; rows that start and end in this lane are final
   T acc = Op::identity(), first_val = Op::identity();
   int nf = 0;
 #pragma unroll
@@ -324,27 +335,29 @@ __device__ __forceinline__ void staged_chunk(const uint32_t (&pk)[8], uint32_t f
       acc = Op::identity();
     }
   }
-  // segmented scan of the open-row parts
+  // the part of each lane's first row held by earlier lanes: one exchange
+  // when every lane ends a row, a segmented scan otherwise
   T S = acc;
-  int h = F > 0;
+  if (!__all_sync(0xffffffffu, F > 0)) {
+    int h = F > 0;
 #pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    const T y = __shfl_up_sync(0xffffffffu, S, o);
-    const int g = __shfl_up_sync(0xffffffffu, h, o);
-    if (lane >= o) {
-      if (!h) S = Op::op(y, S);
-      h |= g;
+    for (int o = 1; o < 32; o <<= 1) {
+      const T y = __shfl_up_sync(0xffffffffu, S, o);
+      const int g = __shfl_up_sync(0xffffffffu, h, o);
+      if (lane >= o) {
+        if (!h) S = Op::op(y, S);
+        h |= g;
+      }
     }
   }
   const T P = __shfl_up_sync(0xffffffffu, S, 1);
   if (F > 0) out[row0] = lane > 0 ? Op::op(P, first_val) : first_val;
   // the row open at the chunk's end
-  const int total = __shfl_sync(0xffffffffu, incl, 31);
   const uint32_t lf = __shfl_sync(0xffffffffu, fl, (n - 1) / IPL);
   if (lane == 31) {
     const bool closed = (lf >> ((n - 1) % IPL)) & 1u;
     carry[c] = closed ? Op::identity() : S;
-    carry_row[c] = closed ? -1 : frow + total;
+    carry_row[c] = closed ? -1 : row0 + F;
   }
 }
 
@@ -354,12 +367,15 @@ __device__ __forceinline__ void prefetch_l2(const void* p, uint32_t bytes) {
 }
 
 __device__ __forceinline__ void staged_load(const uint8_t* __restrict__ cs, int32_t c,
-                                            uint32_t (&pk)[8], uint32_t& fl) {
+                                            uint32_t (&pk)[8], uint32_t& fl, int& pre,
+                                            int32_t& frow) {
   const int lane = threadIdx.x & 31;
   const uint8_t* base = cs + (int64_t)c * kStagedChunkBytes;
   const uint4 qa = __ldcs(reinterpret_cast<const uint4*>(base + lane * 32));
   const uint4 qb = __ldcs(reinterpret_cast<const uint4*>(base + lane * 32 + 16));
   fl = __ldcs(reinterpret_cast<const unsigned short*>(base + 2 * kStagedChunk) + lane);
+  pre = __ldcs(reinterpret_cast<const unsigned short*>(base + 2 * kStagedChunk + 64) + lane);
+  frow = __ldcs(reinterpret_cast<const int32_t*>(base + 2 * kStagedChunk + 128));
   pk[0] = qa.x; pk[1] = qa.y; pk[2] = qa.z; pk[3] = qa.w;
   pk[4] = qb.x; pk[5] = qb.y; pk[6] = qb.z; pk[7] = qb.w;
 }
@@ -418,10 +434,11 @@ staged_gather_kernel(const uint8_t* __restrict__ cs, const typename Op::T* __res
         if ((threadIdx.x & 31) == 0 && ct + 1 < my_hi && (j + WARPS) * CHUNK < Es)
           prefetch_l2(cs + (int64_t)(c + WARPS) * kStagedChunkBytes, kStagedChunkBytes);
         uint32_t pk[8], fl;
-        staged_load(cs, c, pk, fl);
-        const int32_t frow = first_row[c];
-        staged_chunk<Op>(pk, fl, Es - j * CHUNK < CHUNK ? Es - j * CHUNK : CHUNK, c, frow, tab,
-                         tmax, out, carry, carry_row);
+        int pre;
+        int32_t frow;
+        staged_load(cs, c, pk, fl, pre, frow);
+        staged_chunk<Op>(pk, fl, pre, Es - j * CHUNK < CHUNK ? Es - j * CHUNK : CHUNK, c, frow,
+                         tab, tmax, out, carry, carry_row);
       }
       ++ct;
     }
@@ -582,7 +599,7 @@ int seg_plan_configure(SegPlan* p, int threads, int ctas_per_sm, int tab_vertice
   }
   if (chunk[m] > 0) {
     staged_fill_kernel<<<grid_for(chunk[m] * 32, 256), 256, 0, s>>>(
-        p->colf, p->seg_chunk, p->seg_cstart, p->seg_E, m, chunk[m], p->cs);
+        p->colf, p->seg_chunk, p->seg_cstart, p->seg_E, p->first_row, m, chunk[m], p->cs);
     CG_LAUNCH_CHECK();
   }
   CG_CUDA(cudaStreamSynchronize(s));  // host vectors go out of scope
