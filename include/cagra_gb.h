@@ -314,6 +314,45 @@ int pr_iterate_plain(const cg_plain *plain, const float *dev_inv,
                      double *dev_dangling_io, double *dev_resid,
                      int32_t probe, cudaStream_t stream);
 
+/* ------------------------------------------------- no device allocation */
+
+/*
+ * One plain pull PageRank iteration (the same arithmetic as pr_iterate_plain
+ * with iterations = 1 and probe = 0) that allocates no device memory.  The
+ * paper has no counterpart: this exists for callers that cannot allocate at
+ * call time -- code running inside a memory budget reserved up front, hosts
+ * that only let a library touch buffers they registered beforehand, or
+ * latency-critical loops that must not risk the synchronisation an
+ * allocation can cause.  Such a caller passes its own inputs and outputs
+ * (device pointers, as for pr_iterate_plain: in-edge CSR, inv, rank_in,
+ * contrib_in -> rank_out, contrib_out; *dev_dangling_io = D of rank_in on
+ * entry, D of rank_out on exit; dev_resid: one double or NULL) and the work
+ * buffers come from one statically sized device array inside the library,
+ * which every GPU that loads the library holds until the process exits (see
+ * pr_noalloc_limits for its size).
+ *  - Limits: V <= 2^20 vertices and E <= 2^24 edges; larger inputs return
+ *    CG_ERR_INVALID_ARG with a message and enqueue nothing.
+ *  - The CSR is not validated (validation would need scratch); out-of-range
+ *    sources are skipped.
+ *  - No cudaMalloc, cudaFree or allocating library routine is called.  The
+ *    first call on a device looks up the array's device address (once per
+ *    device, with that device current); make that first call before any
+ *    stream capture.
+ *  - Every call shares the one array and the array keeps the last call's
+ *    contents: calls whose executions overlap on the GPU (other streams,
+ *    other host threads) race with each other.  Serialise them.
+ */
+int pr_iterate_plain_noalloc(const int64_t *dev_offsets, const int32_t *dev_src,
+                             int32_t V, int64_t E, const float *dev_inv,
+                             const float *dev_rank_in, const float *dev_contrib_in,
+                             float *dev_rank_out, float *dev_contrib_out,
+                             double damping, double *dev_dangling_io,
+                             double *dev_resid, cudaStream_t stream);
+
+/* Limits and size of the fixed scratch of pr_iterate_plain_noalloc (host). */
+int pr_noalloc_limits(int64_t *max_vertices, int64_t *max_edges,
+                      int64_t *scratch_bytes);
+
 #ifdef __cplusplus
 }
 #endif

@@ -29,6 +29,7 @@ EXPORTS = [
     "pr_gather_table_capacity", "cg_segmented_export",
     "cg_segmented_destroy", "cg_seg_gather", "merge",
     "pr_init", "pr_contrib", "pr_iterate", "pr_merge_update", "pr_plain_create", "pr_plain_destroy", "pr_iterate_plain",
+    "pr_iterate_plain_noalloc", "pr_noalloc_limits",
 ]
 
 
@@ -85,6 +86,9 @@ def load(path: str | None = None):
             "pr_plain_destroy": (ctypes.c_int, [vp]),
             "pr_iterate_plain": (ctypes.c_int, [vp, vp, vp, vp, vp, vp, dbl, i32, vp, vp, i32,
                                                 vp]),
+            "pr_iterate_plain_noalloc": (ctypes.c_int, [vp, vp, i32, i64, vp, vp, vp, vp, vp, dbl,
+                                                        vp, vp, vp]),
+            "pr_noalloc_limits": (ctypes.c_int, [vp, vp, vp]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)
@@ -312,3 +316,21 @@ def pr_iterate_plain(plain: Plain, inv, rank_in, contrib_in, rank_out, contrib_o
                                    _ptr(rank_out), _ptr(contrib_out), damping, iterations,
                                    _ptr(dangling), _ptr(resid), int(probe), _stream(stream)),
            "pr_iterate_plain")
+
+
+def pr_iterate_plain_noalloc(offsets, src, inv, rank_in, contrib_in, rank_out, contrib_out,
+                             damping: float, dangling, resid=None, stream=None):
+    """One plain PageRank iteration using only the library's fixed scratch."""
+    _check(load().pr_iterate_plain_noalloc(_ptr(offsets), _ptr(src) if src.numel() else None,
+                                           offsets.numel() - 1, src.numel(), _ptr(inv),
+                                           _ptr(rank_in), _ptr(contrib_in), _ptr(rank_out),
+                                           _ptr(contrib_out), damping, _ptr(dangling),
+                                           _ptr(resid), _stream(stream)),
+           "pr_iterate_plain_noalloc")
+
+
+def pr_noalloc_limits():
+    mv, me, sb = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+    _check(load().pr_noalloc_limits(ctypes.byref(mv), ctypes.byref(me), ctypes.byref(sb)),
+           "pr_noalloc_limits")
+    return {"max_vertices": mv.value, "max_edges": me.value, "scratch_bytes": sb.value}
