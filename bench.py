@@ -101,21 +101,25 @@ class ClockSampler:
                 "samples": len(self.rows)}
 
 
-def _gather_hash():
+KERNEL_SOURCES = ("seg_gather.cu", "seg_gather.cuh", "pagerank.cu", "update.cuh", "gather.cuh")
+
+
+def kernel_source_hash():
+    """Hash of the sources of the kernels one iteration launches."""
     h = hashlib.sha256()
-    for f in ("gather.cuh",):
+    for f in KERNEL_SOURCES:
         with open(os.path.join(ROOT, "paper_1608_01362_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
 
 
-def _traffic_per_launch(E, V, rows):
-    """DRAM bytes per gather launch from the committed ncu summary, scaled by
-    edges, if it was taken on the current gather kernel source; else None."""
+def _traffic_per_iteration(E):
+    """DRAM bytes per iteration from the committed ncu summary (per edge,
+    scaled to E), when it was taken on the current kernel sources; else None."""
     try:
-        with open(os.path.join(ROOT, "profiles", "gather_traffic.json")) as f:
+        with open(os.path.join(ROOT, "profiles", "pagerank_iteration_rmat25_traffic.json")) as f:
             t = json.load(f)
-        if t.get("gather_source_sha") != _gather_hash():
+        if t.get("kernel_source_sha") != kernel_source_hash():
             return None
         return float(t["dram_bytes_per_edge"]) * E
     except Exception:
@@ -243,23 +247,29 @@ def main():
 
     stream = torch.cuda.current_stream()
     resid = torch.zeros(ITERS, dtype=torch.float64, device=dev)
-    dslot = torch.zeros(2, dtype=torch.float64, device=dev)
     n_ev = args.steps * ITERS
-    ev_a = [torch.cuda.Event(enable_timing=True) for _ in range(n_ev)]
-    ev_b = [torch.cuda.Event(enable_timing=True) for _ in range(n_ev)]
+    # events around the three launch groups of every timed iteration
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(n_ev)] for _ in range(4)]
 
     def one_step(events_at=None):
-        """One PageRank solve; the gather launches bracketed by events."""
+        """One PageRank solve (r_0 = 1/V, ITERS iterations) through the C ABI."""
         pr.init()
         rin, cin, rout, cout = pr.rank[0], pr.contrib[0], pr.rank[1], pr.contrib[1]
         for it in range(ITERS):
-            if events_at is not None:
-                ev_a[events_at + it].record(stream)
-            C.cg_seg_gather(pr.seg, C.CG_OP_SUM_F32, cin, None)
-            if events_at is not None:
-                ev_b[events_at + it].record(stream)
+            e = None if events_at is None else events_at + it
+            if e is not None:
+                ev[0][e].record(stream)
+            C.cg_seg_gather_phases(pr.seg, C.CG_OP_SUM_F32, cin, None, C.PHASE_STAGED)
+            if e is not None:
+                ev[1][e].record(stream)
+            C.cg_seg_gather_phases(pr.seg, C.CG_OP_SUM_F32, cin, None,
+                                   C.PHASE_CACHED | C.PHASE_FIXUP)
+            if e is not None:
+                ev[2][e].record(stream)
             C.pr_merge_update(pr.seg, graph.inv, rin, rout, cout, DAMPING, pr.dangling,
                               pr.dangling, resid[it:it + 1])
+            if e is not None:
+                ev[3][e].record(stream)
             rin, cin, rout, cout = rout, cout, rin, cin
 
     for _ in range(args.warmup):
@@ -283,7 +293,12 @@ def main():
     if pg:
         pg.barrier()
     elapsed = start.elapsed_time(stop) / 1e3
-    gather_ms = [a.elapsed_time(b) for a, b in zip(ev_a, ev_b)]
+
+    def mean_span(i, j):
+        return float(np.mean([x.elapsed_time(y) for x, y in zip(ev[i], ev[j])])) / 1e3
+
+    t_staged, t_cached, t_merge, t_iter_ev = (mean_span(0, 1), mean_span(1, 2), mean_span(2, 3),
+                                              mean_span(0, 3))
     t_max = elapsed
     if pg:
         tt = torch.tensor([elapsed])
@@ -341,14 +356,15 @@ def main():
     seg_iter_s = t_max / (args.steps * ITERS)
     del plain_orig, plain_cl, probe, plain_orig_graph
 
-    # ---- roofline of the dominant kernel (the segment-processing gather)
+    # ---- roofline: the unit is one PageRank iteration (every launch of the hot
+    # path: staged gather, L1/L2 gather, fix-up, merge + vertex update) against
+    # the method-independent byte count B_min = 4E + 28V (int64 offsets, int32
+    # sources, FP32 vertex data), timed by events inside the timed region
     hbm, peak_kind = _peaks()
     rows = int(info["rows"])
-    gather_bytes = 4 * E + 8 * rows + 4 * V      # col, row ends + intermBuf, contrib once
-    gather_s = float(np.mean(gather_ms)) / 1e3
-    achieved = gather_bytes / gather_s / 1e9
-    traffic = _traffic_per_launch(E, V, rows)
-    bmin = 4 * E + 28 * V                         # method-independent bytes per iteration
+    bmin = 4 * E + 28 * V
+    achieved = bmin / t_iter_ev / 1e9
+    traffic = _traffic_per_iteration(E)
 
     line = {
         "metric": METRIC, "value": value, "unit": "GTEPS", "n_gpus": world,
@@ -367,12 +383,14 @@ def main():
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                      "frac": achieved / hbm, "traffic": traffic,
-                     "kernel": "gather_tile_kernel (segment processing)",
-                     "algorithmic_bytes_per_launch": gather_bytes, "peak_kind": peak_kind,
-                     "avg_launch_ms": gather_s * 1e3},
-        "iteration_roofline": {"bytes_min": bmin, "gteps_at_peak": E / (bmin / (hbm * 1e9)) / 1e9,
-                               "frac": (bmin / seg_iter_s / 1e9) / hbm,
-                               "note": "B_min = 4E + 28V per iteration, of measured HBM copy BW"},
+                     "kernel": "one PageRank iteration (staged gather + L1/L2 gather + fix-up "
+                               "+ merge/update launches)",
+                     "algorithmic_bytes_per_launch": bmin, "peak_kind": peak_kind,
+                     "avg_launch_ms": t_iter_ev * 1e3},
+        "kernels_ms": {"staged_gather": t_staged * 1e3, "cached_gather_and_fixup": t_cached * 1e3,
+                       "merge_update": t_merge * 1e3, "staged_edges": int(info["staged_edges"]),
+                       "subgraph_rows": rows},
+        "gteps_at_hbm_peak": E / (bmin / (hbm * 1e9)) / 1e9,
         "comparisons": {
             "segmented_gteps": E / seg_iter_s / 1e9,
             "plain_original_order_gteps": E / t_plain_orig / 1e9,
@@ -388,7 +406,8 @@ def main():
         "rank_mass": mass,
         "e2e": {"value": e2e_value, "unit": "GTEPS", "h2d_bytes_per_step": 4 * V,
                 "d2h_bytes_per_step": 4 * V, "steps": e2e_steps, "result_ok": e2e_ok},
-        "gpu_launches": args.steps * (2 + ITERS * 3),
+        "gpu_launches": args.steps * (2 + ITERS * (2 + int(info["staged_segments"] > 0) +
+                                                   int(int(info["staged_edges"]) < E))),
         "clocks": clk,
     }
     if rank == 0 and not args.no_cpu_baseline:

@@ -222,6 +222,16 @@ int cg_seg_gather(const cg_segmented *seg, int32_t op, const void *dev_x,
                   void *dev_interm, cudaStream_t stream);
 
 /*
+ * The same pass split into its launches, for callers that time or overlap
+ * them: phases is a bit mask of 1 = the shared-memory (staged) segments,
+ * 2 = the segments read through L1/L2, 4 = the carry fix-up that completes
+ * rows spanning chunks.  The three must all run, in this order, before the
+ * intermBuf is complete; cg_seg_gather runs all of them.
+ */
+int cg_seg_gather_phases(const cg_segmented *seg, int32_t op, const void *dev_x,
+                         void *dev_interm, int32_t phases, cudaStream_t stream);
+
+/*
  * Cache-aware merge alone (Algorithm 4, Section III-C): for each block of
  * merge_block destinations (one warp per block, its accumulator in shared
  * memory), out[v] = identity (0 / INT32_MAX), then for each segment in

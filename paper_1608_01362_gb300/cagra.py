@@ -27,7 +27,7 @@ EXPORTS = [
     "cg_out_degree", "cg_inv_outdeg", "cg_cluster", "cg_relabel_csr", "cg_permute4",
     "pr_build_segments", "cg_segmented_get_info", "pr_plan_bounds", "pr_set_gather_config",
     "pr_gather_table_capacity", "cg_segmented_export",
-    "cg_segmented_destroy", "cg_seg_gather", "merge",
+    "cg_segmented_destroy", "cg_seg_gather", "cg_seg_gather_phases", "merge",
     "pr_init", "pr_contrib", "pr_iterate", "pr_merge_update", "pr_plain_create", "pr_plain_destroy", "pr_iterate_plain",
     "pr_iterate_plain_noalloc", "pr_noalloc_limits",
 ]
@@ -77,6 +77,7 @@ def load(path: str | None = None):
             "cg_segmented_export": (ctypes.c_int, [vp, vp, vp, vp, vp, vp, vp, vp, vp]),
             "cg_segmented_destroy": (ctypes.c_int, [vp]),
             "cg_seg_gather": (ctypes.c_int, [vp, i32, vp, vp, vp]),
+            "cg_seg_gather_phases": (ctypes.c_int, [vp, i32, vp, vp, i32, vp]),
             "merge": (ctypes.c_int, [vp, i32, vp, vp, vp]),
             "pr_init": (ctypes.c_int, [vp, i32, vp, vp, vp, vp]),
             "pr_contrib": (ctypes.c_int, [vp, vp, i32, vp, vp, vp]),
@@ -249,6 +250,14 @@ def cg_segmented_export(seg: Segmented, stream=None) -> dict:
 def cg_seg_gather(seg: Segmented, op: int, x, interm=None, stream=None):
     _check(load().cg_seg_gather(seg.handle, op, _ptr(x), _ptr(interm), _stream(stream)),
            "cg_seg_gather")
+
+
+PHASE_STAGED, PHASE_CACHED, PHASE_FIXUP = 1, 2, 4
+
+
+def cg_seg_gather_phases(seg: Segmented, op: int, x, interm=None, phases: int = 7, stream=None):
+    _check(load().cg_seg_gather_phases(seg.handle, op, _ptr(x), _ptr(interm), phases,
+                                       _stream(stream)), "cg_seg_gather_phases")
 
 
 def merge(seg: Segmented, op: int, interm, out, stream=None):

@@ -269,6 +269,21 @@ int pr_contrib(const float* inv, const float* rank, int32_t V, float* contrib, d
   return CG_OK;
 }
 
+int cg_seg_gather_phases(const cg_segmented* g, int32_t op, const void* x, void* interm,
+                         int32_t phases, cudaStream_t stream) {
+  CG_ARG(g && x, "cg_seg_gather_phases: null argument");
+  CG_ARG(phases >= 0 && phases <= kPhaseAll, "cg_seg_gather_phases: phases must be in [0, 7]");
+  if (!interm) interm = g->interm;
+  if (op == CG_OP_SUM_F32)
+    return run_seg_gather<SumF32>(g->plan, (const float*)x, g->V, (float*)interm, stream,
+                                  phases);
+  if (op == CG_OP_MIN_I32)
+    return run_seg_gather<MinI32>(g->plan, (const int32_t*)x, g->V, (int32_t*)interm, stream,
+                                  phases);
+  set_error("cg_seg_gather_phases: unknown op %d", op);
+  return CG_ERR_INVALID_ARG;
+}
+
 int cg_seg_gather(const cg_segmented* g, int32_t op, const void* x, void* interm,
                   cudaStream_t stream) {
   CG_ARG(g && x, "cg_seg_gather: null argument");

@@ -673,31 +673,34 @@ static int launch_staged(const SegPlan& p, const typename Op::T* x, typename Op:
 
 template <class Op>
 int run_seg_gather(const SegPlan& p, const typename Op::T* x, int32_t nx, typename Op::T* out,
-                   cudaStream_t s) {
+                   cudaStream_t s, int phases) {
   if (p.nchunks == 0) return CG_OK;
   using T = typename Op::T;
   // staged segments [0, m): read from a shared-memory copy
-  if (p.m > 0 && p.ct_split > 0) {
+  if ((phases & kPhaseStaged) && p.m > 0 && p.ct_split > 0) {
     if (p.threads == 1024)
       CG_TRY((launch_staged<Op, 1024>(p, x, out, s)));
     else
       CG_TRY((launch_staged<Op, 512>(p, x, out, s)));
   }
   // the rest through L1/L2: no shared memory, so the whole on-chip store is L1
-  if (p.n_ctiles > p.ct_split) {
+  if ((phases & kPhaseCached) && p.n_ctiles > p.ct_split) {
     seg_gather_kernel<Op, 1024><<<p.grid_l2, 1024, 0, s>>>(
         p.colf, x, nx, p.first_row, p.seg_cstart, p.seg_E, p.seg_chunk, p.seg_ctile, p.seg_lo,
         p.k, p.ct_split, (int32_t)p.n_ctiles, out, reinterpret_cast<T*>(p.carry), p.carry_row);
     CG_LAUNCH_CHECK();
   }
-  carry_fixup_kernel<Op><<<grid_for(p.nchunks, 256, 4), 256, 0, s>>>(
-      reinterpret_cast<const T*>(p.carry), p.carry_row, p.nchunks, p.rows, out);
-  CG_LAUNCH_CHECK();
+  if (phases & kPhaseFixup) {
+    carry_fixup_kernel<Op><<<grid_for(p.nchunks, 256, 4), 256, 0, s>>>(
+        reinterpret_cast<const T*>(p.carry), p.carry_row, p.nchunks, p.rows, out);
+    CG_LAUNCH_CHECK();
+  }
   return CG_OK;
 }
 
-template int run_seg_gather<SumF32>(const SegPlan&, const float*, int32_t, float*, cudaStream_t);
+template int run_seg_gather<SumF32>(const SegPlan&, const float*, int32_t, float*, cudaStream_t,
+                                    int);
 template int run_seg_gather<MinI32>(const SegPlan&, const int32_t*, int32_t, int32_t*,
-                                    cudaStream_t);
+                                    cudaStream_t, int);
 
 }  // namespace cg

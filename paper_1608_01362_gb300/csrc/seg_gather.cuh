@@ -91,8 +91,12 @@ int64_t seg_plan_bytes(const SegPlan& p);
 // Recover the unpadded source array (flags cleared) for export.
 int seg_plan_export_col(const SegPlan& p, const int32_t* rp, int32_t* col, cudaStream_t s);
 
+// Launch phases of one pass (all by default): the staged launch, the L1/L2
+// launch and the carry fix-up, in that order.
+constexpr int kPhaseStaged = 1, kPhaseCached = 2, kPhaseFixup = 4, kPhaseAll = 7;
+
 template <class Op>
 int run_seg_gather(const SegPlan& p, const typename Op::T* x, int32_t nx, typename Op::T* out,
-                   cudaStream_t s);
+                   cudaStream_t s, int phases = kPhaseAll);
 
 }  // namespace cg
