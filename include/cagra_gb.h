@@ -324,6 +324,33 @@ int pr_iterate_plain(const cg_plain *plain, const float *dev_inv,
                      double *dev_dangling_io, double *dev_resid,
                      int32_t probe, cudaStream_t stream);
 
+/* ---------------------------------------------------- label propagation */
+
+/*
+ * One synchronous label-propagation pass over the segmented graph (the LP
+ * application of Section VI, Table IV; min-label connected components):
+ * L'[v] = min(L[v], min over the in-neighbours u of v of L[u]), computed as
+ * Algorithm 3's gather with a minimum, Algorithm 4's merge with a minimum and
+ * the label update, all in int32 (exact).  For connected components the graph
+ * must hold both directions of every edge.  dev_labels_in / dev_labels_out:
+ * int32[V] (must not alias).  dev_changed: device int64 receiving the number
+ * of labels this pass changed (NULL: a slot of the handle).  host_changed:
+ * if non-NULL the call synchronizes the stream and stores that number.
+ */
+int lp_iterate(const cg_segmented *seg, const int32_t *dev_labels_in,
+               int32_t *dev_labels_out, int64_t *dev_changed,
+               int64_t *host_changed, cudaStream_t stream);
+
+/*
+ * Passes of lp_iterate until one changes no label (or max_passes): labels in
+ * place (device int32[V]).  *host_passes = passes run (the last one changed
+ * nothing unless max_passes stopped the loop); host_changes (host int64
+ * [max_passes], may be NULL) receives each pass's count.  Synchronizes once
+ * per pass (the stopping test reads the count).
+ */
+int lp_run(const cg_segmented *seg, int32_t *dev_labels, int64_t max_passes,
+           int64_t *host_passes, int64_t *host_changes, cudaStream_t stream);
+
 /* ------------------------------------------------- no device allocation */
 
 /*

@@ -30,6 +30,7 @@ EXPORTS = [
     "cg_segmented_destroy", "cg_seg_gather", "cg_seg_gather_phases", "merge",
     "pr_init", "pr_contrib", "pr_iterate", "pr_merge_update", "pr_plain_create", "pr_plain_destroy", "pr_iterate_plain",
     "pr_iterate_plain_noalloc", "pr_noalloc_limits",
+    "lp_iterate", "lp_run",
 ]
 
 
@@ -90,6 +91,8 @@ def load(path: str | None = None):
             "pr_iterate_plain_noalloc": (ctypes.c_int, [vp, vp, i32, i64, vp, vp, vp, vp, vp, dbl,
                                                         vp, vp, vp]),
             "pr_noalloc_limits": (ctypes.c_int, [vp, vp, vp]),
+            "lp_iterate": (ctypes.c_int, [vp, vp, vp, vp, vp, vp]),
+            "lp_run": (ctypes.c_int, [vp, vp, i64, vp, vp, vp]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)
@@ -343,3 +346,24 @@ def pr_noalloc_limits():
     _check(load().pr_noalloc_limits(ctypes.byref(mv), ctypes.byref(me), ctypes.byref(sb)),
            "pr_noalloc_limits")
     return {"max_vertices": mv.value, "max_edges": me.value, "scratch_bytes": sb.value}
+
+
+# ------------------------------------------------------------------ label propagation
+
+def lp_iterate(seg: Segmented, labels_in, labels_out, dev_changed=None, sync: bool = True,
+               stream=None):
+    """One pass; returns the number of changed labels when sync is True."""
+    h = ctypes.c_int64()
+    _check(load().lp_iterate(seg.handle, _ptr(labels_in), _ptr(labels_out), _ptr(dev_changed),
+                             ctypes.byref(h) if sync else None, _stream(stream)), "lp_iterate")
+    return h.value if sync else None
+
+
+def lp_run(seg: Segmented, labels, max_passes: int = 1 << 20, stream=None):
+    """Passes until no label changes; returns (passes, changes per pass)."""
+    cap = min(max_passes, 1 << 16)
+    ch = np.zeros(cap, dtype=np.int64)
+    p = ctypes.c_int64()
+    _check(load().lp_run(seg.handle, _ptr(labels), cap, ctypes.byref(p), ch.ctypes.data,
+                         _stream(stream)), "lp_run")
+    return p.value, ch[:p.value].copy()

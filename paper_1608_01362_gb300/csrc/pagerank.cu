@@ -23,70 +23,6 @@ namespace {
 
 
 
-// ---------------------------------------------------------------------------
-// Cache-aware merge (Algorithm 4).  Each warp owns one merge block of B
-// destinations (a shared-memory accumulator of B values) and walks the
-// segments in ascending order: for segment s it adds the block's rows
-// [blk[s][b], blk[s][b+1]) of intermBuf into acc[idx_map[i] - b*B].  Inside
-// one segment the destinations are distinct, so lanes never collide; the
-// warp synchronises between segments, which keeps the per-destination order
-// fixed (deterministic).  The first rows of four segments are loaded
-// together before they are applied in order, and no block-wide barrier is
-// involved, so the k segments do not serialise k memory round trips.
-// ---------------------------------------------------------------------------
-
-template <class Op>
-__device__ __forceinline__ void warp_merge(const int32_t* __restrict__ blk,
-                                           const int32_t* __restrict__ idx_map,
-                                           const typename Op::T* __restrict__ interm, int k,
-                                           int nb, int64_t mb, int64_t v0, int n,
-                                           typename Op::T* acc) {
-  using T = typename Op::T;
-  constexpr int G = 4;  // segments whose first rows are loaded together
-  const int lane = threadIdx.x & 31;
-  for (int i = lane; i < n; i += 32) acc[i] = Op::identity();
-  __syncwarp();
-  for (int s0 = 0; s0 < k; s0 += 32) {
-    const int ls = s0 + lane;
-    int32_t lo = 0, hi = 0;
-    if (ls < k) {
-      lo = __ldg(blk + (int64_t)ls * (nb + 1) + mb);
-      hi = __ldg(blk + (int64_t)ls * (nb + 1) + mb + 1);
-    }
-    const int cnt = k - s0 < 32 ? k - s0 : 32;
-    for (int t0 = 0; t0 < cnt; t0 += G) {
-      int32_t ii[G], hh[G], dd[G];
-      T xx[G];
-#pragma unroll
-      for (int u = 0; u < G; ++u) {  // first (up to 32) rows of G segments in flight
-        const int t = t0 + u < 31 ? t0 + u : 31;
-        ii[u] = __shfl_sync(0xffffffffu, lo, t) + lane;
-        hh[u] = t0 + u < cnt ? __shfl_sync(0xffffffffu, hi, t) : 0;
-        dd[u] = 0;
-        xx[u] = Op::identity();
-        if (ii[u] < hh[u]) {
-          dd[u] = __ldcs(idx_map + ii[u]);
-          xx[u] = __ldcs(interm + ii[u]);
-        }
-      }
-#pragma unroll
-      for (int u = 0; u < G; ++u) {  // apply in segment order
-        if (ii[u] < hh[u]) {
-          const int64_t lv = (int64_t)dd[u] - v0;
-          if ((uint64_t)lv < (uint64_t)n) acc[lv] = Op::op(acc[lv], xx[u]);
-        }
-        for (int32_t i = ii[u] + 32; i < hh[u]; i += 32) {  // segments with > 32 rows here
-          const int64_t lv = (int64_t)__ldcs(idx_map + i) - v0;
-          const T x = __ldcs(interm + i);
-          if ((uint64_t)lv < (uint64_t)n) acc[lv] = Op::op(acc[lv], x);
-        }
-        __syncwarp();
-      }
-    }
-  }
-  __syncwarp();
-}
-
 // Cache-aware merge (Algorithm 4) fused with the vertex update.
 __global__ void __launch_bounds__(kMergeWarps * 32, 6)
 merge_update_kernel(const int32_t* __restrict__ blk, const int32_t* __restrict__ idx_map,

@@ -193,3 +193,38 @@ def autotune_segments(graph: Graph, candidates=None, merge_block: int = 512,
 
 def build_candidate(graph: Graph, cand: dict, merge_block: int = 512) -> SegmentedPageRank:
     return _build(graph, cand, merge_block)
+
+
+class LabelPropagation:
+    """Min-label propagation (connected components of a symmetric graph)
+    through the segmented structure.  Labels start at each vertex's original
+    ID, carried through the clustering permutation, so the result is the
+    smallest original ID in each component whatever the renumbering."""
+
+    def __init__(self, graph: Graph, num_segments: int | None = None, bounds=None,
+                 merge_block: int = 512, threads: int = 1024, ctas_per_sm: int = 1,
+                 table_vertices: int = -1):
+        self.g = graph
+        if bounds is not None:
+            bounds = np.asarray(bounds, dtype=np.int64)
+            num_segments = len(bounds) - 1
+        self.seg = C.pr_build_segments(graph.offsets, graph.src, num_segments, bounds=bounds,
+                                       merge_block=merge_block)
+        if (threads, ctas_per_sm, table_vertices) != (1024, 1, -1):
+            C.pr_set_gather_config(self.seg, threads, ctas_per_sm, table_vertices)
+        V = graph.V
+        self.labels = [torch.empty(V, dtype=torch.int32, device=graph.device) for _ in range(2)]
+
+    def init(self):
+        if self.g.old_of_new is None:
+            self.labels[0].copy_(torch.arange(self.g.V, dtype=torch.int32,
+                                              device=self.g.device))
+        else:
+            self.labels[0].copy_(self.g.old_of_new)
+        return self.labels[0]
+
+    def run(self, max_passes: int = 1 << 20):
+        """Returns (labels in original IDs, passes, changes per pass)."""
+        lab = self.init()
+        passes, changes = C.lp_run(self.seg, lab, max_passes)
+        return self.g.to_original(lab), passes, changes
