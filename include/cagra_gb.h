@@ -351,6 +351,41 @@ int lp_iterate(const cg_segmented *seg, const int32_t *dev_labels_in,
 int lp_run(const cg_segmented *seg, int32_t *dev_labels, int64_t max_passes,
            int64_t *host_passes, int64_t *host_changes, cudaStream_t stream);
 
+/* ------------------------------------------- batched small-graph PageRank */
+
+typedef struct cg_batch cg_batch;
+
+/*
+ * Many independent small graphs for one-launch PageRank (the batched form of
+ * the segmented gather; the paper has one graph at a time).  Each graph is
+ * its own single shared-memory segment: its contrib vector lives in one
+ * SM's shared memory for all iterations.  Input: G graphs concatenated as one
+ * in-edge CSR -- host_vbase (host int64[G+1], vbase[0] = 0) gives each
+ * graph's vertex range, dev_offsets (device int64[V_total+1]) are global edge
+ * offsets, dev_src (device int32[E_total]) holds sources LOCAL to their graph
+ * (in [0, V_g)).  Every graph has 1..65536 vertices and must fit one block's
+ * shared memory (CG_ERR_UNSUPPORTED otherwise).  The arrays are copied into
+ * the handle (flagged edges, per-graph out-degrees); synchronizes.
+ */
+int pr_batch_create(int32_t G, const int64_t *host_vbase, const int64_t *dev_offsets,
+                    const int32_t *dev_src, cg_batch **out, cudaStream_t stream);
+int pr_batch_destroy(cg_batch *batch);
+
+/* Threads per block of the batched launch (256, 512 or 1024; default 1024). */
+int pr_batch_set_threads(cg_batch *batch, int32_t threads);
+
+/*
+ * PageRank of every graph of the batch in ONE persistent launch: r_0 = 1/V_g,
+ * `iterations` normalised iterations with uniform dangling redistribution
+ * (the same arithmetic as pr_iterate on each graph alone).  Graphs are taken
+ * largest first by an atomic counter; a block runs all iterations of its
+ * graph on chip.  dev_rank: float[V_total] receives the ranks (graph g's at
+ * vbase[g]); dev_resid: double[G*iterations] (graph-major) or NULL.  Stream-
+ * ordered and capturable in a CUDA graph (a memset and one kernel).
+ */
+int pr_batch_run(cg_batch *batch, int32_t iterations, double damping, float *dev_rank,
+                 double *dev_resid, cudaStream_t stream);
+
 /* ------------------------------------------------- no device allocation */
 
 /*

@@ -31,6 +31,7 @@ EXPORTS = [
     "pr_init", "pr_contrib", "pr_iterate", "pr_merge_update", "pr_plain_create", "pr_plain_destroy", "pr_iterate_plain",
     "pr_iterate_plain_noalloc", "pr_noalloc_limits",
     "lp_iterate", "lp_run",
+    "pr_batch_create", "pr_batch_destroy", "pr_batch_set_threads", "pr_batch_run",
 ]
 
 
@@ -93,6 +94,10 @@ def load(path: str | None = None):
             "pr_noalloc_limits": (ctypes.c_int, [vp, vp, vp]),
             "lp_iterate": (ctypes.c_int, [vp, vp, vp, vp, vp, vp]),
             "lp_run": (ctypes.c_int, [vp, vp, i64, vp, vp, vp]),
+            "pr_batch_create": (ctypes.c_int, [i32, vp, vp, vp, ctypes.POINTER(vp), vp]),
+            "pr_batch_destroy": (ctypes.c_int, [vp]),
+            "pr_batch_set_threads": (ctypes.c_int, [vp, i32]),
+            "pr_batch_run": (ctypes.c_int, [vp, i32, dbl, vp, vp, vp]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)
@@ -367,3 +372,42 @@ def lp_run(seg: Segmented, labels, max_passes: int = 1 << 20, stream=None):
     _check(load().lp_run(seg.handle, _ptr(labels), cap, ctypes.byref(p), ch.ctypes.data,
                          _stream(stream)), "lp_run")
     return p.value, ch[:p.value].copy()
+
+
+# ------------------------------------------------------------------ batched small graphs
+
+class Batch:
+    """Owner of a cg_batch handle."""
+
+    def __init__(self, handle: int, G: int, vbase):
+        self.handle = handle
+        self.G = G
+        self.vbase = vbase
+
+    def __del__(self):
+        self.close()
+
+    def close(self):
+        if getattr(self, "handle", None):
+            try:
+                load().pr_batch_destroy(self.handle)
+            finally:
+                self.handle = None
+
+
+def pr_batch_create(vbase, offsets, src, stream=None) -> Batch:
+    vb = np.ascontiguousarray(np.asarray(vbase, dtype=np.int64))
+    G = vb.shape[0] - 1
+    h = ctypes.c_void_p()
+    _check(load().pr_batch_create(G, vb.ctypes.data, _ptr(offsets), _ptr(src), ctypes.byref(h),
+                                  _stream(stream)), "pr_batch_create")
+    return Batch(h.value, G, vb)
+
+
+def pr_batch_set_threads(batch: Batch, threads: int):
+    _check(load().pr_batch_set_threads(batch.handle, threads), "pr_batch_set_threads")
+
+
+def pr_batch_run(batch: Batch, iterations: int, damping: float, rank, resid=None, stream=None):
+    _check(load().pr_batch_run(batch.handle, iterations, damping, _ptr(rank), _ptr(resid),
+                               _stream(stream)), "pr_batch_run")

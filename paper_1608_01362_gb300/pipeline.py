@@ -228,3 +228,39 @@ class LabelPropagation:
         lab = self.init()
         passes, changes = C.lp_run(self.seg, lab, max_passes)
         return self.g.to_original(lab), passes, changes
+
+
+def concat_graphs(graphs):
+    """Concatenate in-edge CSRs (numpy offsets int64, src int32, local IDs)
+    into the batched layout: (vbase, global offsets, local sources)."""
+    vbase = np.zeros(len(graphs) + 1, dtype=np.int64)
+    ebase = np.zeros(len(graphs) + 1, dtype=np.int64)
+    for i, g in enumerate(graphs):
+        vbase[i + 1] = vbase[i] + (len(g.offsets) - 1)
+        ebase[i + 1] = ebase[i] + len(g.src)
+    offsets = np.empty(vbase[-1] + 1, dtype=np.int64)
+    src = np.empty(ebase[-1], dtype=np.int32)
+    for i, g in enumerate(graphs):
+        offsets[vbase[i]:vbase[i + 1]] = np.asarray(g.offsets[:-1]) + ebase[i]
+        src[ebase[i]:ebase[i + 1]] = g.src
+    offsets[-1] = ebase[-1]
+    return vbase, offsets, src
+
+
+class BatchedPageRank:
+    """PageRank of many small graphs in one persistent launch."""
+
+    def __init__(self, graphs, device="cuda", threads: int = 1024):
+        vbase, offsets, src = concat_graphs(graphs)
+        self.device = torch.device(device)
+        self.vbase = vbase
+        self.offsets = torch.as_tensor(offsets).to(self.device)
+        self.src = torch.as_tensor(src).to(self.device)
+        self.batch = C.pr_batch_create(vbase, self.offsets, self.src)
+        if threads != 1024:
+            C.pr_batch_set_threads(self.batch, threads)
+        self.rank = torch.empty(int(vbase[-1]), dtype=torch.float32, device=self.device)
+
+    def run(self, iterations: int = 20, damping: float = 0.85, resid=None):
+        C.pr_batch_run(self.batch, iterations, damping, self.rank, resid)
+        return self.rank

@@ -1,0 +1,80 @@
+"""Batched small-graph PageRank (one persistent launch) against the FP64
+oracle graph by graph, and against itself when captured in a CUDA graph."""
+import numpy as np
+import pytest
+
+import graphgen
+import oracle as O
+
+pytestmark = pytest.mark.gpu
+
+TOL_L1 = 1e-5
+RESID_FLOOR = 2.4e-7
+
+
+@pytest.fixture(scope="module")
+def C():
+    import torch
+    assert torch.cuda.is_available()
+    from paper_1608_01362_gb300 import build, cagra
+    build.build()
+    cagra.load()
+    return cagra
+
+
+def _batch_graphs():
+    gs = graphgen.small_graph_batch(count=40, seed=7, scale_lo=5, scale_hi=12)
+    gs.append(graphgen.from_edges(1, [], []))                                  # one vertex
+    n = 700
+    gs.append(graphgen.from_edges(n, np.arange(n), (np.arange(n) + 1) % n))     # cycle
+    gs.append(graphgen.from_edges(n + 1, np.arange(1, n + 1), np.zeros(n, int)))  # in-star
+    gs.append(graphgen.from_edges(5, [], []))                                  # isolated
+    return gs
+
+
+@pytest.mark.parametrize("threads", [1024, 256])
+def test_batched_matches_oracle_per_graph(C, threads):
+    import torch
+    from paper_1608_01362_gb300 import pipeline as P
+    gs = _batch_graphs()
+    bp = P.BatchedPageRank(gs, threads=threads)
+    resid = torch.zeros(len(gs) * 20, dtype=torch.float64, device="cuda")
+    rank = bp.run(20, resid=resid).cpu().numpy()
+    res = resid.cpu().numpy().reshape(len(gs), 20)
+    for i, g in enumerate(gs):
+        want, wres = O.pagerank(g.offsets, g.src, iters=20)
+        got = rank[bp.vbase[i]:bp.vbase[i + 1]].astype(np.float64)
+        err = np.abs(got - want).sum() / np.abs(want).sum()
+        assert err <= TOL_L1, (i, err)
+        assert np.all(np.abs(res[i] - wres) <= 1e-2 * wres + RESID_FLOOR), i
+
+
+def test_batched_cuda_graph_replay_and_determinism(C):
+    import torch
+    from paper_1608_01362_gb300 import pipeline as P
+    gs = _batch_graphs()
+    bp = P.BatchedPageRank(gs)
+    first = bp.run(20).clone()
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(s):
+        bp.run(20)  # warm-up on the capture stream
+        torch.cuda.synchronize()
+        with torch.cuda.graph(graph, stream=s):
+            C.pr_batch_run(bp.batch, 20, 0.85, bp.rank)
+    torch.cuda.current_stream().wait_stream(s)
+    bp.rank.zero_()
+    graph.replay()
+    torch.cuda.synchronize()
+    assert torch.equal(bp.rank, first)
+
+
+def test_batch_rejects_oversized_graph(C):
+    import torch
+    V = 70000
+    vb = np.array([0, V], dtype=np.int64)
+    off = torch.zeros(V + 1, dtype=torch.int64, device="cuda")
+    src = torch.zeros(1, dtype=torch.int32, device="cuda")
+    with pytest.raises(C.CagraError, match="65536"):
+        C.pr_batch_create(vb, off, src)
