@@ -325,6 +325,172 @@ def run_batched(args):
     print(json.dumps(line), flush=True)
 
 
+def ppr_seeds(g, n=64, seed=1):
+    """n seed vertices: the source endpoints of n edges drawn uniformly by a
+    seeded SplitMix64 stream (vertices with out-edges, degree-weighted)."""
+    import graphgen
+    draws = graphgen.splitmix_draws(seed, 0, n)
+    return g.src[(draws % np.uint64(len(g.src))).astype(np.int64)].astype(np.int32)
+
+
+def _ppr_bounds(nd, V, k):
+    """k uniform segments over the sources with out-edges [0, nd) of the
+    clustered numbering, and one edgeless segment [nd, V)."""
+    b = [int(round(i * nd / k)) for i in range(k + 1)]
+    if nd < V:
+        b.append(V)
+    return np.unique(np.asarray(b, dtype=np.int64))
+
+
+def run_ppr(args):
+    """64 personalised PageRank vectors on a directed RMAT graph (default
+    scale 22), 20 iterations, rank matrix stored as BF16 hi+lo planes with
+    FP32 accumulation: one batched solve against 64 single-vector solves."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1608_01362_gb300 import cagra as C
+    from paper_1608_01362_gb300 import pipeline as P
+    scale = args.scale if args.scale != 25 else 22
+    g, gen_s = make_graph(scale)
+    graph = P.Graph(g.offsets, g.src, cluster_mode=0)
+    nd = int((graph.outdeg > 0).sum().item())
+    seeds = ppr_seeds(g)
+    ev = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
+
+    def time_solve(b, reps=2, iters=ITERS):
+        b.init(seeds)
+        C.ppr_batched_iterate(b.ppr, graph.inv, DAMPING, 2)
+        torch.cuda.synchronize()
+        a, z = ev(), ev()
+        a.record()
+        for _ in range(reps):
+            C.ppr_batched_iterate(b.ppr, graph.inv, DAMPING, iters)
+        z.record()
+        z.synchronize()
+        return a.elapsed_time(z) / 1e3 / (reps * iters)
+
+    # autotune the segment count (Section III-D's trade-off, 64-wide rows)
+    tune = {}
+    best = None
+    for planes in (2, 1):
+        for k in (args.k,) if args.k else (1, 2, 4, 8, 16, 32):
+            b = P.BatchedPPR(graph, bounds=_ppr_bounds(nd, graph.V, k), planes=planes)
+            t = time_solve(b, reps=1, iters=5)
+            tune[f"planes{planes}_k{k}"] = {"ms_per_iter": t * 1e3, "q": b.seg.info["q"],
+                                            "bytes": b.ppr.bytes}
+            if planes == 2 and (best is None or t < tune[f"planes2_k{best}"]["ms_per_iter"] / 1e3):
+                best = k
+            del b
+    b = P.BatchedPPR(graph, bounds=_ppr_bounds(nd, graph.V, best), planes=2)
+    info = b.seg.info
+    # timed: steps x (init + 20 iterations), inputs resident in HBM (the
+    # 1 GB rank matrix and 0.5 GB BF16 planes exceed L2: no flush needed)
+    for _ in range(args.warmup):
+        b.init(seeds)
+        C.ppr_batched_iterate(b.ppr, graph.inv, DAMPING, ITERS, b.rank)
+    torch.cuda.synchronize()
+    clk = ClockSampler(int(os.environ.get("LOCAL_RANK", "0")))
+    clk.start()
+    a, z = ev(), ev()
+    a.record()
+    for _ in range(args.steps):
+        b.init(seeds)
+        C.ppr_batched_iterate(b.ppr, graph.inv, DAMPING, ITERS, b.rank)
+    z.record()
+    z.synchronize()
+    clocks = clk.stop()
+    t_step = a.elapsed_time(z) / 1e3 / args.steps
+    # per launch of one iteration
+    phase_ms = {}
+    for ph, name in ((1, "gather"), (2, "fixup"), (4, "merge")):
+        b.init(seeds)
+        C.ppr_batched_iterate(b.ppr, graph.inv, DAMPING, 2)
+        ts = []
+        for _ in range(5):
+            C.ppr_batched_step(b.ppr, graph.inv, DAMPING, 7 - ph)  # the others, untimed
+            e0, e1 = ev(), ev()
+            e0.record()
+            C.ppr_batched_step(b.ppr, graph.inv, DAMPING, ph)
+            e1.record()
+            e1.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        phase_ms[name] = float(np.median(ts))
+    # result in original IDs, errors against the oracle on sampled columns
+    b.init(seeds)
+    R, resid = b.run(seeds, ITERS)
+    Rh = R.cpu().numpy()
+    import oracle
+    cols = np.array([0, 21, 42, 63])
+    t0 = time.time()
+    want = oracle.ppr(g.offsets, g.src, seeds[cols], iters=ITERS)
+    oracle_s = time.time() - t0
+    err = np.abs(Rh[:, cols].astype(np.float64) - want).sum(0) / np.abs(want).sum(0)
+    # 64 single-vector solves through the segmented PageRank path
+    cand, _ = P.autotune_segments(graph)
+    sp = P.build_candidate(graph, cand)
+    r1, _ = sp.run_ppr(int(seeds[0]), ITERS)
+    err1 = float(np.abs(r1.cpu().numpy() - want[:, 0]).sum() / np.abs(want[:, 0]).sum())
+    torch.cuda.synchronize()
+    a.record()
+    for s in seeds:
+        sp.run_ppr(int(s), ITERS)
+    z.record()
+    z.synchronize()
+    t_single = a.elapsed_time(z) / 1e3
+    # end to end through the public API: seeds in from the host, R out to pinned host memory
+    Rhost = torch.empty_like(b.rank, device="cpu").pin_memory()
+    torch.cuda.synchronize()
+    a.record()
+    for _ in range(max(1, args.steps // 2)):
+        b.run(seeds, ITERS)
+        Rhost.copy_(b.rank, non_blocking=True)
+    z.record()
+    z.synchronize()
+    t_e2e = a.elapsed_time(z) / 1e3 / max(1, args.steps // 2)
+    # roofline of the dominant launch (algorithmic bytes per launch)
+    pl = 2
+    cbytes = 128 * pl * nd
+    rows = int(info["rows"])
+    alg = {"gather": 4 * g.E + cbytes + 256 * rows + 8 * b.ppr.chunks,
+           "fixup": 0, "merge": 256 * rows + 4 * rows + 8 * graph.V + cbytes}
+    dom = max(("gather", "merge"), key=lambda n: phase_ms[n])
+    peak, peak_kind = _peaks()
+    ach = alg[dom] / (phase_ms[dom] / 1e3) / 1e9
+    edge_cols = g.E * 64 * ITERS
+    line = {"metric": "batched personalised PageRank: edge-vector GTEPS (64 vectors x 20 "
+                      "iterations) at BF16 hi+lo storage",
+            "value": edge_cols / t_step / 1e9, "unit": "GTEPS (edge x vector)", "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_step * 1e3,
+            "higher_is_better": True, "dtype": "bf16x2 storage, f32 accumulate",
+            "data": "synthetic",
+            "config": {"workload": f"ppr64_rmat{scale}_ef16", "V": g.V, "E": g.E,
+                       "nondangling": nd, "segments": info["num_segments"], "q": info["q"],
+                       "planes": 2, "l2_flush": "inputs larger than L2"},
+            "vs_baseline": None,
+            "kernels_ms_per_iteration": phase_ms,
+            "roofline": {"bound": "hbm", "kernel": dom, "achieved": ach, "peak": peak,
+                         "unit": "GB/s", "frac": ach / peak, "traffic": None,
+                         "peak_source": peak_kind, "algorithmic_bytes": alg[dom]},
+            "single_vector_64_runs_ms": t_single * 1e3,
+            "speedup_vs_64_single_runs": t_single / t_step,
+            "rel_l1_vs_oracle_sampled_columns": {int(c): float(e) for c, e in zip(cols, err)},
+            "single_vector_rel_l1_col0": err1,
+            "autotune": tune, "clocks": clocks,
+            "e2e": {"value": edge_cols / t_e2e / 1e9, "unit": "GTEPS (edge x vector)",
+                    "h2d_bytes_per_step": 64 * 4, "d2h_bytes_per_step": int(Rhost.numel() * 4)},
+            "gpu_launches": args.steps * (3 * ITERS + 1),
+            "generate_host_s": gen_s, "oracle_4_columns_s": oracle_s}
+    if not args.no_cpu_baseline:
+        t0 = time.time()
+        oracle.ppr(g.offsets, g.src, seeds, iters=1)
+        t1 = time.time() - t0
+        line["cpu_baseline"] = {"value": g.E * 64 / t1 / 1e9, "unit": "GTEPS (edge x vector)",
+                                "cores": oracle.num_threads(), "kind": "oracle",
+                                "sample": "one iteration of all 64 vectors over the full graph"}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -341,7 +507,7 @@ def main():
     ap.add_argument("--merge-block", type=int, default=512)
     ap.add_argument("--sweep", action="store_true", help="k = 1..64 sweep table")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="pagerank", choices=["pagerank", "lp", "batched"],
+    ap.add_argument("--workload", default="pagerank", choices=["pagerank", "lp", "batched", "ppr"],
                     help="pagerank (the headline), lp (label propagation, RMAT-24 undirected) "
                          "or batched (1,024 small RMAT graphs, scales 8-15)")
     ap.add_argument("--graphs", type=int, default=1024, help="graphs of the batched workload")
@@ -350,6 +516,8 @@ def main():
         return run_reference(args)
     if args.workload == "lp":
         return run_lp(args)
+    if args.workload == "ppr":
+        return run_ppr(args)
     if args.workload == "batched":
         return run_batched(args)
 

@@ -106,6 +106,16 @@ int cg_relabel_csr(const int64_t *dev_offsets, const int32_t *dev_src,
 int cg_permute4(const void *dev_in, int64_t n_in, const int32_t *dev_idx,
                 int64_t n, void *dev_out, cudaStream_t stream);
 
+/*
+ * The same gather for rows of row_bytes bytes (a positive multiple of 16;
+ * both buffers 16-byte aligned): row i of dev_out = row idx[i] of dev_in
+ * (zeros where idx[i] is outside [0, n_in)).  Carries per-vertex rows, such
+ * as the 64 ranks per vertex of the batched personalised PageRank, between
+ * numberings.  in/out must not alias.
+ */
+int cg_permute_rows(const void *dev_in, int64_t n_in, int32_t row_bytes,
+                    const int32_t *dev_idx, int64_t n, void *dev_out, cudaStream_t stream);
+
 /* ---------------------------------------------------------------- segmenting */
 
 typedef struct cg_segmented cg_segmented;
@@ -297,6 +307,25 @@ int pr_merge_update(const cg_segmented *seg, const float *dev_inv,
                     float *dev_contrib_out, double damping, const double *dev_D_in,
                     double *dev_D_out, double *dev_resid_out, cudaStream_t stream);
 
+/*
+ * Personalised PageRank, one vector (the personalised form of the PageRank
+ * application; the paper runs the uniform form): the teleport and the
+ * dangling mass return to one seed vertex instead of spreading over all V,
+ *   rank'[v] = d sum_{u->v} contrib[u] + [v == seed] ((1-d) + d D).
+ * pr_init_ppr writes the start state rank = one-hot at the seed, contrib =
+ * rank * inv, *dev_dangling = 1 if the seed has no out-edges, else 0.
+ * pr_iterate_ppr runs `iterations` of it through the segmented graph with
+ * the same arguments, buffers and FP64 reductions as pr_iterate.  seed must
+ * be in [0, V) (CG_ERR_INVALID_ARG otherwise).
+ */
+int pr_init_ppr(const float *dev_inv, int32_t V, int32_t seed, float *dev_rank,
+                float *dev_contrib, double *dev_dangling, cudaStream_t stream);
+int pr_iterate_ppr(const cg_segmented *seg, const float *dev_inv,
+                   const float *dev_rank_in, const float *dev_contrib_in,
+                   float *dev_rank_out, float *dev_contrib_out, double damping,
+                   int32_t iterations, int32_t seed, double *dev_dangling_io,
+                   double *dev_resid, cudaStream_t stream);
+
 /* The plain pull baseline (Algorithm 1 without segmenting). */
 typedef struct cg_plain cg_plain;
 
@@ -385,6 +414,61 @@ int pr_batch_set_threads(cg_batch *batch, int32_t threads);
  */
 int pr_batch_run(cg_batch *batch, int32_t iterations, double damping, float *dev_rank,
                  double *dev_resid, cudaStream_t stream);
+
+/* ----------------------------------- batched personalised PageRank (64) */
+
+typedef struct cg_ppr cg_ppr;
+
+/*
+ * 64 personalised PageRank vectors advanced together over one segmented
+ * graph (the paper computes one vector at a time; this is its gather and
+ * merge with 64-wide rows, an SpMM with a dense 64-column operand).  Column j
+ * teleports to seed_j and returns its dangling mass there:
+ *   R'[v][j] = d sum_{u->v} C[u][j] + [v == seed_j] ((1-d) + d D_j)
+ *   C'[v][j] = R'[v][j] * inv[v],  D'_j = sum over inv[v] = 0 of R'[v][j]
+ * The state C is held by the handle as BF16: planes = 2 stores hi = bf16(c)
+ * and lo = bf16(c - hi) (about 16 significant bits), planes = 1 stores hi
+ * only (8 bits, half the gather traffic); sums are FP32, D_j and residuals
+ * FP64.  The segmented graph must outlive the handle and stay unchanged.
+ * Memory: about rows*256 + V*(256 + 128*planes) + E/128*260 bytes.
+ * Synchronizes.
+ */
+int ppr_batched_create(const cg_segmented *seg, int32_t planes, cg_ppr **out,
+                       cudaStream_t stream);
+int ppr_batched_destroy(cg_ppr *ppr);
+
+/* Device bytes held by the handle and its number of 128-edge gather chunks. */
+int ppr_batched_bytes(const cg_ppr *ppr, int64_t *bytes, int64_t *chunks);
+
+/*
+ * Start state: R_0 = one-hot at each column's seed.  host_seeds: host
+ * int32[64], each in [0, V) (repeats allowed).  dev_inv: float[V], the
+ * reciprocal out-degrees of the segmented graph's vertices.  Synchronizes.
+ */
+int ppr_batched_init(cg_ppr *ppr, const float *dev_inv, const int32_t *host_seeds,
+                     cudaStream_t stream);
+
+/*
+ * `iterations` iterations from the handle's current state.  dev_rank_out
+ * (float[V][64], row-major: vertex v's 64 values contiguous, or NULL)
+ * receives R after the last iteration.  dev_resid (double[64] or NULL; needs
+ * iterations >= 2 and dev_rank_out) receives sum_v |R_T[v][j] - R_{T-1}[v][j]|
+ * per column.  Stream-ordered; capturable in a CUDA graph.
+ */
+int ppr_batched_iterate(cg_ppr *ppr, const float *dev_inv, double damping,
+                        int32_t iterations, float *dev_rank_out, double *dev_resid,
+                        cudaStream_t stream);
+
+/*
+ * One iteration's launches selected by `phases` (1 gather, 2 carry fix-up,
+ * 4 merge + update; 7 = one whole iteration), for timing each launch.  The
+ * merge writes R' to dev_rank_out when non-NULL and, when dev_rank_old is
+ * given, the per-column L1 distance to it in dev_resid (double[64], may be
+ * NULL).
+ */
+int ppr_batched_step(cg_ppr *ppr, const float *dev_inv, double damping, int32_t phases,
+                     const float *dev_rank_old, float *dev_rank_out, double *dev_resid,
+                     cudaStream_t stream);
 
 /* ------------------------------------------------- no device allocation */
 

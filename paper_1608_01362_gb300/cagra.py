@@ -25,6 +25,7 @@ CG_OP_MIN_I32 = 1
 EXPORTS = [
     "cg_status_string", "cg_last_error_message", "cg_version",
     "cg_out_degree", "cg_inv_outdeg", "cg_cluster", "cg_relabel_csr", "cg_permute4",
+    "cg_permute_rows",
     "pr_build_segments", "cg_segmented_get_info", "pr_plan_bounds", "pr_set_gather_config",
     "pr_gather_table_capacity", "cg_segmented_export",
     "cg_segmented_destroy", "cg_seg_gather", "cg_seg_gather_phases", "merge",
@@ -32,6 +33,9 @@ EXPORTS = [
     "pr_iterate_plain_noalloc", "pr_noalloc_limits",
     "lp_iterate", "lp_run",
     "pr_batch_create", "pr_batch_destroy", "pr_batch_set_threads", "pr_batch_run",
+    "pr_init_ppr", "pr_iterate_ppr",
+    "ppr_batched_create", "ppr_batched_destroy", "ppr_batched_bytes", "ppr_batched_init",
+    "ppr_batched_iterate", "ppr_batched_step",
 ]
 
 
@@ -70,6 +74,7 @@ def load(path: str | None = None):
             "cg_cluster": (ctypes.c_int, [vp, i32, i64, i32, vp, vp, vp]),
             "cg_relabel_csr": (ctypes.c_int, [vp, vp, i32, i64, vp, vp, vp, vp, vp]),
             "cg_permute4": (ctypes.c_int, [vp, i64, vp, i64, vp, vp]),
+            "cg_permute_rows": (ctypes.c_int, [vp, i64, i32, vp, i64, vp, vp]),
             "pr_build_segments": (ctypes.c_int, [vp, vp, i32, i64, i32, vp, i32,
                                                  ctypes.POINTER(vp), vp]),
             "cg_segmented_get_info": (ctypes.c_int, [vp, ctypes.POINTER(SegInfo)]),
@@ -98,6 +103,15 @@ def load(path: str | None = None):
             "pr_batch_destroy": (ctypes.c_int, [vp]),
             "pr_batch_set_threads": (ctypes.c_int, [vp, i32]),
             "pr_batch_run": (ctypes.c_int, [vp, i32, dbl, vp, vp, vp]),
+            "pr_init_ppr": (ctypes.c_int, [vp, i32, i32, vp, vp, vp, vp]),
+            "pr_iterate_ppr": (ctypes.c_int, [vp, vp, vp, vp, vp, vp, dbl, i32, i32, vp, vp,
+                                              vp]),
+            "ppr_batched_create": (ctypes.c_int, [vp, i32, ctypes.POINTER(vp), vp]),
+            "ppr_batched_destroy": (ctypes.c_int, [vp]),
+            "ppr_batched_bytes": (ctypes.c_int, [vp, vp, vp]),
+            "ppr_batched_init": (ctypes.c_int, [vp, vp, vp, vp]),
+            "ppr_batched_iterate": (ctypes.c_int, [vp, vp, dbl, i32, vp, vp, vp]),
+            "ppr_batched_step": (ctypes.c_int, [vp, vp, dbl, i32, vp, vp, vp, vp]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)
@@ -169,6 +183,14 @@ def cg_permute4(x, idx, out, stream=None):
         raise CagraError("cg_permute4 needs 4-byte elements")
     _check(load().cg_permute4(_ptr(x), x.numel(), _ptr(idx), idx.numel(), _ptr(out),
                               _stream(stream)), "cg_permute4")
+
+
+def cg_permute_rows(x, idx, out, stream=None):
+    """Row i of out = row idx[i] of x (2-D tensors, rows a multiple of 16 bytes)."""
+    if x.dim() != 2 or out.dim() != 2 or x.shape[1] != out.shape[1] or x.dtype != out.dtype:
+        raise CagraError("cg_permute_rows needs 2-D tensors of equal row shape and dtype")
+    _check(load().cg_permute_rows(_ptr(x), x.shape[0], x.shape[1] * x.element_size(), _ptr(idx),
+                                  idx.numel(), _ptr(out), _stream(stream)), "cg_permute_rows")
 
 
 # ------------------------------------------------------------------ segmenting
@@ -372,6 +394,86 @@ def lp_run(seg: Segmented, labels, max_passes: int = 1 << 20, stream=None):
     _check(load().lp_run(seg.handle, _ptr(labels), cap, ctypes.byref(p), ch.ctypes.data,
                          _stream(stream)), "lp_run")
     return p.value, ch[:p.value].copy()
+
+
+def pr_init_ppr(inv, seed: int, rank, contrib, dangling, stream=None):
+    _check(load().pr_init_ppr(_ptr(inv), inv.numel(), seed, _ptr(rank), _ptr(contrib),
+                              _ptr(dangling), _stream(stream)), "pr_init_ppr")
+
+
+def pr_iterate_ppr(seg: Segmented, inv, rank_in, contrib_in, rank_out, contrib_out,
+                   damping: float, iterations: int, seed: int, dangling, resid=None,
+                   stream=None):
+    _check(load().pr_iterate_ppr(seg.handle, _ptr(inv), _ptr(rank_in), _ptr(contrib_in),
+                                 _ptr(rank_out), _ptr(contrib_out), damping, iterations, seed,
+                                 _ptr(dangling), _ptr(resid), _stream(stream)), "pr_iterate_ppr")
+
+
+# ------------------------------------------------------------------ batched personalised PR
+
+PPR_COLUMNS = 64
+
+
+class PprBatch:
+    """Owner of a cg_ppr handle (keeps its segmented graph alive)."""
+
+    def __init__(self, handle: int, seg: Segmented, planes: int):
+        self.handle = handle
+        self.seg = seg
+        self.planes = planes
+
+    def __del__(self):
+        self.close()
+
+    def close(self):
+        if getattr(self, "handle", None):
+            try:
+                load().ppr_batched_destroy(self.handle)
+            finally:
+                self.handle = None
+
+    @property
+    def bytes(self) -> int:
+        b, c = ctypes.c_int64(), ctypes.c_int64()
+        _check(load().ppr_batched_bytes(self.handle, ctypes.byref(b), ctypes.byref(c)),
+               "ppr_batched_bytes")
+        return int(b.value)
+
+    @property
+    def chunks(self) -> int:
+        b, c = ctypes.c_int64(), ctypes.c_int64()
+        _check(load().ppr_batched_bytes(self.handle, ctypes.byref(b), ctypes.byref(c)),
+               "ppr_batched_bytes")
+        return int(c.value)
+
+
+def ppr_batched_create(seg: Segmented, planes: int = 2, stream=None) -> PprBatch:
+    h = ctypes.c_void_p()
+    _check(load().ppr_batched_create(seg.handle, planes, ctypes.byref(h), _stream(stream)),
+           "ppr_batched_create")
+    return PprBatch(h.value, seg, planes)
+
+
+def ppr_batched_init(ppr: PprBatch, inv, seeds, stream=None):
+    sd = np.ascontiguousarray(np.asarray(seeds, dtype=np.int32))
+    if sd.shape != (PPR_COLUMNS,):
+        raise CagraError(f"ppr_batched_init: need {PPR_COLUMNS} seeds, got shape {sd.shape}")
+    _check(load().ppr_batched_init(ppr.handle, _ptr(inv), sd.ctypes.data, _stream(stream)),
+           "ppr_batched_init")
+
+
+def ppr_batched_iterate(ppr: PprBatch, inv, damping: float, iterations: int, rank_out=None,
+                        resid=None, stream=None):
+    _check(load().ppr_batched_iterate(ppr.handle, _ptr(inv), damping, iterations,
+                                      _ptr(rank_out), _ptr(resid), _stream(stream)),
+           "ppr_batched_iterate")
+
+
+def ppr_batched_step(ppr: PprBatch, inv, damping: float, phases: int = 7, rank_old=None,
+                     rank_out=None, resid=None, stream=None):
+    _check(load().ppr_batched_step(ppr.handle, _ptr(inv), damping, phases, _ptr(rank_old),
+                                   _ptr(rank_out), _ptr(resid), _stream(stream)),
+           "ppr_batched_step")
 
 
 # ------------------------------------------------------------------ batched small graphs

@@ -80,6 +80,17 @@ __global__ void relabel_copy_kernel(const int64_t* __restrict__ offsets,
   }
 }
 
+// Rows of w 16-byte words: out[i] = in[idx[i]] (zeros where idx[i] is out of range).
+__global__ void permute_rows_kernel(const uint4* __restrict__ in, const int32_t* __restrict__ idx,
+                                    int64_t n, int64_t n_in, int w, uint4* __restrict__ out) {
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n * w;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = t / w, c = t - i * w;
+    const int32_t j = idx[i];
+    out[t] = (j >= 0 && j < n_in) ? in[(int64_t)j * w + c] : make_uint4(0u, 0u, 0u, 0u);
+  }
+}
+
 __global__ void permute4_kernel(const uint32_t* __restrict__ in, const int32_t* __restrict__ idx,
                                 int64_t n, int64_t n_in, uint32_t* __restrict__ out) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
@@ -159,6 +170,22 @@ int cg_permute4(const void* in, int64_t n_in, const int32_t* idx, int64_t n, voi
   CG_ARG(in && idx && out && in != out, "cg_permute4: null or aliased pointer");
   permute4_kernel<<<grid_for(n, 256), 256, 0, stream>>>((const uint32_t*)in, idx, n, n_in,
                                                         (uint32_t*)out);
+  CG_LAUNCH_CHECK();
+  return CG_OK;
+}
+
+int cg_permute_rows(const void* in, int64_t n_in, int32_t row_bytes, const int32_t* idx,
+                    int64_t n, void* out, cudaStream_t stream) {
+  CG_ARG(n >= 0 && n_in >= 0, "cg_permute_rows: negative size");
+  CG_ARG(row_bytes > 0 && row_bytes % 16 == 0, "cg_permute_rows: row_bytes must be a positive "
+         "multiple of 16 (got %d)", row_bytes);
+  if (n == 0) return CG_OK;
+  CG_ARG(in && idx && out && in != out, "cg_permute_rows: null or aliased pointer");
+  CG_ARG(((uintptr_t)in | (uintptr_t)out) % 16 == 0, "cg_permute_rows: rows need 16-byte "
+         "aligned buffers");
+  const int w = row_bytes / 16;
+  permute_rows_kernel<<<grid_for(n * w, 256), 256, 0, stream>>>((const uint4*)in, idx, n, n_in, w,
+                                                                (uint4*)out);
   CG_LAUNCH_CHECK();
   return CG_OK;
 }

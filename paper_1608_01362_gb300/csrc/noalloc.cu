@@ -122,6 +122,7 @@ int pr_iterate_plain_noalloc(const int64_t* offsets, const int32_t* src, int32_t
   a.partials = partials;
   a.counter = counter;
   a.V = V;
+  a.seed = -1;
   const int B = 512;
   const int nb = (int)ceil_div(V, B);
   const size_t smem = (size_t)kMergeWarps * B * 4;

@@ -37,7 +37,7 @@ merge_update_kernel(const int32_t* __restrict__ blk, const int32_t* __restrict__
     const int64_t v0 = mb * B;
     const int n = (int)((a.V - v0) < B ? (a.V - v0) : B);
     warp_merge<SumF32>(blk, idx_map, interm, k, nb, mb, v0, n, acc);
-    warp_vertex_update(acc, v0, n, a, (float)(D * a.inv_V), &dsum, &rsum);
+    warp_vertex_update(acc, v0, n, a, D, &dsum, &rsum);
   }
   block_finish(dsum, rsum, a);
 }
@@ -73,6 +73,20 @@ __global__ void pr_init_kernel(const float* __restrict__ inv, int32_t V, float* 
   }
   c = warp_sum(c);
   if ((threadIdx.x & 31) == 0 && c) atomicAdd(ndang, c);
+}
+
+// Personalised start: all mass on the seed; D = the seed's mass if it is
+// dangling.
+__global__ void ppr_init_kernel(const float* __restrict__ inv, int32_t V, int32_t seed,
+                                float* __restrict__ rank, float* __restrict__ contrib,
+                                double* __restrict__ D) {
+  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < V;
+       v += (int64_t)gridDim.x * blockDim.x) {
+    const float r = v == seed ? 1.0f : 0.0f;
+    rank[v] = r;
+    contrib[v] = r * inv[v];
+    if (v == seed) *D = inv[v] == 0.0f ? 1.0 : 0.0;
+  }
 }
 
 __global__ void pr_init_finish_kernel(const unsigned long long* __restrict__ ndang, int32_t V,
@@ -254,9 +268,22 @@ int merge(const cg_segmented* g, int32_t op, const void* interm, void* out, cuda
   return CG_OK;
 }
 
+static int merge_update_seeded(const cg_segmented* g, const float* inv, const float* rank_in,
+                               float* rank_out, float* contrib_out, double damping,
+                               const double* D_in, double* D_out, double* resid_out,
+                               int32_t seed, cudaStream_t stream);
+
 int pr_merge_update(const cg_segmented* g, const float* inv, const float* rank_in,
                     float* rank_out, float* contrib_out, double damping, const double* D_in,
                     double* D_out, double* resid_out, cudaStream_t stream) {
+  return merge_update_seeded(g, inv, rank_in, rank_out, contrib_out, damping, D_in, D_out,
+                             resid_out, -1, stream);
+}
+
+static int merge_update_seeded(const cg_segmented* g, const float* inv, const float* rank_in,
+                               float* rank_out, float* contrib_out, double damping,
+                               const double* D_in, double* D_out, double* resid_out,
+                               int32_t seed, cudaStream_t stream) {
   CG_ARG(g && inv && rank_in && rank_out && contrib_out && D_in && D_out,
          "pr_merge_update: null argument");
   CG_ARG(damping >= 0.0 && damping <= 1.0, "pr_merge_update: damping must be in [0, 1]");
@@ -278,6 +305,7 @@ int pr_merge_update(const cg_segmented* g, const float* inv, const float* rank_i
   a.partials = g->partials;
   a.counter = g->counter;
   a.V = g->V;
+  a.seed = seed;
   merge_update_kernel<<<(unsigned)ceil_div(g->nb, kMergeWarps), kMergeWarps * 32, smem,
                         stream>>>(g->blk, g->idx_map, (const float*)g->interm, g->k, g->nb,
                                   g->B, a);
@@ -285,20 +313,47 @@ int pr_merge_update(const cg_segmented* g, const float* inv, const float* rank_i
   return CG_OK;
 }
 
-int pr_iterate(const cg_segmented* g, const float* inv, const float* rank_in,
-               const float* contrib_in, float* rank_out, float* contrib_out, double damping,
-               int32_t iterations, double* D_io, double* resid, cudaStream_t stream) {
-  CG_ARG(g != nullptr, "pr_iterate: null handle");
+static int iterate_seeded(const cg_segmented* g, const float* inv, const float* rank_in,
+                          const float* contrib_in, float* rank_out, float* contrib_out,
+                          double damping, int32_t iterations, double* D_io, double* resid,
+                          int32_t seed, cudaStream_t stream) {
   CG_TRY(check_pr_args(g->V, inv, rank_in, contrib_in, rank_out, contrib_out, damping,
                        iterations, D_io));
   for (int t = 0; t < iterations; ++t) {
     IterBufs b = iter_bufs(t, iterations, rank_in, contrib_in, rank_out, contrib_out,
                            g->rank_tmp, g->contrib_tmp, D_io, g->dslot, resid);
     CG_TRY(run_seg_gather<SumF32>(g->plan, b.contrib_in, g->V, (float*)g->interm, stream));
-    CG_TRY(pr_merge_update(g, inv, b.rank_in, b.rank_out, b.contrib_out, damping, b.D_in,
-                           b.D_out, b.resid, stream));
+    CG_TRY(merge_update_seeded(g, inv, b.rank_in, b.rank_out, b.contrib_out, damping, b.D_in,
+                               b.D_out, b.resid, seed, stream));
   }
   return CG_OK;
+}
+
+int pr_iterate(const cg_segmented* g, const float* inv, const float* rank_in,
+               const float* contrib_in, float* rank_out, float* contrib_out, double damping,
+               int32_t iterations, double* D_io, double* resid, cudaStream_t stream) {
+  CG_ARG(g != nullptr, "pr_iterate: null handle");
+  return iterate_seeded(g, inv, rank_in, contrib_in, rank_out, contrib_out, damping, iterations,
+                        D_io, resid, -1, stream);
+}
+
+int pr_init_ppr(const float* inv, int32_t V, int32_t seed, float* rank, float* contrib,
+                double* D, cudaStream_t stream) {
+  CG_ARG(V >= 1 && inv && rank && contrib && D, "pr_init_ppr: bad arguments");
+  CG_ARG(seed >= 0 && seed < V, "pr_init_ppr: seed %d outside [0, %d)", seed, V);
+  ppr_init_kernel<<<grid_for(V, 256), 256, 0, stream>>>(inv, V, seed, rank, contrib, D);
+  CG_LAUNCH_CHECK();
+  return CG_OK;
+}
+
+int pr_iterate_ppr(const cg_segmented* g, const float* inv, const float* rank_in,
+                   const float* contrib_in, float* rank_out, float* contrib_out, double damping,
+                   int32_t iterations, int32_t seed, double* D_io, double* resid,
+                   cudaStream_t stream) {
+  CG_ARG(g != nullptr, "pr_iterate_ppr: null handle");
+  CG_ARG(seed >= 0 && seed < g->V, "pr_iterate_ppr: seed %d outside [0, %d)", seed, g->V);
+  return iterate_seeded(g, inv, rank_in, contrib_in, rank_out, contrib_out, damping, iterations,
+                        D_io, resid, seed, stream);
 }
 
 // ------------------------------------------------------------------ plain
@@ -391,6 +446,7 @@ int pr_iterate_plain(const cg_plain* p, const float* inv, const float* rank_in,
     a.partials = p->partials;
     a.counter = p->counter;
     a.V = p->V;
+    a.seed = -1;
     dense_update_kernel<<<(unsigned)ceil_div(nb, kMergeWarps), kMergeWarps * 32, smem,
                           stream>>>(p->acc, B, nb, a);
     CG_LAUNCH_CHECK();

@@ -88,19 +88,28 @@ struct PrArgs {
   double* partials;
   unsigned* counter;
   int32_t V;
+  int32_t seed;    // -1: uniform teleport; else personalised to this vertex
 };
 
 // Vertex update (Algorithm 5's VertexUpdate, normalised) for one warp's
 // destinations [v0, v0+n) with sums in acc; returns the warp's FP64 partial
 // sums of the dangling mass and of the L1 residual (valid in lane 0).
 __device__ __forceinline__ void warp_vertex_update(const float* acc, int64_t v0, int n,
-                                                   const PrArgs& a, float Dv, double* dsum,
+                                                   const PrArgs& a, double Dfull, double* dsum,
                                                    double* rsum) {
+  const float Dv = (float)(Dfull * a.inv_V);
   const int lane = threadIdx.x & 31;
+  const float tele = (float)((1.0 - (double)a.d) + (double)a.d * Dfull);
   float dpart = 0.0f, rpart = 0.0f;  // <= B/32 terms per lane, then FP64
   for (int i = lane; i < n; i += 32) {
     const int64_t v = v0 + i;
-    const float r = a.base + a.d * (acc[i] + Dv);
+    float r;
+    if (a.seed < 0) {
+      r = a.base + a.d * (acc[i] + Dv);
+    } else {  // personalised: teleport and dangling mass return to the seed
+      r = a.d * acc[i];
+      if (v == a.seed) r += tele;
+    }
     const float iv = __ldcs(a.inv + v);
     const float old = __ldcs(a.rank_in + v);
     __stcs(a.rank_out + v, r);
@@ -168,7 +177,7 @@ dense_update_kernel(const float* __restrict__ sums, int B, int nb, PrArgs a) {
     const int n = (int)((a.V - v0) < B ? (a.V - v0) : B);
     for (int i = lane; i < n; i += 32) acc[i] = __ldcs(sums + v0 + i);
     __syncwarp();
-    warp_vertex_update(acc, v0, n, a, (float)(D * a.inv_V), &dsum, &rsum);
+    warp_vertex_update(acc, v0, n, a, D, &dsum, &rsum);
   }
   block_finish(dsum, rsum, a);
 }

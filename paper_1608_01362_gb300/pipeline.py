@@ -44,6 +44,23 @@ class Graph:
             self.new_of_old, self.old_of_new = n2o, o2n
         self.inv = torch.empty(self.V, dtype=torch.float32, device=self.device)
         C.cg_inv_outdeg(self.outdeg, self.inv)
+        self._n2o_host = None
+
+    def to_clustered_id(self, v: int) -> int:
+        """Vertex ID in the numbering the kernels use."""
+        if self.new_of_old is None:
+            return int(v)
+        if self._n2o_host is None:
+            self._n2o_host = self.new_of_old.cpu().numpy()
+        return int(self._n2o_host[int(v)])
+
+    def rows_to_original(self, x):
+        """[V, w] per-vertex rows in the clustered numbering -> original."""
+        if self.new_of_old is None:
+            return x
+        out = torch.empty_like(x)
+        C.cg_permute_rows(x, self.new_of_old, out)
+        return out
 
     def to_original(self, x):
         """Vertex vector in the clustered numbering -> original numbering."""
@@ -109,6 +126,48 @@ class SegmentedPageRank(_PageRankBase):
     def step(self, rank_in, contrib_in, rank_out, contrib_out, damping, iterations, resid=None):
         C.pr_iterate(self.seg, self.g.inv, rank_in, contrib_in, rank_out, contrib_out, damping,
                      iterations, self.dangling, resid)
+
+
+    def run_ppr(self, seed: int, iterations: int = 20, damping: float = 0.85, resid=None):
+        """Personalised PageRank of one seed (original ID): one-hot start,
+        `iterations` iterations; returns (rank in original IDs, residuals)."""
+        if resid is None:
+            resid = torch.zeros(iterations, dtype=torch.float64, device=self.g.device)
+        s = self.g.to_clustered_id(seed)
+        C.pr_init_ppr(self.g.inv, s, self.rank[0], self.contrib[0], self.dangling)
+        C.pr_iterate_ppr(self.seg, self.g.inv, self.rank[0], self.contrib[0], self.rank[1],
+                         self.contrib[1], damping, iterations, s, self.dangling, resid)
+        return self.g.to_original(self.rank[1]), resid
+
+
+class BatchedPPR:
+    """64 personalised PageRank vectors through one segmented graph."""
+
+    def __init__(self, graph: Graph, num_segments: int | None = None, bounds=None,
+                 planes: int = 2, merge_block: int = 512):
+        self.g = graph
+        if bounds is not None:
+            bounds = np.asarray(bounds, dtype=np.int64)
+            num_segments = len(bounds) - 1
+        self.seg = C.pr_build_segments(graph.offsets, graph.src, num_segments, bounds=bounds,
+                                       merge_block=merge_block)
+        self.ppr = C.ppr_batched_create(self.seg, planes)
+        self.rank = torch.empty((graph.V, C.PPR_COLUMNS), dtype=torch.float32,
+                                device=graph.device)
+        self.resid = torch.zeros(C.PPR_COLUMNS, dtype=torch.float64, device=graph.device)
+
+    def init(self, seeds):
+        """seeds: 64 vertex IDs (original numbering)."""
+        C.ppr_batched_init(self.ppr, self.g.inv,
+                           [self.g.to_clustered_id(int(s)) for s in seeds])
+
+    def run(self, seeds, iterations: int = 20, damping: float = 0.85):
+        """Returns (R [V, 64] in original vertex IDs, per-column residual of the
+        last iteration as a device FP64 tensor)."""
+        self.init(seeds)
+        C.ppr_batched_iterate(self.ppr, self.g.inv, damping, iterations, self.rank,
+                              self.resid if iterations >= 2 else None)
+        return self.g.rows_to_original(self.rank), self.resid
 
 
 class PlainPageRank(_PageRankBase):
