@@ -63,6 +63,8 @@ def _load():
             lib.gg_permutation.argtypes = [u64, i64, vp]
             lib.gg_splitmix_draws.restype = ctypes.c_int
             lib.gg_splitmix_draws.argtypes = [u64, u64, i32, vp]
+            lib.gg_uniform_rows.restype = ctypes.c_int
+            lib.gg_uniform_rows.argtypes = [u64, i64, i32, dbl, vp]
             lib.gg_free.restype = None
             lib.gg_free.argtypes = [vp]
             lib.gg_num_threads.restype = ctypes.c_int
@@ -139,6 +141,22 @@ def splitmix_draws(seed: int, i: int, n: int) -> np.ndarray:
     out = np.empty(n, dtype=np.uint64)
     _load().gg_splitmix_draws(seed, i, n, out.ctypes.data)
     return out
+
+
+def uniform_rows(seed: int, n: int, K: int, hi: float) -> np.ndarray:
+    """n x K float64 matrix; row v holds the first K draws of SplitMix64
+    stream (seed, v) mapped to [0, hi) (top 53 bits)."""
+    out = np.empty((n, K), dtype=np.float64)
+    if _load().gg_uniform_rows(seed, n, K, hi, out.ctypes.data) != 0:
+        raise ValueError("graphgen: uniform_rows needs n >= 0 and K >= 1")
+    return out
+
+
+def cf_factors(U: int, I: int, K: int = 32, seed: int = 1):
+    """Initial latent factors: entries uniform in [0, sqrt(12/K)) so that
+    E[p . q] = 3 (the mean rating); users from seed, items from seed + 1."""
+    hi = float(np.sqrt(12.0 / K))
+    return uniform_rows(seed, U, K, hi), uniform_rows(seed + 1, I, K, hi)
 
 
 @dataclass

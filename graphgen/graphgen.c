@@ -63,6 +63,17 @@ int gg_splitmix_draws(uint64_t seed, uint64_t i, int32_t n, uint64_t *out) {
     return 0;
 }
 
+/* Row v of an n x K matrix: K uniform draws in [0, hi) from stream (seed, v). */
+int gg_uniform_rows(uint64_t seed, int64_t n, int32_t K, double hi, double *out) {
+    if (n < 0 || K < 1) return -1;
+    #pragma omp parallel for schedule(static)
+    for (int64_t v = 0; v < n; ++v) {
+        sm64 g = stream_at(seed, (uint64_t)v);
+        for (int32_t k = 0; k < K; ++k) out[v * K + k] = unit(&g) * hi;
+    }
+    return 0;
+}
+
 /* Fisher-Yates shuffle of 0..n-1 from stream (seed, 0): perm[old] = new. */
 int gg_permutation(uint64_t seed, int64_t n, int32_t *perm) {
     for (int64_t i = 0; i < n; ++i) perm[i] = (int32_t)i;

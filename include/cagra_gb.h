@@ -470,6 +470,66 @@ int ppr_batched_step(cg_ppr *ppr, const float *dev_inv, double damping, int32_t 
                      const float *dev_rank_old, float *dev_rank_out, double *dev_resid,
                      cudaStream_t stream);
 
+/* ------------------------------------------------ collaborative filtering */
+
+typedef struct cg_bipartite cg_bipartite;
+
+/*
+ * Item-major copy of a user-major rating CSR (the other side of the
+ * bipartite graph): dev_uoff int64[U+1], dev_uitem int32[R] (items in
+ * [0, I)), dev_urate uint8[R] -> dev_ioff int64[I+1], dev_iuser int32[R]
+ * (users ascending within each item: a stable sort by item), dev_irate
+ * uint8[R].  Out-of-range items give CG_ERR_INVALID_ARG.  Synchronizes.
+ */
+int cf_transpose(int64_t U, int64_t I, const int64_t *dev_uoff, const int32_t *dev_uitem,
+                 const uint8_t *dev_urate, int64_t *dev_ioff, int32_t *dev_iuser,
+                 uint8_t *dev_irate, cudaStream_t stream);
+
+/*
+ * Collaborative filtering by gradient descent (the CF application of
+ * Section VI, Table III; the paper gives no formula, so the loss is
+ * 1/2 sum (r_ui - p_u.q_i)^2 + lambda/2 (|P|^2 + |Q|^2) with the
+ * degree-averaged gradient).  The rating CSRs of both sides (from
+ * cf_transpose) are NOT copied and must stay valid.  K = 16, 32 or 64
+ * latent dimensions.  precision: 0 stores P, Q in FP32, 1 in BF16, 2 as
+ * BF16 hi + lo planes (hi = bf16(x), lo = bf16(x - hi)); arithmetic is FP32
+ * and the squared-error sum FP64.  The handle owns the factor storage (see
+ * cf_set_factors).  Synchronizes.
+ */
+int cf_create(int64_t U, int64_t I, int32_t K, int32_t precision, const int64_t *dev_uoff,
+              const int32_t *dev_uitem, const uint8_t *dev_urate, const int64_t *dev_ioff,
+              const int32_t *dev_iuser, const uint8_t *dev_irate, cg_bipartite **out,
+              cudaStream_t stream);
+int cf_destroy(cg_bipartite *cf);
+
+/* Load the factors (device FP32, row-major P[U][K], Q[I][K]) into the
+ * handle's storage format (rounding to BF16 where it stores BF16). */
+int cf_set_factors(cg_bipartite *cf, const float *dev_P, const float *dev_Q,
+                   cudaStream_t stream);
+/* Read the stored factors back as FP32 (either pointer may be NULL). */
+int cf_get_factors(const cg_bipartite *cf, float *dev_P, float *dev_Q, cudaStream_t stream);
+
+/*
+ * `sweeps` Jacobi sweeps: both sides read the old P, Q;
+ *   e_ui = r_ui - p_u . q_i
+ *   p_u += step ((1/deg u) sum_{i in N(u)} e_ui q_i - lambda p_u)
+ *   q_i += step ((1/deg i) sum_{u in N(i)} e_ui p_u - lambda q_i)
+ * (vertices without ratings only decay).  dev_sse: double[sweeps] or NULL;
+ * entry t receives sum over ratings of e_ui^2 for the factors entering
+ * sweep t.  Stream-ordered; deterministic for a given device.
+ */
+int cf_sweep(cg_bipartite *cf, int32_t sweeps, double lambda, double step, double *dev_sse,
+             cudaStream_t stream);
+
+/* One launch of a sweep (0 user gather + SSE, 1 item gather, 2 user update,
+ * 3 item update; a sweep is 0, 1, 2, 3 in that order), for timing. */
+int cf_sweep_phase(cg_bipartite *cf, int32_t phase, double lambda, double step,
+                   double *dev_sse, cudaStream_t stream);
+
+/* Ratings, gather pieces per side and device bytes of the handle. */
+int cf_info(const cg_bipartite *cf, int64_t *ratings, int64_t *user_pieces,
+            int64_t *item_pieces, int64_t *bytes);
+
 /* ------------------------------------------------- no device allocation */
 
 /*

@@ -36,6 +36,8 @@ EXPORTS = [
     "pr_init_ppr", "pr_iterate_ppr",
     "ppr_batched_create", "ppr_batched_destroy", "ppr_batched_bytes", "ppr_batched_init",
     "ppr_batched_iterate", "ppr_batched_step",
+    "cf_transpose", "cf_create", "cf_destroy", "cf_set_factors", "cf_get_factors", "cf_sweep",
+    "cf_sweep_phase", "cf_info",
 ]
 
 
@@ -112,6 +114,15 @@ def load(path: str | None = None):
             "ppr_batched_init": (ctypes.c_int, [vp, vp, vp, vp]),
             "ppr_batched_iterate": (ctypes.c_int, [vp, vp, dbl, i32, vp, vp, vp]),
             "ppr_batched_step": (ctypes.c_int, [vp, vp, dbl, i32, vp, vp, vp, vp]),
+            "cf_transpose": (ctypes.c_int, [i64, i64, vp, vp, vp, vp, vp, vp, vp]),
+            "cf_create": (ctypes.c_int, [i64, i64, i32, i32, vp, vp, vp, vp, vp, vp,
+                                         ctypes.POINTER(vp), vp]),
+            "cf_destroy": (ctypes.c_int, [vp]),
+            "cf_set_factors": (ctypes.c_int, [vp, vp, vp, vp]),
+            "cf_get_factors": (ctypes.c_int, [vp, vp, vp, vp]),
+            "cf_sweep": (ctypes.c_int, [vp, i32, dbl, dbl, vp, vp]),
+            "cf_sweep_phase": (ctypes.c_int, [vp, i32, dbl, dbl, vp, vp]),
+            "cf_info": (ctypes.c_int, [vp, vp, vp, vp, vp]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)
@@ -474,6 +485,67 @@ def ppr_batched_step(ppr: PprBatch, inv, damping: float, phases: int = 7, rank_o
     _check(load().ppr_batched_step(ppr.handle, _ptr(inv), damping, phases, _ptr(rank_old),
                                    _ptr(rank_out), _ptr(resid), _stream(stream)),
            "ppr_batched_step")
+
+
+# ------------------------------------------------------------------ collaborative filtering
+
+CF_FP32, CF_BF16, CF_BF16X2 = 0, 1, 2
+
+
+def cf_transpose(U: int, I: int, uoff, uitem, urate, ioff, iuser, irate, stream=None):
+    _check(load().cf_transpose(U, I, _ptr(uoff), _ptr(uitem), _ptr(urate), _ptr(ioff),
+                               _ptr(iuser), _ptr(irate), _stream(stream)), "cf_transpose")
+
+
+class Bipartite:
+    """Owner of a cg_bipartite handle (keeps the rating CSRs alive)."""
+
+    def __init__(self, handle: int, keep):
+        self.handle = handle
+        self._keep = keep
+
+    def __del__(self):
+        self.close()
+
+    def close(self):
+        if getattr(self, "handle", None):
+            try:
+                load().cf_destroy(self.handle)
+            finally:
+                self.handle = None
+
+    @property
+    def info(self) -> dict:
+        v = [ctypes.c_int64() for _ in range(4)]
+        _check(load().cf_info(self.handle, *[ctypes.byref(x) for x in v]), "cf_info")
+        return dict(zip(("ratings", "user_pieces", "item_pieces", "bytes"),
+                        [int(x.value) for x in v]))
+
+
+def cf_create(U: int, I: int, K: int, precision: int, uoff, uitem, urate, ioff, iuser, irate,
+              stream=None) -> Bipartite:
+    h = ctypes.c_void_p()
+    _check(load().cf_create(U, I, K, precision, _ptr(uoff), _ptr(uitem), _ptr(urate), _ptr(ioff),
+                            _ptr(iuser), _ptr(irate), ctypes.byref(h), _stream(stream)),
+           "cf_create")
+    return Bipartite(h.value, (uoff, uitem, urate, ioff, iuser, irate))
+
+
+def cf_set_factors(cf: Bipartite, P, Q, stream=None):
+    _check(load().cf_set_factors(cf.handle, _ptr(P), _ptr(Q), _stream(stream)), "cf_set_factors")
+
+
+def cf_get_factors(cf: Bipartite, P=None, Q=None, stream=None):
+    _check(load().cf_get_factors(cf.handle, _ptr(P), _ptr(Q), _stream(stream)), "cf_get_factors")
+
+
+def cf_sweep(cf: Bipartite, sweeps: int, lam: float, step: float, sse=None, stream=None):
+    _check(load().cf_sweep(cf.handle, sweeps, lam, step, _ptr(sse), _stream(stream)), "cf_sweep")
+
+
+def cf_sweep_phase(cf: Bipartite, phase: int, lam: float, step: float, sse=None, stream=None):
+    _check(load().cf_sweep_phase(cf.handle, phase, lam, step, _ptr(sse), _stream(stream)),
+           "cf_sweep_phase")
 
 
 # ------------------------------------------------------------------ batched small graphs

@@ -4,13 +4,15 @@ through the batched SpMM-form gather with BF16 hi+lo (or hi-only) storage.
 
 Tolerances.  One vector is FP32 throughout: the same 1e-5 relative L1 as
 uniform PageRank.  The batched form stores the contributions C = R / outdeg
-in BF16 planes: two planes keep |c - (hi + lo)| <= 2^-9 * 2^-9 |c| = 2^-18 |c|,
-one plane keeps |c - hi| <= 2^-9 |c|.  That storage error enters every
-iteration and is damped by d per iteration, so after T iterations the
-relative L1 error is at most delta * sum_t d^t < delta / (1 - d) = 6.67 delta,
-plus the FP32 sums (below 1e-6 at these degrees):
-    two planes:  6.67 * 2^-18 = 2.5e-5   -> bound used 1e-4
-    one plane:   6.67 * 2^-9  = 1.3e-2   -> bound used 1.5e-2
+in BF16 planes (8 significant bits, unit roundoff u = 2^-8): two planes keep
+|c - (hi + lo)| <= 2^-8 |c - hi| <= 2^-16 |c|, one plane |c - hi| <= 2^-8 |c|.
+The iteration map R -> d A (R / outdeg) + teleport, with the dangling mass
+returned to the seed, is a contraction by d in the L1 norm, and each column
+of R has L1 norm 1, so the storage error of one iteration (at most d u) adds
+up to at most u d / (1 - d) = 5.67 u after any number of iterations, plus
+the FP32 sums (below 1e-6 at these degrees):
+    two planes:  5.67 * 2^-16 = 8.6e-5   -> bound used 1.5e-4
+    one plane:   5.67 * 2^-8  = 2.2e-2   -> bound used 3e-2
 """
 import numpy as np
 import pytest
@@ -21,7 +23,7 @@ import oracle as O
 pytestmark = pytest.mark.gpu
 
 TOL_SINGLE = 1e-5
-TOL_PLANES = {2: 1e-4, 1: 1.5e-2}
+TOL_PLANES = {2: 1.5e-4, 1: 3e-2}
 COLS = 64
 
 
