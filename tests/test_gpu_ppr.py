@@ -223,3 +223,36 @@ def test_batched_errors(env, rmat13):
     resid = torch.zeros(COLS, dtype=torch.float64, device="cuda")
     with pytest.raises(C.CagraError):  # residual needs two iterations
         C.ppr_batched_iterate(b, G.inv, 0.85, 1, None, resid)
+
+
+def test_batched_column_matches_single_vector_run(env, rmat13):
+    """Each column of the batched solve is the one-vector personalised
+    PageRank of its seed (same graph, same segments), within the storage bound."""
+    torch, C, P = env
+    g = rmat13
+    G = P.Graph(g.offsets, g.src, cluster_mode=0)
+    b = P.BatchedPPR(G, num_segments=4, planes=2)
+    seeds = mixed_seeds(g)
+    R, _ = b.run(seeds, iterations=20)
+    R = R.cpu().numpy()
+    pr = P.SegmentedPageRank(G, num_segments=4)
+    for j in (0, 3, 17, 63):
+        r1, _ = pr.run_ppr(int(seeds[j]), iterations=20)
+        r1 = r1.cpu().numpy().astype(np.float64)
+        assert np.sum(np.abs(R[:, j] - r1)) / np.sum(np.abs(r1)) <= TOL_PLANES[2] + TOL_SINGLE
+
+
+def test_batched_columns_are_independent(env, rmat13):
+    """Permuting the seeds permutes the columns bit for bit: a column's
+    arithmetic never involves another column."""
+    torch, C, P = env
+    g = rmat13
+    G = P.Graph(g.offsets, g.src, cluster_mode=0)
+    b = P.BatchedPPR(G, num_segments=3, planes=2)
+    seeds = mixed_seeds(g)
+    R1, res1 = b.run(seeds, iterations=9)
+    R1, res1 = R1.clone(), res1.clone()
+    perm = np.random.default_rng(4).permutation(COLS)
+    R2, res2 = b.run(seeds[perm], iterations=9)
+    assert torch.equal(R2, R1[:, torch.as_tensor(perm, device="cuda")])
+    assert torch.equal(res2, res1[torch.as_tensor(perm, device="cuda")])
