@@ -20,10 +20,13 @@
 // (hi = bf16(x), lo = bf16(x - hi)); arithmetic is FP32, SSE is FP64.
 #include <cuda_bf16.h>
 
+#include <vector>
+
 #include "common.cuh"
 
 namespace cg {
 constexpr int kCfPiece = 512;   // ratings per gather piece
+constexpr int kCfWide = 64;     // vertices with more pieces are updated by a whole block
 constexpr int kCfThreads = 256;
 }  // namespace cg
 
@@ -44,6 +47,8 @@ struct cg_bipartite {
   int64_t* poff[2] = {nullptr, nullptr};
   int64_t npieces[2] = {0, 0};
   float* gpart[2] = {nullptr, nullptr};  // [npieces][K] piece gradients
+  int32_t* wide[2] = {nullptr, nullptr};  // vertices with more than kCfWide pieces
+  int32_t nwide[2] = {0, 0};
   // factor storage: plane 0 = FP32 / BF16 / BF16 hi, plane 1 = BF16 lo
   void* P[2] = {nullptr, nullptr};
   void* Q[2] = {nullptr, nullptr};
@@ -150,10 +155,12 @@ cf_gather_kernel(const int32_t* __restrict__ pvtx, const int64_t* __restrict__ p
       // two ratings of this group in flight
       const int64_t r2 = r + GROUPS;
       const bool has2 = r2 < e_end;
-      const int32_t u1 = __ldg(nbr + r);
-      const int32_t u2 = has2 ? __ldg(nbr + r2) : u1;
-      const float rt1 = (float)__ldg(rate + r);
-      const float rt2 = has2 ? (float)__ldg(rate + r2) : 0.0f;
+      // the rating stream is read once: evict-first, so it does not push
+      // factor rows out of L2
+      const int32_t u1 = __ldcs(nbr + r);
+      const int32_t u2 = has2 ? __ldcs(nbr + r2) : u1;
+      const float rt1 = (float)__ldcs(rate + r);
+      const float rt2 = has2 ? (float)__ldcs(rate + r2) : 0.0f;
       float y1[8], y2[8];
       load8<PREC>(n0, n1, u1, K, d0, y1);
       load8<PREC>(n0, n1, u2, K, d0, y2);
@@ -219,6 +226,7 @@ cf_update_kernel(const int64_t* __restrict__ poff, const int64_t* __restrict__ o
   const int sub = (int)(t % LANES);
   const int d0 = 8 * sub;
   for (int64_t v = t / LANES; v < n; v += ng) {
+    if (poff[v + 1] - poff[v] > kCfWide) continue;  // cf_update_wide_kernel's
     float g[8], x[8];
 #pragma unroll
     for (int q = 0; q < 8; ++q) g[q] = 0.0f;
@@ -234,6 +242,64 @@ cf_update_kernel(const int64_t* __restrict__ poff, const int64_t* __restrict__ o
 #pragma unroll
     for (int q = 0; q < 8; ++q) x[q] = x[q] + step * (g[q] * inv - lambda * x[q]);
     store8<PREC>(x0, x1, v, K, d0, x);
+  }
+}
+
+// Vertices with more than kCfWide pieces (hub items): one block each.  The
+// block's groups of LANES lanes sum interleaved subsets of the pieces (four
+// independent accumulators per group, combined in a fixed order), then a
+// fixed-order tree over the groups gives the gradient sum; deterministic.
+template <int LANES, int PREC>
+__global__ void __launch_bounds__(kCfThreads)
+cf_update_wide_kernel(const int32_t* __restrict__ wide, int32_t nwide,
+                      const int64_t* __restrict__ poff, const int64_t* __restrict__ off,
+                      const float* __restrict__ gpart, void* x0, void* x1, float lambda,
+                      float step) {
+  constexpr int K = 8 * LANES;
+  constexpr int GROUPS = kCfThreads / LANES;
+  constexpr int U = 4;
+  __shared__ __align__(16) float red[GROUPS * K];
+  const int sub = threadIdx.x % LANES, g = threadIdx.x / LANES;
+  const int d0 = 8 * sub;
+  for (int32_t wv = blockIdx.x; wv < nwide; wv += gridDim.x) {
+    const int32_t v = wide[wv];
+    const int64_t p0 = poff[v], p1 = poff[v + 1];
+    float a[U][8];
+#pragma unroll
+    for (int j = 0; j < U; ++j)
+#pragma unroll
+      for (int q = 0; q < 8; ++q) a[j][q] = 0.0f;
+    for (int64_t p = p0 + g; p < p1; p += U * GROUPS) {
+#pragma unroll
+      for (int j = 0; j < U; ++j) {
+        const int64_t pj = p + (int64_t)j * GROUPS;
+        if (pj < p1) {
+          const float4* s = reinterpret_cast<const float4*>(gpart + pj * K + d0);
+          const float4 x = __ldcs(s), y = __ldcs(s + 1);
+          a[j][0] += x.x; a[j][1] += x.y; a[j][2] += x.z; a[j][3] += x.w;
+          a[j][4] += y.x; a[j][5] += y.y; a[j][6] += y.z; a[j][7] += y.w;
+        }
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < 8; ++q) red[g * K + d0 + q] = (a[0][q] + a[1][q]) + (a[2][q] + a[3][q]);
+    __syncthreads();
+    for (int st = GROUPS / 2; st >= 1; st >>= 1) {
+      if (g < st)
+#pragma unroll
+        for (int q = 0; q < 8; ++q) red[g * K + d0 + q] += red[(g + st) * K + d0 + q];
+      __syncthreads();
+    }
+    if (g == 0) {
+      const int64_t deg = off[v + 1] - off[v];
+      const float inv = 1.0f / (float)deg;
+      float x[8];
+      load8<PREC>(x0, x1, v, K, d0, x);
+#pragma unroll
+      for (int q = 0; q < 8; ++q) x[q] = x[q] + step * (red[d0 + q] * inv - lambda * x[q]);
+      store8<PREC>(x0, x1, v, K, d0, x);
+    }
+    __syncthreads();
   }
 }
 
@@ -352,6 +418,12 @@ int sweep_side(cg_bipartite* h, int side, double* sse, float lambda, float step,
   } else {
     cf_update_kernel<LANES, PREC><<<grid_for(n * LANES, kCfThreads, 8), kCfThreads, 0, s>>>(
         h->poff[side], off, n, h->gpart[side], self[0], self[1], lambda, step);
+    if (h->nwide[side] > 0) {
+      CG_LAUNCH_CHECK();
+      cf_update_wide_kernel<LANES, PREC><<<h->nwide[side], kCfThreads, 0, s>>>(
+          h->wide[side], h->nwide[side], h->poff[side], off, h->gpart[side], self[0], self[1],
+          lambda, step);
+    }
   }
   CG_LAUNCH_CHECK();
   return CG_OK;
@@ -422,6 +494,7 @@ void cf_free(cg_bipartite* h) {
     cudaFree(h->pbeg[s]);
     cudaFree(h->poff[s]);
     cudaFree(h->gpart[s]);
+    cudaFree(h->wide[s]);
     cudaFree(h->P[s]);
     cudaFree(h->Q[s]);
   }
@@ -463,6 +536,22 @@ int build_pieces(cg_bipartite* h, int side, cudaStream_t s) {
     piece_fill_kernel<<<grid_for(n, 256), 256, 0, s>>>(off, h->poff[side], n, h->pvtx[side],
                                                         h->pbeg[side]);
     CG_LAUNCH_CHECK();
+  }
+  // vertices with many pieces get a whole block in the update
+  std::vector<int64_t> hp((size_t)n + 1);
+  CG_CUDA(cudaMemcpyAsync(hp.data(), h->poff[side], sizeof(int64_t) * (size_t)(n + 1),
+                          cudaMemcpyDeviceToHost, s));
+  CG_CUDA(cudaStreamSynchronize(s));
+  std::vector<int32_t> wide;
+  for (int64_t v = 0; v < n; ++v)
+    if (hp[v + 1] - hp[v] > kCfWide) wide.push_back((int32_t)v);
+  h->nwide[side] = (int32_t)wide.size();
+  if (!wide.empty()) {
+    CG_CUDA(cudaMalloc((void**)&h->wide[side], sizeof(int32_t) * wide.size()));
+    h->bytes += 4 * (int64_t)wide.size();
+    CG_CUDA(cudaMemcpyAsync(h->wide[side], wide.data(), sizeof(int32_t) * wide.size(),
+                            cudaMemcpyHostToDevice, s));
+    CG_CUDA(cudaStreamSynchronize(s));
   }
   return CG_OK;
 }

@@ -114,10 +114,12 @@ __device__ __forceinline__ void split_row(const float (&c)[8], uint4* hi, uint4*
   if (lo) *lo = make_uint4(l[0], l[1], l[2], l[3]);
 }
 
+// streaming (evict-first) store: intermBuf and carries must not push the
+// segment's C rows out of L2
 __device__ __forceinline__ void store_row(float* dst, const float (&a)[8]) {
   float4* p = reinterpret_cast<float4*>(dst);
-  p[0] = make_float4(a[0], a[1], a[2], a[3]);
-  p[1] = make_float4(a[4], a[5], a[6], a[7]);
+  __stcs(p, make_float4(a[0], a[1], a[2], a[3]));
+  __stcs(p + 1, make_float4(a[4], a[5], a[6], a[7]));
 }
 
 __device__ __forceinline__ void load_row(const float* src, float (&a)[8]) {

@@ -188,3 +188,22 @@ def test_cf_errors(env, small):
     rate = torch.ones(4, dtype=torch.uint8, device="cuda")
     with pytest.raises(C.CagraError):
         C.cf_transpose(1, small.I, uoff, bad, rate, ioff, out_u, out_r)
+
+
+def test_hub_item_block_update(env):
+    """An item rated by every user (40,000 ratings: more than 64 gather
+    pieces, so its update runs on a whole block with a fixed-order tree)."""
+    torch, C = env
+    U, I = 40_000, 50
+    rng = np.random.default_rng(11)
+    items, offs = [], [0]
+    for u in range(U):
+        row = sorted({0, *rng.integers(1, I, 2).tolist()})
+        items += row
+        offs.append(len(items))
+    bp = graphgen.Bipartite(U, I, np.array(offs, dtype=np.int64), np.array(items, dtype=np.int32),
+                            rng.integers(1, 6, len(items)).astype(np.uint8))
+    Pg, Qg, sse, P, Q, want = _run_both(torch, C, bp, 32, C.CF_FP32, 3)
+    assert np.max(np.abs(Pg - P)) <= 2e-6 * np.max(np.abs(P))
+    assert np.max(np.abs(Qg - Q)) <= 2e-6 * np.max(np.abs(Q))
+    assert np.all(np.abs(sse - want) <= 1e-5 * want)
