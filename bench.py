@@ -41,6 +41,22 @@ def _dist():
     return rank, world, local
 
 
+def max_over_ranks(x: float, pg) -> float:
+    """The largest x over the process group's ranks (x itself without one)."""
+    if pg is None:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64)
+    pg.all_reduce(t, op=pg.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_value(units_per_rank: float, world: int, t_max: float) -> float:
+    """Whole-job throughput of `world` replicas: all ranks' units over the
+    slowest rank's time."""
+    return units_per_rank * world / t_max
+
+
 def _peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -760,12 +776,8 @@ def main():
 
     t_staged, t_cached, t_merge, t_iter_ev = (mean_span(0, 1), mean_span(1, 2), mean_span(2, 3),
                                               mean_span(0, 3))
-    t_max = elapsed
-    if pg:
-        tt = torch.tensor([elapsed])
-        pg.all_reduce(tt, op=pg.ReduceOp.MAX)
-        t_max = float(tt.item())
-    value = E * ITERS * args.steps * world / t_max / 1e9
+    t_max = max_over_ranks(elapsed, pg)
+    value = replica_value(E * ITERS * args.steps, world, t_max) / 1e9
 
     # ---- parity of the timed configuration (one solve, sampled rows, oracle-free
     # check of the rank mass; the full oracle comparison lives in the tests)
@@ -799,8 +811,8 @@ def main():
         e2e_step()
     e_stop.record(stream)
     torch.cuda.synchronize()
-    e2e_t = e_start.elapsed_time(e_stop) / 1e3
-    e2e_value = E * ITERS * e2e_steps * world / e2e_t / 1e9
+    e2e_t = max_over_ranks(e_start.elapsed_time(e_stop) / 1e3, pg)
+    e2e_value = replica_value(E * ITERS * e2e_steps, world, e2e_t) / 1e9
     e2e_ok = abs(float(out_h.double().sum()) - 1.0) < 1e-3
 
     # ---- comparisons on the same GPU: plain pull (original / clustered order), probe
