@@ -381,10 +381,11 @@ __device__ __forceinline__ void staged_load(const uint8_t* __restrict__ cs, int3
 }
 
 // The staged launch: segments [0, m) are read from a shared-memory copy of
-// their source values.  Work pieces of `piece` consecutive block-groups are
-// handed out in increasing order by an atomic counter: a block's groups only
-// move forward (so it stages each segment's table at most once) and a slow
-// block simply takes fewer pieces.  A warp's chunk is 512 edges of the
+// their source values.  Work pieces of consecutive block-groups (at most
+// `piece`, shrinking towards the end) are handed out in increasing order by
+// an atomic counter of block-groups: a block's groups only move forward (so
+// it stages each segment's table at most once) and a slow block simply
+// takes fewer pieces.  A warp's chunk is 512 edges of the
 // compressed stream (lane l holds 16); while it works on one chunk the TMA
 // unit prefetches its next one into L2.
 template <class Op, int THREADS>
@@ -400,7 +401,7 @@ staged_gather_kernel(const uint8_t* __restrict__ cs, const typename Op::T* __res
   constexpr int WARPS = THREADS / 32;
   constexpr int CHUNK = kStagedChunk;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  __shared__ int32_t s_piece;
+  __shared__ int32_t s_piece, s_size;
   T* tab = reinterpret_cast<T*>(smem_raw);
   const int tid = threadIdx.x, w = tid >> 5;
   int s = 0;
@@ -409,11 +410,20 @@ staged_gather_kernel(const uint8_t* __restrict__ cs, const typename Op::T* __res
 
   for (;;) {
     __syncthreads();  // everyone is done with the previous piece's s_piece
-    if (tid == 0) s_piece = (int32_t)atomicAdd(next_piece, 1u);
+    if (tid == 0) {
+      // guided self-scheduling: a piece is the remaining block-groups over
+      // twice the grid, at most `piece` and at least one, so the last
+      // pieces are small and the blocks finish together
+      const int32_t cur = (int32_t)*(volatile unsigned*)next_piece;
+      int32_t sz = (ct_end - cur) / (2 * (int32_t)gridDim.x);
+      sz = sz < 1 ? 1 : (sz > piece ? piece : sz);
+      s_piece = (int32_t)atomicAdd(next_piece, (unsigned)sz);
+      s_size = sz;
+    }
     __syncthreads();
-    const int32_t my_lo = s_piece * piece;
+    const int32_t my_lo = s_piece;
     if (my_lo >= ct_end) break;
-    const int32_t my_hi = my_lo + piece < ct_end ? my_lo + piece : ct_end;
+    const int32_t my_hi = my_lo + s_size < ct_end ? my_lo + s_size : ct_end;
     for (int32_t ct = my_lo; ct < my_hi;) {
       if (ct >= ctnext) {  // a new segment (uniform across the block)
         while (ct >= seg_ctile[s + 1]) ++s;

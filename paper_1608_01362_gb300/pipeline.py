@@ -199,7 +199,7 @@ def time_iterations(pr, iterations: int = 3, damping: float = 0.85, reps: int = 
     return times[len(times) // 2]
 
 
-def default_candidates(uniform_k=(1, 4), shapes=GATHER_SHAPES, min_deg=(4.0, 16.0, 64.0, 256.0),
+def default_candidates(uniform_k=(1, 4), shapes=GATHER_SHAPES, min_deg=(4.0, 16.0, 24.0, 32.0, 48.0, 64.0, 256.0),
                        tables=(-1, 0)):
     """Autotuner search space: the paper's uniform split into k segments, and
     the GPU plan (shared-memory segments over the hot head, L2 segments over
