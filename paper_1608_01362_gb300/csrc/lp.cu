@@ -25,11 +25,21 @@ lp_merge_update_kernel(const int32_t* __restrict__ blk, const int32_t* __restric
   const int n = (int)((V - v0) < B ? (V - v0) : B);
   warp_merge<MinI32>(blk, idx_map, interm, k, nb, mb, v0, n, acc);
   unsigned long long cnt = 0;
-  for (int i = lane; i < n; i += 32) {
-    const int32_t old = __ldcs(labels_in + v0 + i);
-    const int32_t l = acc[i] < old ? acc[i] : old;
-    __stcs(labels_out + v0 + i, l);
-    cnt += (l != old);
+  constexpr int U = 4;  // labels per lane loaded together
+  for (int i0 = lane; i0 < n; i0 += 32 * U) {
+    int32_t old[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+      old[u] = i0 + 32 * u < n ? __ldcs(labels_in + v0 + i0 + 32 * u) : 0;
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int i = i0 + 32 * u;
+      if (i < n) {
+        const int32_t l = acc[i] < old[u] ? acc[i] : old[u];
+        __stcs(labels_out + v0 + i, l);
+        cnt += (l != old[u]);
+      }
+    }
   }
   cnt = warp_sum(cnt);
   if (lane == 0 && cnt) atomicAdd(changed, cnt);

@@ -101,21 +101,37 @@ __device__ __forceinline__ void warp_vertex_update(const float* acc, int64_t v0,
   const int lane = threadIdx.x & 31;
   const float tele = (float)((1.0 - (double)a.d) + (double)a.d * Dfull);
   float dpart = 0.0f, rpart = 0.0f;  // <= B/32 terms per lane, then FP64
-  for (int i = lane; i < n; i += 32) {
-    const int64_t v = v0 + i;
-    float r;
-    if (a.seed < 0) {
-      r = a.base + a.d * (acc[i] + Dv);
-    } else {  // personalised: teleport and dangling mass return to the seed
-      r = a.d * acc[i];
-      if (v == a.seed) r += tele;
+  constexpr int U = 4;  // destinations per lane whose inputs are loaded together
+  for (int i0 = lane; i0 < n; i0 += 32 * U) {
+    float iv[U], old[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int i = i0 + 32 * u;
+      iv[u] = 0.0f;
+      old[u] = 0.0f;
+      if (i < n) {
+        iv[u] = __ldcs(a.inv + v0 + i);
+        old[u] = __ldcs(a.rank_in + v0 + i);
+      }
     }
-    const float iv = __ldcs(a.inv + v);
-    const float old = __ldcs(a.rank_in + v);
-    __stcs(a.rank_out + v, r);
-    __stcs(a.contrib_out + v, r * iv);
-    if (iv == 0.0f) dpart += r;
-    rpart += fabsf(r - old);
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int i = i0 + 32 * u;
+      if (i < n) {
+        const int64_t v = v0 + i;
+        float r;
+        if (a.seed < 0) {
+          r = a.base + a.d * (acc[i] + Dv);
+        } else {  // personalised: teleport and dangling mass return to the seed
+          r = a.d * acc[i];
+          if (v == a.seed) r += tele;
+        }
+        __stcs(a.rank_out + v, r);
+        __stcs(a.contrib_out + v, r * iv[u]);
+        if (iv[u] == 0.0f) dpart += r;
+        rpart += fabsf(r - old[u]);
+      }
+    }
   }
   *dsum = warp_sum((double)dpart);
   *rsum = warp_sum((double)rpart);
