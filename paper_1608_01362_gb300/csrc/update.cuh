@@ -101,7 +101,7 @@ __device__ __forceinline__ void warp_vertex_update(const float* acc, int64_t v0,
   const int lane = threadIdx.x & 31;
   const float tele = (float)((1.0 - (double)a.d) + (double)a.d * Dfull);
   float dpart = 0.0f, rpart = 0.0f;  // <= B/32 terms per lane, then FP64
-  constexpr int U = 4;  // destinations per lane whose inputs are loaded together
+  constexpr int U = 8;  // destinations per lane whose inputs are loaded together
   for (int i0 = lane; i0 < n; i0 += 32 * U) {
     float iv[U], old[U];
 #pragma unroll
