@@ -240,6 +240,15 @@ def run_lp(args):
                        "staged_segments": lp.seg.info["staged_segments"]},
             "passes": passes, "components": int(np.unique(labels).size),
             "generate_host_s": gen_s}
+    # roofline of one pass: B_min = 4E (arcs) + 8V (offsets) + 12V (labels gathered once,
+    # read by the update, written)
+    peak, peak_kind = _peaks()
+    bmin = 4 * g.E + 20 * g.V
+    ach = bmin / (dt / passes) / 1e9
+    line["roofline"] = {"bound": "hbm", "kernel": "one pass (gather + merge/update launches)",
+                        "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
+                        "traffic": None, "peak_source": peak_kind, "algorithmic_bytes": bmin}
+    line["gpu_launches"] = 4 * passes
     if not args.no_cpu_baseline:
         import oracle
         t0 = time.time()
