@@ -139,13 +139,15 @@ __device__ __forceinline__ uint32_t pick(const uint4& v, int c) {
 // at any moment belong to one or two segments' source slices.
 // ---------------------------------------------------------------------------
 template <int PLANES>
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(kThreads, 6)
 ppr_gather_kernel(const uint32_t* __restrict__ colf, const PprSeg* __restrict__ segs,
                   const int2* __restrict__ chunks, int64_t nchunks,
                   const uint4* __restrict__ c_hi, const uint4* __restrict__ c_lo,
                   float* __restrict__ interm, float* __restrict__ carry,
                   int32_t* __restrict__ carry_row) {
-  constexpr int U = 8 / PLANES;  // edges whose rows are loaded together
+  // edges whose rows are loaded together: one with two planes (more resident
+  // warps hide the latency better than more loads per warp)
+  constexpr int U = 2 / PLANES;
   const int lane8 = threadIdx.x & 7;
   const unsigned omask = 0xffu << (threadIdx.x & 24);
   const int64_t noct = ((int64_t)gridDim.x * blockDim.x) >> 3;
@@ -167,28 +169,31 @@ ppr_gather_kernel(const uint32_t* __restrict__ colf, const PprSeg* __restrict__ 
       const int m = min(32, n - sb);
       uint4 f4 = make_uint4(0u, 0u, 0u, 0u);
       if (4 * lane8 < m) f4 = __ldcs(cf + (sb >> 2) + lane8);
-      for (int g = 0; g < m; g += U) {
-        uint32_t f[U];
-        uint4 h[U], l[U];
+      for (int g = 0; g < m; g += 4) {  // the 4 edges held by octet lane g / 4
 #pragma unroll
-        for (int u = 0; u < U; ++u) {
-          f[u] = __shfl_sync(omask, pick(f4, u & 3), (g + u) >> 2, 8);
-          if (g + u < m) {
-            const int64_t s = (int64_t)(f[u] & ~kRowEnd) * 8;
-            h[u] = __ldg(hb + s);
-            if (PLANES == 2) l[u] = __ldg(lb + s);
+        for (int u0 = 0; u0 < 4; u0 += U) {
+          uint32_t f[U];
+          uint4 h[U], l[U];
+#pragma unroll
+          for (int u = 0; u < U; ++u) {
+            f[u] = __shfl_sync(omask, pick(f4, u0 + u), g >> 2, 8);
+            if (g + u0 + u < m) {
+              const int64_t s = (int64_t)(f[u] & ~kRowEnd) * 8;
+              h[u] = __ldg(hb + s);
+              if (PLANES == 2) l[u] = __ldg(lb + s);
+            }
           }
-        }
 #pragma unroll
-        for (int u = 0; u < U; ++u) {
-          if (g + u < m) {
-            if (PLANES == 2) add_row2(acc, h[u], l[u]); else add_row(acc, h[u]);
-            last = f[u];
-            if (f[u] & kRowEnd) {
-              store_row(interm + (int64_t)row * kCols + lane8 * 8, acc);
-              ++row;
+          for (int u = 0; u < U; ++u) {
+            if (g + u0 + u < m) {
+              if (PLANES == 2) add_row2(acc, h[u], l[u]); else add_row(acc, h[u]);
+              last = f[u];
+              if (f[u] & kRowEnd) {
+                store_row(interm + (int64_t)row * kCols + lane8 * 8, acc);
+                ++row;
 #pragma unroll
-              for (int q = 0; q < 8; ++q) acc[q] = 0.0f;
+                for (int q = 0; q < 8; ++q) acc[q] = 0.0f;
+              }
             }
           }
         }
