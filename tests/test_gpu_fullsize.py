@@ -1,0 +1,136 @@
+"""Parity at the benchmark sizes, in the launch configurations the bench times:
+RMAT-25 PageRank against the full FP64 oracle, RMAT-24 label propagation bit
+for bit, 64-vector PPR on RMAT-22 (sampled columns), CF on the Netflix-shaped
+ratings (two sweeps) and the 1,024-graph batch (sampled graphs).  These take a
+few minutes of host time for the oracle runs."""
+import os
+import sys
+
+import numpy as np
+import pytest
+
+import graphgen
+import oracle as O
+
+pytestmark = pytest.mark.gpu
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def env():
+    import torch
+    assert torch.cuda.is_available()
+    from paper_1608_01362_gb300 import build, cagra, pipeline
+    build.build()
+    cagra.load()
+    if ROOT not in sys.path:
+        sys.path.insert(0, ROOT)
+    return torch, cagra, pipeline
+
+
+def rel_l1(got, want):
+    return float(np.abs(np.asarray(got, np.float64) - want).sum() / np.abs(want).sum())
+
+
+def test_pagerank_rmat25_full(env):
+    """20 iterations on RMAT-25 with planned segments (staging threshold 24,
+    the autotuner's usual pick): relative L1 <= 1e-5 over all 33.5 M ranks."""
+    torch, C, P = env
+    g = graphgen.rmat(25, 16, seed=1)
+    graph = P.Graph(g.offsets, g.src, cluster_mode=0)
+    pr = P.SegmentedPageRank(graph, bounds=P.plan_bounds(graph, 1, 24.0))
+    rank, resid = pr.run(20)
+    got = rank.cpu().numpy()
+    del pr, graph
+    torch.cuda.empty_cache()
+    want, want_resid = O.pagerank(g.offsets, g.src, iters=20)
+    assert rel_l1(got, want) <= 1e-5
+    assert abs(float(got.astype(np.float64).sum()) - 1.0) <= 1e-4
+    r = resid.cpu().numpy()
+    assert np.all(np.abs(r - want_resid) <= 1e-2 * want_resid + 2.4e-7)
+
+
+def test_label_propagation_rmat24_full(env):
+    """Undirected RMAT-24, planned segments: final labels and pass count equal
+    the oracle's exactly."""
+    torch, C, P = env
+    g = graphgen.rmat(24, 16, seed=1, symmetric=True)
+    graph = P.Graph(g.offsets, g.src, cluster_mode=0)
+    lp = P.LabelPropagation(graph, bounds=P.plan_bounds(graph, 1, 16.0))
+    labels, passes, changes = lp.run()
+    got = labels.cpu().numpy()
+    del lp, graph
+    torch.cuda.empty_cache()
+    want, want_passes, want_changes = O.label_propagation(g.offsets, g.src,
+                                                          np.arange(g.V, dtype=np.int32))
+    assert passes == want_passes
+    assert np.array_equal(np.asarray(changes[:passes]), want_changes)
+    assert np.array_equal(got, want)
+
+
+def test_batched_ppr_rmat22_sampled_columns(env):
+    """64 vectors on RMAT-22 with the bench's seeds and 8 segments; eight
+    columns against the oracle within the hi+lo storage bound (1.5e-4)."""
+    torch, C, P = env
+    import bench
+    g = graphgen.rmat(22, 16, seed=1)
+    graph = P.Graph(g.offsets, g.src, cluster_mode=0)
+    nd = int((graph.outdeg > 0).sum().item())
+    b = P.BatchedPPR(graph, bounds=bench._ppr_bounds(nd, graph.V, 8), planes=2)
+    seeds = bench.ppr_seeds(g)
+    assert len(set(seeds.tolist())) == 64
+    R, _ = b.run(seeds, 20)
+    cols = np.array([0, 9, 18, 27, 36, 45, 54, 63])
+    got = R.cpu().numpy()[:, cols]
+    want = O.ppr(g.offsets, g.src, seeds[cols], iters=20)
+    for j in range(len(cols)):
+        assert rel_l1(got[:, j], want[:, j]) <= 1.5e-4
+
+
+def test_cf_netflix_shape_two_sweeps(env):
+    """The full rating graph, K = 32: two FP32 sweeps within 2e-6 of FP64 and
+    the SSE within 1e-5; BF16 hi+lo within its storage bound."""
+    torch, C, P = env
+    bp = graphgen.bipartite(seed=1)
+    dev = lambda a, dt: torch.as_tensor(np.ascontiguousarray(a), dtype=dt).cuda()  # noqa: E731
+    uoff, uitem, urate = (dev(bp.user_offsets, torch.int64), dev(bp.items, torch.int32),
+                          dev(bp.ratings, torch.uint8))
+    ioff = torch.empty(bp.I + 1, dtype=torch.int64, device="cuda")
+    iuser = torch.empty(bp.R, dtype=torch.int32, device="cuda")
+    irate = torch.empty(bp.R, dtype=torch.uint8, device="cuda")
+    C.cf_transpose(bp.U, bp.I, uoff, uitem, urate, ioff, iuser, irate)
+    P0, Q0 = graphgen.cf_factors(bp.U, bp.I, 32, seed=1)
+    P0, Q0 = P0.astype(np.float32), Q0.astype(np.float32)
+    io, iu, ir = O.item_major(bp.U, bp.I, bp.user_offsets, bp.items, bp.ratings)
+    Pw, Qw = P0.astype(np.float64), Q0.astype(np.float64)
+    want_sse = []
+    for _ in range(2):
+        Pw, Qw, e = O.cf_sweep(bp.U, bp.I, bp.user_offsets, bp.items, bp.ratings, io, iu, ir, Pw,
+                               Qw, 0.05, 1e-3)
+        want_sse.append(e)
+    want_sse = np.array(want_sse)
+    for prec, tol in ((C.CF_FP32, 2e-6), (C.CF_BF16X2, 3 * 2.0 ** -16 + 2e-6)):
+        h = C.cf_create(bp.U, bp.I, 32, prec, uoff, uitem, urate, ioff, iuser, irate)
+        C.cf_set_factors(h, dev(P0, torch.float32), dev(Q0, torch.float32))
+        sse = torch.zeros(2, dtype=torch.float64, device="cuda")
+        C.cf_sweep(h, 2, 0.05, 1e-3, sse)
+        Pg = torch.empty((bp.U, 32), dtype=torch.float32, device="cuda")
+        Qg = torch.empty((bp.I, 32), dtype=torch.float32, device="cuda")
+        C.cf_get_factors(h, Pg, Qg)
+        assert np.max(np.abs(Pg.cpu().numpy() - Pw)) <= tol * np.max(np.abs(Pw))
+        assert np.max(np.abs(Qg.cpu().numpy() - Qw)) <= tol * np.max(np.abs(Qw))
+        if prec == C.CF_FP32:
+            assert np.all(np.abs(sse.cpu().numpy() - want_sse) <= 1e-5 * want_sse)
+        del h
+
+
+def test_batched_1024_graphs_sampled(env):
+    """The 1,024-graph batch in one launch; 32 graphs against the oracle."""
+    torch, C, P = env
+    gs = graphgen.small_graph_batch(count=1024, seed=1, scale_lo=8, scale_hi=15)
+    bpr = P.BatchedPageRank(gs, threads=512)
+    rank = bpr.run(20).cpu().numpy()
+    for i in range(0, 1024, 32):
+        want, _ = O.pagerank(gs[i].offsets, gs[i].src, iters=20)
+        assert rel_l1(rank[bpr.vbase[i]:bpr.vbase[i + 1]], want) <= 1e-5
