@@ -20,7 +20,11 @@
 //                      stay in L2), and writes each subgraph row's 64 sums
 //                      to intermBuf; the row open at the chunk's end goes
 //                      to a carry slot;
-//   ppr_fixup_kernel   adds each run of carries into its row, in chunk order;
+//   ppr_fixup_kernel   completes the rows that span chunks: each run of
+//                      carries (consecutive chunks open on the same row, a
+//                      static structure) is cut into pieces of <= 32 chunks
+//                      summed in parallel; the last piece of a run adds the
+//                      pieces' sums, in order, into the row;
 //   ppr_merge_kernel   an octet takes 16 consecutive destinations, sums
 //                      their intermBuf rows (destination-major list of the
 //                      rows, in segment order), applies the update and
@@ -28,6 +32,7 @@
 //                      reduced by the last block.
 #include <cuda_bf16.h>
 
+#include <algorithm>
 #include <vector>
 
 #include "handles.cuh"
@@ -59,7 +64,11 @@ struct cg_ppr {
   cg::PprSeg* segs = nullptr;    // [k]
   int2* chunks = nullptr;        // [nchunks] (first subgraph row, segment)
   float* carry = nullptr;        // [nchunks][64]
-  int32_t* carry_row = nullptr;  // [nchunks]
+  int4* pieces = nullptr;        // [npieces] (first chunk, chunks, run, -)
+  int4* runs = nullptr;          // [nruns] (row, first piece, pieces, -)
+  float* piece_sum = nullptr;    // [npieces][64]
+  unsigned* run_done = nullptr;  // [nruns] pieces of the run finished (last-piece detection)
+  int64_t npieces = 0, nruns = 0;
   int32_t* dst_off = nullptr;    // [V+1] destination-major row lists
   int32_t* dst_rows = nullptr;   // [rows]
   float* interm = nullptr;       // [rows][64] intermBuf
@@ -143,8 +152,7 @@ __global__ void __launch_bounds__(kThreads, 6)
 ppr_gather_kernel(const uint32_t* __restrict__ colf, const PprSeg* __restrict__ segs,
                   const int2* __restrict__ chunks, int64_t nchunks,
                   const uint4* __restrict__ c_hi, const uint4* __restrict__ c_lo,
-                  float* __restrict__ interm, float* __restrict__ carry,
-                  int32_t* __restrict__ carry_row) {
+                  float* __restrict__ interm, float* __restrict__ carry) {
   // edges whose rows are loaded together: one with two planes (more resident
   // warps hide the latency better than more loads per warp)
   constexpr int U = 2 / PLANES;
@@ -199,36 +207,65 @@ ppr_gather_kernel(const uint32_t* __restrict__ colf, const PprSeg* __restrict__ 
         }
       }
     }
-    const bool open = !(last & kRowEnd);
-    if (open) store_row(carry + c * kCols + lane8 * 8, acc);
-    if (lane8 == 0) carry_row[c] = open ? row : -1;
+    if (!(last & kRowEnd)) store_row(carry + c * kCols + lane8 * 8, acc);  // open row
   }
 }
 
-// Rows that span chunks: the first chunk of each run of equal carry_row adds
-// the run's carries, in chunk order, into the row (whose final part the
-// chunk where it ends has already written).
+// Rows that span chunks.  One octet per piece (<= 32 consecutive chunks of
+// one run): it sums the pieces' carries in chunk order.  A run of one piece
+// adds its sum into the row directly; otherwise each piece stores its sum and
+// the last piece of the run to finish (atomic count, no waiting) adds the
+// pieces' sums in piece order into the row -- deterministic, and a hub row
+// spanning thousands of chunks no longer holds up one octet.
 __global__ void __launch_bounds__(kThreads)
-ppr_fixup_kernel(const float* __restrict__ carry, const int32_t* __restrict__ carry_row,
-                 int64_t nchunks, float* __restrict__ interm) {
+ppr_fixup_kernel(const int4* __restrict__ pieces, int64_t npieces, const int4* __restrict__ runs,
+                 const float* __restrict__ carry, float* __restrict__ piece_sum,
+                 unsigned* __restrict__ run_done, float* __restrict__ interm) {
   const int lane8 = threadIdx.x & 7;
+  const unsigned omask = 0xffu << (threadIdx.x & 24);
   const int64_t noct = ((int64_t)gridDim.x * blockDim.x) >> 3;
-  for (int64_t c = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 3; c < nchunks;
-       c += noct) {
-    const int32_t r = carry_row[c];
-    if (r < 0 || (c > 0 && carry_row[c - 1] == r)) continue;
+  for (int64_t p = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 3; p < npieces;
+       p += noct) {
+    const int4 pc = __ldg(pieces + p);  // (first chunk, chunks, run)
+    const int4 rn = __ldg(runs + pc.z); // (row, first piece, pieces)
     float sum[8], x[8];
-    load_row(carry + c * kCols + lane8 * 8, sum);
-    for (int64_t c2 = c + 1; c2 < nchunks && carry_row[c2] == r; ++c2) {
-      load_row(carry + c2 * kCols + lane8 * 8, x);
+    load_row(carry + (int64_t)pc.x * kCols + lane8 * 8, sum);
+    for (int j = 1; j < pc.y; ++j) {
+      load_row(carry + ((int64_t)pc.x + j) * kCols + lane8 * 8, x);
 #pragma unroll
       for (int q = 0; q < 8; ++q) sum[q] += x[q];
     }
-    float* dst = interm + (int64_t)r * kCols + lane8 * 8;
+    float* dst = interm + (int64_t)rn.x * kCols + lane8 * 8;
+    if (rn.z == 1) {
+      load_row(dst, x);
+#pragma unroll
+      for (int q = 0; q < 8; ++q) x[q] += sum[q];
+      store_row(dst, x);
+      continue;
+    }
+    store_row(piece_sum + p * kCols + lane8 * 8, sum);
+    __threadfence();
+    __syncwarp(omask);
+    unsigned prev = 0;
+    if (lane8 == 0) prev = atomicAdd(run_done + pc.z, 1u);
+    prev = __shfl_sync(omask, prev, 0, 8);
+    if (prev != (unsigned)rn.z - 1) continue;  // not the run's last piece
+    __threadfence();
+    float tot[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) tot[q] = 0.0f;
+    for (int j = 0; j < rn.z; ++j) {
+      const float4* ps =
+          reinterpret_cast<const float4*>(piece_sum + ((int64_t)rn.y + j) * kCols + lane8 * 8);
+      const float4 u = __ldcg(ps), w = __ldcg(ps + 1);
+      tot[0] += u.x; tot[1] += u.y; tot[2] += u.z; tot[3] += u.w;
+      tot[4] += w.x; tot[5] += w.y; tot[6] += w.z; tot[7] += w.w;
+    }
     load_row(dst, x);
 #pragma unroll
-    for (int q = 0; q < 8; ++q) x[q] += sum[q];
+    for (int q = 0; q < 8; ++q) x[q] += tot[q];
     store_row(dst, x);
+    if (lane8 == 0) run_done[pc.z] = 0u;  // ready for the next iteration
   }
 }
 
@@ -438,6 +475,29 @@ __global__ void ppr_chunks_kernel(const int32_t* __restrict__ rp, const int64_t*
   }
 }
 
+// The row open at each chunk's end (-1 when the chunk ends a row): the
+// subgraph row of the chunk's last edge, if that row continues past it.
+__global__ void carry_rows_kernel(const int32_t* __restrict__ rp, const int64_t* __restrict__ meta,
+                                  const PprSeg* __restrict__ segs, const int2* __restrict__ chunks,
+                                  int k, int64_t nchunks, int32_t* __restrict__ carry_row) {
+  const int64_t* row_base = meta;
+  const int64_t* edge_base = meta + (k + 1);
+  for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < nchunks;
+       c += (int64_t)gridDim.x * blockDim.x) {
+    const int s = chunks[c].y;
+    const int64_t el = (c - segs[s].chunk0) * kChunk;
+    const int64_t n = min((int64_t)kChunk, (int64_t)segs[s].E - el);
+    const int64_t e = edge_base[s] + el + n - 1;  // global index of the chunk's last edge
+    int64_t lo = row_base[s], hi = row_base[s + 1];  // last row with rp[row] <= e
+    while (lo < hi) {
+      const int64_t mid = (lo + hi) >> 1;
+      if (rp[mid] <= e) lo = mid + 1; else hi = mid;
+    }
+    const int64_t row = lo - 1;
+    carry_row[c] = (int64_t)rp[row + 1] - 1 > e ? (int32_t)row : -1;
+  }
+}
+
 __global__ void count_dst_kernel(const int32_t* __restrict__ idx_map, int64_t rows,
                                  int32_t* __restrict__ cnt) {
   for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < rows;
@@ -515,20 +575,18 @@ int gather_launch(cg_ppr* p, cudaStream_t s) {
   const SegPlan& sp = p->seg->plan;
   if (p->planes == 2)
     ppr_gather_kernel<2><<<p->gather_grid, kThreads, 0, s>>>(
-        sp.colf, p->segs, p->chunks, p->nchunks, p->c_hi, p->c_lo, p->interm, p->carry,
-        p->carry_row);
+        sp.colf, p->segs, p->chunks, p->nchunks, p->c_hi, p->c_lo, p->interm, p->carry);
   else
     ppr_gather_kernel<1><<<p->gather_grid, kThreads, 0, s>>>(
-        sp.colf, p->segs, p->chunks, p->nchunks, p->c_hi, p->c_hi, p->interm, p->carry,
-        p->carry_row);
+        sp.colf, p->segs, p->chunks, p->nchunks, p->c_hi, p->c_hi, p->interm, p->carry);
   CG_LAUNCH_CHECK();
   return CG_OK;
 }
 
 int fixup_launch(cg_ppr* p, cudaStream_t s) {
-  if (p->nchunks == 0) return CG_OK;
-  ppr_fixup_kernel<<<grid_for(p->nchunks * 8, kThreads, 8), kThreads, 0, s>>>(
-      p->carry, p->carry_row, p->nchunks, p->interm);
+  if (p->npieces == 0) return CG_OK;
+  ppr_fixup_kernel<<<grid_for(p->npieces * 8, kThreads, 8), kThreads, 0, s>>>(
+      p->pieces, p->npieces, p->runs, p->carry, p->piece_sum, p->run_done, p->interm);
   CG_LAUNCH_CHECK();
   return CG_OK;
 }
@@ -537,7 +595,10 @@ void ppr_free(cg_ppr* p) {
   cudaFree(p->segs);
   cudaFree(p->chunks);
   cudaFree(p->carry);
-  cudaFree(p->carry_row);
+  cudaFree(p->pieces);
+  cudaFree(p->runs);
+  cudaFree(p->piece_sum);
+  cudaFree(p->run_done);
   cudaFree(p->dst_off);
   cudaFree(p->dst_rows);
   cudaFree(p->interm);
@@ -579,11 +640,48 @@ int ppr_build(cg_ppr* p, cudaStream_t s) {
   CG_CUDA(cudaMemcpyAsync(p->segs, hs.data(), sizeof(PprSeg) * k, cudaMemcpyHostToDevice, s));
   CG_CUDA(alloc(&p->chunks, nch, &B));
   CG_CUDA(alloc(&p->carry, nch * kCols, &B));
-  CG_CUDA(alloc(&p->carry_row, nch, &B));
   if (nch > 0) {
     ppr_chunks_kernel<<<grid_for(nch, 256), 256, 0, s>>>(sp.rp32, sp.meta, p->segs, k, nch,
                                                           p->chunks);
     CG_LAUNCH_CHECK();
+    // runs of carries (static) cut into pieces of <= 32 chunks
+    int32_t* crow = nullptr;
+    CG_CUDA(cudaMallocAsync((void**)&crow, sizeof(int32_t) * (size_t)nch, s));
+    carry_rows_kernel<<<grid_for(nch, 256), 256, 0, s>>>(sp.rp32, sp.meta, p->segs, p->chunks,
+                                                         k, nch, crow);
+    cudaError_t ce = cudaGetLastError();
+    std::vector<int32_t> hc((size_t)nch);
+    if (ce == cudaSuccess)
+      ce = cudaMemcpyAsync(hc.data(), crow, sizeof(int32_t) * (size_t)nch,
+                           cudaMemcpyDeviceToHost, s);
+    if (ce == cudaSuccess) ce = cudaStreamSynchronize(s);
+    cudaFreeAsync(crow, s);
+    if (ce != cudaSuccess) return cuda_fail(ce, "ppr_batched_create", __FILE__, __LINE__);
+    std::vector<int4> hp, hr;
+    for (int64_t c = 0; c < nch;) {
+      if (hc[c] < 0) { ++c; continue; }
+      int64_t e = c + 1;
+      while (e < nch && hc[e] == hc[c]) ++e;
+      const int32_t run = (int32_t)hr.size(), p0 = (int32_t)hp.size();
+      for (int64_t x = c; x < e; x += 32)
+        hp.push_back(make_int4((int32_t)x, (int32_t)std::min<int64_t>(32, e - x), run, 0));
+      hr.push_back(make_int4(hc[c], p0, (int32_t)hp.size() - p0, 0));
+      c = e;
+    }
+    p->npieces = (int64_t)hp.size();
+    p->nruns = (int64_t)hr.size();
+    CG_CUDA(alloc(&p->pieces, p->npieces, &B));
+    CG_CUDA(alloc(&p->runs, p->nruns, &B));
+    CG_CUDA(alloc(&p->piece_sum, p->npieces * kCols, &B));
+    CG_CUDA(alloc(&p->run_done, p->nruns, &B));
+    if (p->npieces > 0) {
+      CG_CUDA(cudaMemcpyAsync(p->pieces, hp.data(), sizeof(int4) * hp.size(),
+                              cudaMemcpyHostToDevice, s));
+      CG_CUDA(cudaMemcpyAsync(p->runs, hr.data(), sizeof(int4) * hr.size(),
+                              cudaMemcpyHostToDevice, s));
+      CG_CUDA(cudaMemsetAsync(p->run_done, 0, sizeof(unsigned) * hr.size(), s));
+      CG_CUDA(cudaStreamSynchronize(s));  // hp / hr go out of scope
+    }
   }
   // destination-major row lists
   const int32_t V = p->V;
