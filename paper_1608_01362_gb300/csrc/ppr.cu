@@ -292,7 +292,7 @@ struct MergeArgs {
 };
 
 template <int PLANES, bool RESID>
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(kThreads, 4)
 ppr_merge_kernel(MergeArgs a) {
   __shared__ float s_tele[kCols];
   __shared__ int32_t s_seed[kCols];
@@ -368,7 +368,7 @@ ppr_merge_kernel(MergeArgs a) {
     };
     const int32_t o_lo = off_of(0);
     int32_t iend = off_of(1);
-    constexpr int G = 4;  // intermBuf rows loaded together
+    constexpr int G = 2;  // intermBuf rows loaded together (4 blocks per SM fit)
     for (int32_t p = o_lo; p < o_end; p += G) {
       int32_t rr[G];
       float4 x[G], y[G];
