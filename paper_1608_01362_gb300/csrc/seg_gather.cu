@@ -54,6 +54,62 @@ __global__ void export_col_kernel(const uint32_t* __restrict__ colf,
   }
 }
 
+// The row open at each chunk's end (-1 when the chunk ends a row): the
+// subgraph row of the chunk's last edge, if that row continues past it.
+__global__ void open_row_kernel(const int32_t* __restrict__ rp,
+                                const int64_t* __restrict__ row_base,
+                                const int64_t* __restrict__ edge_base,
+                                const int64_t* __restrict__ chunk_base, int k, int m, int chunk_a,
+                                int chunk_b, int64_t nchunks, int32_t* __restrict__ open_row) {
+  for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < nchunks;
+       c += (int64_t)gridDim.x * blockDim.x) {
+    const int s = last_le(chunk_base, k + 1, c);
+    const int64_t size = s < m ? chunk_a : chunk_b;
+    const int64_t e0 = edge_base[s] + (c - chunk_base[s]) * size;
+    const int64_t e = min(e0 + size, edge_base[s + 1]) - 1;  // the chunk's last edge
+    int64_t lo = row_base[s], hi = row_base[s + 1];  // last row with rp[row] <= e
+    while (lo < hi) {
+      const int64_t mid = (lo + hi) >> 1;
+      if (rp[mid] <= e) lo = mid + 1; else hi = mid;
+    }
+    open_row[c] = (int64_t)rp[lo] - 1 > e ? (int32_t)(lo - 1) : -1;
+  }
+}
+
+// Completion of the rows that span chunks, one thread per piece (<= 32
+// consecutive chunks of one run of carries on the same row).  A one-piece
+// run folds its carries into the row directly; otherwise every piece stores
+// its fold and the last piece of the run to finish (an atomic count, no
+// waiting) folds the pieces in order into the row.  Deterministic, and a hub
+// row spanning many chunks is spread over many threads.
+template <class Op>
+__global__ void seg_fixup_kernel(const int4* __restrict__ pieces, int64_t npieces,
+                                 const int4* __restrict__ runs,
+                                 const typename Op::T* __restrict__ carry,
+                                 typename Op::T* __restrict__ psum, unsigned* __restrict__ done,
+                                 typename Op::T* __restrict__ out) {
+  using T = typename Op::T;
+  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < npieces;
+       p += (int64_t)gridDim.x * blockDim.x) {
+    const int4 pc = pieces[p];  // (first chunk, chunks, run)
+    const int4 rn = runs[pc.z]; // (row, first piece, pieces)
+    T v = carry[pc.x];
+    for (int j = 1; j < pc.y; ++j) v = Op::op(v, carry[pc.x + j]);
+    if (rn.z == 1) {
+      out[rn.x] = Op::op(v, out[rn.x]);
+      continue;
+    }
+    psum[p] = v;
+    __threadfence();
+    if (atomicAdd(done + pc.z, 1u) != (unsigned)rn.z - 1) continue;
+    __threadfence();
+    T t = __ldcg(psum + rn.y);
+    for (int j = 1; j < rn.z; ++j) t = Op::op(t, __ldcg(psum + rn.y + j));
+    out[rn.x] = Op::op(t, out[rn.x]);
+    done[pc.z] = 0u;  // ready for the next pass
+  }
+}
+
 // Subgraph row of each chunk's first edge (segments [0, m) use chunks of
 // chunk_a edges, the others chunks of chunk_b).
 __global__ void first_row_kernel(const int32_t* __restrict__ rp,
@@ -612,6 +668,54 @@ int seg_plan_configure(SegPlan* p, int threads, int ctas_per_sm, int tab_vertice
         p->colf, p->seg_chunk, p->seg_cstart, p->seg_E, p->first_row, m, chunk[m], p->cs);
     CG_LAUNCH_CHECK();
   }
+  // static runs of carries, cut into pieces for the parallel completion
+  cudaFree(p->fx_pieces);
+  cudaFree(p->fx_runs);
+  cudaFree(p->fx_sum);
+  cudaFree(p->fx_done);
+  p->fx_pieces = nullptr;
+  p->fx_runs = nullptr;
+  p->fx_sum = nullptr;
+  p->fx_done = nullptr;
+  p->fx_npieces = p->fx_nruns = 0;
+  if (nchunks > 0) {
+    int32_t* orow = nullptr;
+    CG_CUDA(cudaMallocAsync((void**)&orow, sizeof(int32_t) * (size_t)nchunks, s));
+    open_row_kernel<<<grid_for(nchunks, 256), 256, 0, s>>>(
+        p->rp32, p->meta, p->meta + (k + 1), p->seg_chunk, k, m, chunk_a, chunk_b, nchunks, orow);
+    cudaError_t ce = cudaGetLastError();
+    std::vector<int32_t> hc((size_t)nchunks);
+    if (ce == cudaSuccess)
+      ce = cudaMemcpyAsync(hc.data(), orow, sizeof(int32_t) * (size_t)nchunks,
+                           cudaMemcpyDeviceToHost, s);
+    if (ce == cudaSuccess) ce = cudaStreamSynchronize(s);
+    cudaFreeAsync(orow, s);
+    if (ce != cudaSuccess) return cuda_fail(ce, "segmented gather: carry runs", __FILE__, __LINE__);
+    std::vector<int4> hp, hr;
+    for (int64_t c = 0; c < nchunks;) {
+      if (hc[c] < 0) { ++c; continue; }
+      int64_t e = c + 1;
+      while (e < nchunks && hc[e] == hc[c]) ++e;
+      const int32_t run = (int32_t)hr.size(), p0 = (int32_t)hp.size();
+      for (int64_t x = c; x < e; x += 32)
+        hp.push_back(make_int4((int32_t)x, (int32_t)std::min<int64_t>(32, e - x), run, 0));
+      hr.push_back(make_int4(hc[c], p0, (int32_t)hp.size() - p0, 0));
+      c = e;
+    }
+    p->fx_npieces = (int64_t)hp.size();
+    p->fx_nruns = (int64_t)hr.size();
+    if (!hp.empty()) {
+      CG_CUDA(cudaMalloc((void**)&p->fx_pieces, sizeof(int4) * hp.size()));
+      CG_CUDA(cudaMalloc((void**)&p->fx_runs, sizeof(int4) * hr.size()));
+      CG_CUDA(cudaMalloc(&p->fx_sum, 4 * hp.size()));
+      CG_CUDA(cudaMalloc((void**)&p->fx_done, sizeof(unsigned) * hr.size()));
+      CG_CUDA(cudaMemcpyAsync(p->fx_pieces, hp.data(), sizeof(int4) * hp.size(),
+                              cudaMemcpyHostToDevice, s));
+      CG_CUDA(cudaMemcpyAsync(p->fx_runs, hr.data(), sizeof(int4) * hr.size(),
+                              cudaMemcpyHostToDevice, s));
+      CG_CUDA(cudaMemsetAsync(p->fx_done, 0, sizeof(unsigned) * hr.size(), s));
+    }
+  }
   CG_CUDA(cudaStreamSynchronize(s));  // host vectors go out of scope
   p->threads = threads;
   p->ctas_per_sm = ctas_per_sm;
@@ -646,6 +750,10 @@ void seg_plan_free(SegPlan* p) {
   cudaFree(p->first_row);
   cudaFree(p->carry);
   cudaFree(p->carry_row);
+  cudaFree(p->fx_pieces);
+  cudaFree(p->fx_runs);
+  cudaFree(p->fx_sum);
+  cudaFree(p->fx_done);
   *p = SegPlan();
 }
 
@@ -700,9 +808,10 @@ int run_seg_gather(const SegPlan& p, const typename Op::T* x, int32_t nx, typena
         p.k, p.ct_split, (int32_t)p.n_ctiles, out, reinterpret_cast<T*>(p.carry), p.carry_row);
     CG_LAUNCH_CHECK();
   }
-  if (phases & kPhaseFixup) {
-    carry_fixup_kernel<Op><<<grid_for(p.nchunks, 256, 4), 256, 0, s>>>(
-        reinterpret_cast<const T*>(p.carry), p.carry_row, p.nchunks, p.rows, out);
+  if ((phases & kPhaseFixup) && p.fx_npieces > 0) {
+    seg_fixup_kernel<Op><<<grid_for(p.fx_npieces, 256, 4), 256, 0, s>>>(
+        p.fx_pieces, p.fx_npieces, p.fx_runs, reinterpret_cast<const T*>(p.carry),
+        reinterpret_cast<T*>(p.fx_sum), p.fx_done, out);
     CG_LAUNCH_CHECK();
   }
   return CG_OK;

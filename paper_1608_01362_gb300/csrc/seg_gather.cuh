@@ -67,6 +67,13 @@ struct SegPlan {
   int32_t piece = 1;        // block-groups per work piece of the staged launch
   unsigned* counter = nullptr;  // next staged work piece
   int grid_l2 = 0;          // unstaged launch blocks (1024 threads, 2 per SM)
+  // rows spanning chunks: runs of carries (a static structure) cut into
+  // pieces of <= 32 chunks, completed in parallel (see run_seg_gather)
+  int4* fx_pieces = nullptr;   // [fx_npieces] (first chunk, chunks, run, -)
+  int4* fx_runs = nullptr;     // [fx_nruns] (row, first piece, pieces, -)
+  void* fx_sum = nullptr;      // [fx_npieces] 4-byte piece sums
+  unsigned* fx_done = nullptr; // [fx_nruns] finished pieces per run
+  int64_t fx_npieces = 0, fx_nruns = 0;
 };
 
 // Largest shared table (entries, multiple of 32) for `ctas` blocks per SM.
