@@ -492,7 +492,8 @@ int cf_transpose(int64_t U, int64_t I, const int64_t *dev_uoff, const int32_t *d
  * degree-averaged gradient).  The rating CSRs of both sides (from
  * cf_transpose) are NOT copied and must stay valid.  K = 16, 32 or 64
  * latent dimensions.  precision: 0 stores P, Q in FP32, 1 in BF16, 2 as
- * BF16 hi + lo planes (hi = bf16(x), lo = bf16(x - hi)); arithmetic is FP32
+ * BF16 hi + lo pairs (hi = bf16(x), lo = bf16(x - hi), packed in one 32-bit
+ * word per entry: a row has the size and alignment of FP32); arithmetic is FP32
  * and the squared-error sum FP64.  The handle owns the factor storage (see
  * cf_set_factors).  Synchronizes.
  */

@@ -16,8 +16,9 @@
 // lane 8 dimensions: 32 or 16 bytes of the row).  Piece partial gradients
 // are summed per vertex, in piece order, by the update kernel.
 //
-// Storage precision of P and Q: FP32, BF16, or BF16 hi + lo planes
-// (hi = bf16(x), lo = bf16(x - hi)); arithmetic is FP32, SSE is FP64.
+// Storage precision of P and Q: FP32, BF16, or BF16 hi + lo pairs
+// (hi = bf16(x), lo = bf16(x - hi), packed in one 32-bit word per entry);
+// arithmetic is FP32, SSE is FP64.
 #include <cuda_bf16.h>
 
 #include <vector>
@@ -49,7 +50,7 @@ struct cg_bipartite {
   float* gpart[2] = {nullptr, nullptr};  // [npieces][K] piece gradients
   int32_t* wide[2] = {nullptr, nullptr};  // vertices with more than kCfWide pieces
   int32_t nwide[2] = {0, 0};
-  // factor storage: plane 0 = FP32 / BF16 / BF16 hi, plane 1 = BF16 lo
+  // factor storage (FP32, BF16, or BF16 hi + lo words); index 1 unused
   void* P[2] = {nullptr, nullptr};
   void* Q[2] = {nullptr, nullptr};
   double* partials = nullptr;  // [gather grid] SSE
@@ -75,46 +76,53 @@ __device__ __forceinline__ uint32_t pk(float a, float b) {
 }
 
 // 8 consecutive dimensions of row `row` (K per row) in the storage format.
+// BF16 hi + lo is stored as one 32-bit word per dimension (hi in the low
+// half, lo in the high half), so a row is one 128-byte line at K = 32, like
+// FP32, and a lane reads its 8 dimensions with two 16-byte loads.
+__device__ __forceinline__ float hilo(uint32_t w) { return b_lo(w) + b_hi(w); }
+
 template <int PREC>
-__device__ __forceinline__ void load8(const void* p0, const void* p1, int64_t row, int K, int d0,
-                                      float (&y)[8]) {
+__device__ __forceinline__ void load8(const void* p0, int64_t row, int K, int d0, float (&y)[8]) {
   const int64_t at = row * K + d0;
   if (PREC == 0) {
     const float4* f = reinterpret_cast<const float4*>(static_cast<const float*>(p0) + at);
     const float4 a = __ldg(f), b = __ldg(f + 1);
     y[0] = a.x; y[1] = a.y; y[2] = a.z; y[3] = a.w;
     y[4] = b.x; y[5] = b.y; y[6] = b.z; y[7] = b.w;
+  } else if (PREC == 1) {
+    unpack8(__ldg(reinterpret_cast<const uint4*>(static_cast<const uint16_t*>(p0) + at)), y);
   } else {
-    const uint4 h = __ldg(reinterpret_cast<const uint4*>(static_cast<const uint16_t*>(p0) + at));
-    unpack8(h, y);
-    if (PREC == 2) {
-      float l[8];
-      unpack8(__ldg(reinterpret_cast<const uint4*>(static_cast<const uint16_t*>(p1) + at)), l);
-#pragma unroll
-      for (int q = 0; q < 8; ++q) y[q] += l[q];
-    }
+    const uint4* f = reinterpret_cast<const uint4*>(static_cast<const uint32_t*>(p0) + at);
+    const uint4 a = __ldg(f), b = __ldg(f + 1);
+    y[0] = hilo(a.x); y[1] = hilo(a.y); y[2] = hilo(a.z); y[3] = hilo(a.w);
+    y[4] = hilo(b.x); y[5] = hilo(b.y); y[6] = hilo(b.z); y[7] = hilo(b.w);
   }
 }
 
+// hi = bf16(x), lo = bf16(x - hi) as one word (hi low, lo high)
+__device__ __forceinline__ uint32_t pack_hilo(float x) {
+  const uint32_t h = (uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(x));
+  const float hf = __uint_as_float(h << 16);
+  const uint32_t l = (uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(x - hf));
+  return h | (l << 16);
+}
+
 template <int PREC>
-__device__ __forceinline__ void store8(void* p0, void* p1, int64_t row, int K, int d0,
-                                       const float (&x)[8]) {
+__device__ __forceinline__ void store8(void* p0, int64_t row, int K, int d0, const float (&x)[8]) {
   const int64_t at = row * K + d0;
   if (PREC == 0) {
     float4* f = reinterpret_cast<float4*>(static_cast<float*>(p0) + at);
     f[0] = make_float4(x[0], x[1], x[2], x[3]);
     f[1] = make_float4(x[4], x[5], x[6], x[7]);
-  } else {
-    uint32_t h[4], l[4];
+  } else if (PREC == 1) {
+    uint32_t h[4];
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      h[q] = pk(x[2 * q], x[2 * q + 1]);
-      l[q] = pk(x[2 * q] - b_lo(h[q]), x[2 * q + 1] - b_hi(h[q]));
-    }
+    for (int q = 0; q < 4; ++q) h[q] = pk(x[2 * q], x[2 * q + 1]);
     *reinterpret_cast<uint4*>(static_cast<uint16_t*>(p0) + at) = make_uint4(h[0], h[1], h[2], h[3]);
-    if (PREC == 2)
-      *reinterpret_cast<uint4*>(static_cast<uint16_t*>(p1) + at) =
-          make_uint4(l[0], l[1], l[2], l[3]);
+  } else {
+    uint4* f = reinterpret_cast<uint4*>(static_cast<uint32_t*>(p0) + at);
+    f[0] = make_uint4(pack_hilo(x[0]), pack_hilo(x[1]), pack_hilo(x[2]), pack_hilo(x[3]));
+    f[1] = make_uint4(pack_hilo(x[4]), pack_hilo(x[5]), pack_hilo(x[6]), pack_hilo(x[7]));
   }
 }
 
@@ -128,8 +136,7 @@ __global__ void __launch_bounds__(kCfThreads)
 cf_gather_kernel(const int32_t* __restrict__ pvtx, const int64_t* __restrict__ pbeg,
                  const int64_t* __restrict__ off, int64_t npieces,
                  const int32_t* __restrict__ nbr, const uint8_t* __restrict__ rate,
-                 const void* __restrict__ s0, const void* __restrict__ s1,
-                 const void* __restrict__ n0, const void* __restrict__ n1,
+                 const void* __restrict__ s0, const void* __restrict__ n0,
                  float* __restrict__ gpart, double* __restrict__ partials,
                  unsigned* __restrict__ counter, double* __restrict__ sse_out) {
   constexpr int K = 8 * LANES;
@@ -147,7 +154,7 @@ cf_gather_kernel(const int32_t* __restrict__ pvtx, const int64_t* __restrict__ p
     const int64_t vend = __ldg(off + v + 1);
     const int64_t e_end = min(b + kCfPiece, vend);
     float x[8], g[8];
-    load8<PREC>(s0, s1, v, K, d0, x);
+    load8<PREC>(s0, v, K, d0, x);
 #pragma unroll
     for (int q = 0; q < 8; ++q) g[q] = 0.0f;
     float se = 0.0f;
@@ -162,8 +169,8 @@ cf_gather_kernel(const int32_t* __restrict__ pvtx, const int64_t* __restrict__ p
       const float rt1 = (float)__ldcs(rate + r);
       const float rt2 = has2 ? (float)__ldcs(rate + r2) : 0.0f;
       float y1[8], y2[8];
-      load8<PREC>(n0, n1, u1, K, d0, y1);
-      load8<PREC>(n0, n1, u2, K, d0, y2);
+      load8<PREC>(n0, u1, K, d0, y1);
+      load8<PREC>(n0, u2, K, d0, y2);
       float t1 = 0.0f, t2 = 0.0f;
 #pragma unroll
       for (int q = 0; q < 8; ++q) {
@@ -219,7 +226,7 @@ cf_gather_kernel(const int32_t* __restrict__ pvtx, const int64_t* __restrict__ p
 template <int LANES, int PREC>
 __global__ void __launch_bounds__(kCfThreads)
 cf_update_kernel(const int64_t* __restrict__ poff, const int64_t* __restrict__ off, int64_t n,
-                 const float* __restrict__ gpart, void* x0, void* x1, float lambda, float step) {
+                 const float* __restrict__ gpart, void* x0, float lambda, float step) {
   constexpr int K = 8 * LANES;
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int64_t ng = ((int64_t)gridDim.x * blockDim.x) / LANES;
@@ -238,10 +245,10 @@ cf_update_kernel(const int64_t* __restrict__ poff, const int64_t* __restrict__ o
     }
     const int64_t deg = off[v + 1] - off[v];
     const float inv = deg > 0 ? 1.0f / (float)deg : 0.0f;
-    load8<PREC>(x0, x1, v, K, d0, x);
+    load8<PREC>(x0, v, K, d0, x);
 #pragma unroll
     for (int q = 0; q < 8; ++q) x[q] = x[q] + step * (g[q] * inv - lambda * x[q]);
-    store8<PREC>(x0, x1, v, K, d0, x);
+    store8<PREC>(x0, v, K, d0, x);
   }
 }
 
@@ -253,7 +260,7 @@ template <int LANES, int PREC>
 __global__ void __launch_bounds__(kCfThreads)
 cf_update_wide_kernel(const int32_t* __restrict__ wide, int32_t nwide,
                       const int64_t* __restrict__ poff, const int64_t* __restrict__ off,
-                      const float* __restrict__ gpart, void* x0, void* x1, float lambda,
+                      const float* __restrict__ gpart, void* x0, float lambda,
                       float step) {
   constexpr int K = 8 * LANES;
   constexpr int GROUPS = kCfThreads / LANES;
@@ -294,17 +301,17 @@ cf_update_wide_kernel(const int32_t* __restrict__ wide, int32_t nwide,
       const int64_t deg = off[v + 1] - off[v];
       const float inv = 1.0f / (float)deg;
       float x[8];
-      load8<PREC>(x0, x1, v, K, d0, x);
+      load8<PREC>(x0, v, K, d0, x);
 #pragma unroll
       for (int q = 0; q < 8; ++q) x[q] = x[q] + step * (red[d0 + q] * inv - lambda * x[q]);
-      store8<PREC>(x0, x1, v, K, d0, x);
+      store8<PREC>(x0, v, K, d0, x);
     }
     __syncthreads();
   }
 }
 
 template <int LANES, int PREC>
-__global__ void cf_encode_kernel(const float* __restrict__ in, int64_t n, void* x0, void* x1) {
+__global__ void cf_encode_kernel(const float* __restrict__ in, int64_t n, void* x0) {
   constexpr int K = 8 * LANES;
   for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n * LANES;
        t += (int64_t)gridDim.x * blockDim.x) {
@@ -313,12 +320,12 @@ __global__ void cf_encode_kernel(const float* __restrict__ in, int64_t n, void* 
     float x[8];
 #pragma unroll
     for (int q = 0; q < 8; ++q) x[q] = in[v * K + d0 + q];
-    store8<PREC>(x0, x1, v, K, d0, x);
+    store8<PREC>(x0, v, K, d0, x);
   }
 }
 
 template <int LANES, int PREC>
-__global__ void cf_decode_kernel(const void* x0, const void* x1, int64_t n,
+__global__ void cf_decode_kernel(const void* x0, int64_t n,
                                  float* __restrict__ out) {
   constexpr int K = 8 * LANES;
   for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n * LANES;
@@ -326,7 +333,7 @@ __global__ void cf_decode_kernel(const void* x0, const void* x1, int64_t n,
     const int64_t v = t / LANES;
     const int d0 = 8 * (int)(t % LANES);
     float x[8];
-    load8<PREC>(x0, x1, v, K, d0, x);
+    load8<PREC>(x0, v, K, d0, x);
 #pragma unroll
     for (int q = 0; q < 8; ++q) out[v * K + d0 + q] = x[q];
   }
@@ -409,19 +416,19 @@ int sweep_side(cg_bipartite* h, int side, double* sse, float lambda, float step,
     }
     if (side == 0)
       cf_gather_kernel<LANES, PREC, true><<<h->gather_grid, kCfThreads, 0, s>>>(
-          h->pvtx[0], h->pbeg[0], off, h->npieces[0], nb, rt, self[0], self[1], other[0],
-          other[1], h->gpart[0], h->partials, h->counter, sse);
+          h->pvtx[0], h->pbeg[0], off, h->npieces[0], nb, rt, self[0], other[0], h->gpart[0],
+          h->partials, h->counter, sse);
     else
       cf_gather_kernel<LANES, PREC, false><<<h->gather_grid, kCfThreads, 0, s>>>(
-          h->pvtx[1], h->pbeg[1], off, h->npieces[1], nb, rt, self[0], self[1], other[0],
-          other[1], h->gpart[1], h->partials, h->counter, nullptr);
+          h->pvtx[1], h->pbeg[1], off, h->npieces[1], nb, rt, self[0], other[0], h->gpart[1],
+          h->partials, h->counter, nullptr);
   } else {
     cf_update_kernel<LANES, PREC><<<grid_for(n * LANES, kCfThreads, 8), kCfThreads, 0, s>>>(
-        h->poff[side], off, n, h->gpart[side], self[0], self[1], lambda, step);
+        h->poff[side], off, n, h->gpart[side], self[0], lambda, step);
     if (h->nwide[side] > 0) {
       CG_LAUNCH_CHECK();
       cf_update_wide_kernel<LANES, PREC><<<h->nwide[side], kCfThreads, 0, s>>>(
-          h->wide[side], h->nwide[side], h->poff[side], off, h->gpart[side], self[0], self[1],
+          h->wide[side], h->nwide[side], h->poff[side], off, h->gpart[side], self[0],
           lambda, step);
     }
   }
@@ -462,16 +469,16 @@ int codec(cg_bipartite* h, const float* P, const float* Q, float* Pout, float* Q
     const int grid = grid_for(n[side] * LANES, 256, 8);
     if (in[side]) {
       switch (h->precision) {
-        case 0: cf_encode_kernel<LANES, 0><<<grid, 256, 0, s>>>(in[side], n[side], st[side][0], st[side][1]); break;
-        case 1: cf_encode_kernel<LANES, 1><<<grid, 256, 0, s>>>(in[side], n[side], st[side][0], st[side][1]); break;
-        default: cf_encode_kernel<LANES, 2><<<grid, 256, 0, s>>>(in[side], n[side], st[side][0], st[side][1]);
+        case 0: cf_encode_kernel<LANES, 0><<<grid, 256, 0, s>>>(in[side], n[side], st[side][0]); break;
+        case 1: cf_encode_kernel<LANES, 1><<<grid, 256, 0, s>>>(in[side], n[side], st[side][0]); break;
+        default: cf_encode_kernel<LANES, 2><<<grid, 256, 0, s>>>(in[side], n[side], st[side][0]);
       }
     }
     if (out[side]) {
       switch (h->precision) {
-        case 0: cf_decode_kernel<LANES, 0><<<grid, 256, 0, s>>>(st[side][0], st[side][1], n[side], out[side]); break;
-        case 1: cf_decode_kernel<LANES, 1><<<grid, 256, 0, s>>>(st[side][0], st[side][1], n[side], out[side]); break;
-        default: cf_decode_kernel<LANES, 2><<<grid, 256, 0, s>>>(st[side][0], st[side][1], n[side], out[side]);
+        case 0: cf_decode_kernel<LANES, 0><<<grid, 256, 0, s>>>(st[side][0], n[side], out[side]); break;
+        case 1: cf_decode_kernel<LANES, 1><<<grid, 256, 0, s>>>(st[side][0], n[side], out[side]); break;
+        default: cf_decode_kernel<LANES, 2><<<grid, 256, 0, s>>>(st[side][0], n[side], out[side]);
       }
     }
     CG_LAUNCH_CHECK();
@@ -661,8 +668,8 @@ int cf_create(int64_t U, int64_t I, int32_t K, int32_t precision, const int64_t*
   int st = build_pieces(h, 0, stream);
   if (st == CG_OK) st = build_pieces(h, 1, stream);
   cudaError_t e = cudaSuccess;
-  const size_t el = precision == 0 ? 4 : 2;
-  const int planes = precision == 2 ? 2 : 1;
+  const size_t el = precision == 1 ? 2 : 4;  // BF16 hi + lo: one 32-bit word per entry
+  const int planes = 1;
   for (int pl = 0; pl < planes && st == CG_OK && e == cudaSuccess; ++pl) {
     e = cudaMalloc(&h->P[pl], el * (size_t)U * K);
     if (e == cudaSuccess) e = cudaMalloc(&h->Q[pl], el * (size_t)I * K);
