@@ -347,6 +347,18 @@ def run_batched(args):
             "per_graph_launches_ms": t_per * 1e3, "speedup_vs_per_graph": t_per / t_batch,
             "max_rel_l1_vs_oracle": max(errs), "oracle_sample_graphs": len(errs),
             "generate_host_s": gen_s}
+    # roofline of one solve of all graphs: the method needs the edges and the
+    # per-vertex arrays from HBM once (a graph's iterations run on chip, its
+    # edges re-read from L2): B_min = 4E + 8(V + G) offsets + 4V degrees + 4V ranks
+    peak, peak_kind = _peaks()
+    bmin = 4 * Etot + 8 * (Vtot + len(gs)) + 8 * Vtot
+    ach = bmin / t_batch / 1e9
+    line["roofline"] = {"bound": "hbm", "kernel": "batch_pagerank_kernel (one solve, 20 iterations)",
+                        "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
+                        "traffic": None, "peak_source": peak_kind, "algorithmic_bytes": bmin,
+                        "note": "iterations 2-20 re-read each graph's edges from L2, so the "
+                                "solve is bound by L2 and latency, not HBM"}
+    line["gpu_launches"] = args.steps
     print(json.dumps(line), flush=True)
 
 
