@@ -141,8 +141,7 @@ seg_gather_kernel(const uint32_t* __restrict__ colf, const typename Op::T* __res
                   const int64_t* __restrict__ seg_cstart, const int32_t* __restrict__ seg_E,
                   const int64_t* __restrict__ seg_chunk, const int32_t* __restrict__ seg_ctile,
                   const int32_t* __restrict__ seg_lo, int k, int32_t ct_begin, int32_t ct_end,
-                  typename Op::T* __restrict__ out, typename Op::T* __restrict__ carry,
-                  int32_t* __restrict__ carry_row) {
+                  typename Op::T* __restrict__ out, typename Op::T* __restrict__ carry) {
   using T = typename Op::T;
   constexpr int WARPS = THREADS / 32;
   constexpr int IPL = 8;
@@ -235,14 +234,9 @@ seg_gather_kernel(const uint32_t* __restrict__ colf, const typename Op::T* __res
     const T P = __shfl_up_sync(0xffffffffu, S, 1);
     if (F > 0) out[row0] = lane > 0 ? Op::op(P, first_val) : first_val;
 
-    // 5. the row open at the chunk's end
-    const int total = __shfl_sync(0xffffffffu, incl, 31);
+    // 5. the row open at the chunk's end (completed by the carry pieces)
     const uint32_t lf = __shfl_sync(0xffffffffu, fl, (n - 1) / IPL);
-    if (lane == 31) {
-      const bool closed = (lf >> ((n - 1) % IPL)) & 1u;
-      carry[c] = closed ? Op::identity() : S;
-      carry_row[c] = closed ? -1 : frow + total;
-    }
+    if (lane == 31 && !((lf >> ((n - 1) % IPL)) & 1u)) carry[c] = S;
   }
 }
 
@@ -352,8 +346,7 @@ __device__ __forceinline__ void staged_chunk(const uint32_t (&pk)[8], uint32_t f
                                              int n, int32_t c, int32_t frow,
                                              const typename Op::T* tab, uint32_t tmax,
                                              typename Op::T* __restrict__ out,
-                                             typename Op::T* __restrict__ carry,
-                                             int32_t* __restrict__ carry_row) {
+                                             typename Op::T* __restrict__ carry) {
   using T = typename Op::T;
   constexpr int IPL = kStagedIPL;
   constexpr int CHUNK = kStagedChunk;
@@ -408,13 +401,9 @@ __device__ __forceinline__ void staged_chunk(const uint32_t (&pk)[8], uint32_t f
   }
   const T P = __shfl_up_sync(0xffffffffu, S, 1);
   if (F > 0) out[row0] = lane > 0 ? Op::op(P, first_val) : first_val;
-  // the row open at the chunk's end
+  // the row open at the chunk's end (completed by the carry pieces)
   const uint32_t lf = __shfl_sync(0xffffffffu, fl, (n - 1) / IPL);
-  if (lane == 31) {
-    const bool closed = (lf >> ((n - 1) % IPL)) & 1u;
-    carry[c] = closed ? Op::identity() : S;
-    carry_row[c] = closed ? -1 : row0 + F;
-  }
+  if (lane == 31 && !((lf >> ((n - 1) % IPL)) & 1u)) carry[c] = S;
 }
 
 // Bulk prefetch of [p, p + bytes) into L2 (TMA; p and bytes 16-byte aligned).
@@ -451,8 +440,7 @@ staged_gather_kernel(const uint8_t* __restrict__ cs, const typename Op::T* __res
                      const int64_t* __restrict__ seg_chunk, const int32_t* __restrict__ seg_ctile,
                      const int32_t* __restrict__ seg_lo, const int32_t* __restrict__ seg_tab,
                      int m, int32_t ct_end, int32_t piece, unsigned* __restrict__ next_piece,
-                     typename Op::T* __restrict__ out, typename Op::T* __restrict__ carry,
-                     int32_t* __restrict__ carry_row) {
+                     typename Op::T* __restrict__ out, typename Op::T* __restrict__ carry) {
   using T = typename Op::T;
   constexpr int WARPS = THREADS / 32;
   constexpr int CHUNK = kStagedChunk;
@@ -504,7 +492,7 @@ staged_gather_kernel(const uint8_t* __restrict__ cs, const typename Op::T* __res
         int32_t frow;
         staged_load(cs, c, pk, fl, pre, frow);
         staged_chunk<Op>(pk, fl, pre, Es - j * CHUNK < CHUNK ? Es - j * CHUNK : CHUNK, c, frow,
-                         tab, tmax, out, carry, carry_row);
+                         tab, tmax, out, carry);
       }
       ++ct;
     }
@@ -631,15 +619,12 @@ int seg_plan_configure(SegPlan* p, int threads, int ctas_per_sm, int tab_vertice
   if (nchunks > p->chunk_cap) {
     cudaFree(p->first_row);
     cudaFree(p->carry);
-    cudaFree(p->carry_row);
     p->first_row = nullptr;
     p->carry = nullptr;
-    p->carry_row = nullptr;
     p->chunk_cap = 0;
     const size_t nc = (size_t)(nchunks > 0 ? nchunks : 1);
     CG_CUDA(cudaMalloc((void**)&p->first_row, sizeof(int32_t) * nc));
     CG_CUDA(cudaMalloc(&p->carry, sizeof(int32_t) * nc));
-    CG_CUDA(cudaMalloc((void**)&p->carry_row, sizeof(int32_t) * nc));
     p->chunk_cap = nchunks;
   }
   const int64_t cs_bytes = chunk[m] * kStagedChunkBytes;
@@ -749,7 +734,6 @@ void seg_plan_free(SegPlan* p) {
   cudaFree(p->seg_tab);
   cudaFree(p->first_row);
   cudaFree(p->carry);
-  cudaFree(p->carry_row);
   cudaFree(p->fx_pieces);
   cudaFree(p->fx_runs);
   cudaFree(p->fx_sum);
@@ -758,7 +742,8 @@ void seg_plan_free(SegPlan* p) {
 }
 
 int64_t seg_plan_bytes(const SegPlan& p) {
-  return 4 * p.colf_len + p.cs_cap + 12 * p.chunk_cap + 72 * (int64_t)p.k;
+  return 4 * p.colf_len + p.cs_cap + 8 * p.chunk_cap + 72 * (int64_t)p.k + 20 * p.fx_npieces +
+         20 * p.fx_nruns;
 }
 
 int seg_plan_export_col(const SegPlan& p, const int32_t* rp, int32_t* col, cudaStream_t s) {
@@ -784,7 +769,7 @@ static int launch_staged(const SegPlan& p, const typename Op::T* x, typename Op:
                                  (int)smem));
   fn<<<p.grid, THREADS, smem, s>>>(p.cs, x, p.first_row, p.seg_E, p.seg_chunk, p.seg_ctile,
                                    p.seg_lo, p.seg_tab, p.m, p.ct_split, p.piece, p.counter, out,
-                                   reinterpret_cast<T*>(p.carry), p.carry_row);
+                                   reinterpret_cast<T*>(p.carry));
   CG_LAUNCH_CHECK();
   return CG_OK;
 }
@@ -805,7 +790,7 @@ int run_seg_gather(const SegPlan& p, const typename Op::T* x, int32_t nx, typena
   if ((phases & kPhaseCached) && p.n_ctiles > p.ct_split) {
     seg_gather_kernel<Op, 1024><<<p.grid_l2, 1024, 0, s>>>(
         p.colf, x, nx, p.first_row, p.seg_cstart, p.seg_E, p.seg_chunk, p.seg_ctile, p.seg_lo,
-        p.k, p.ct_split, (int32_t)p.n_ctiles, out, reinterpret_cast<T*>(p.carry), p.carry_row);
+        p.k, p.ct_split, (int32_t)p.n_ctiles, out, reinterpret_cast<T*>(p.carry));
     CG_LAUNCH_CHECK();
   }
   if ((phases & kPhaseFixup) && p.fx_npieces > 0) {

@@ -50,10 +50,9 @@ struct SegPlan {
   int32_t* seg_tab = nullptr;      // [k]   table entries used for each segment
   int32_t* first_row = nullptr;    // [nchunks] subgraph row of each chunk's first edge
   void* carry = nullptr;           // [nchunks] 4-byte values
-  int32_t* carry_row = nullptr;    // [nchunks]
   int64_t* meta = nullptr;         // [4(k+1)] row_base, edge_base, cstart, bounds (device)
   const int32_t* rp32 = nullptr;   // subgraph row starts (owned by the handle)
-  int64_t chunk_cap = 0;           // capacity of first_row / carry / carry_row
+  int64_t chunk_cap = 0;           // capacity of first_row / carry
   std::vector<int64_t> h_cstart, src_bounds, edge_base, row_base;
   int threads = 1024;       // staged-segment launch shape
   int ctas_per_sm = 1;
