@@ -284,8 +284,8 @@ __device__ __forceinline__ void stage_table(const T* __restrict__ src, int n, T*
 // Staged chunk stream, per 512-edge chunk (1168 bytes):
 //   [0, 1024)     512 uint16 segment-local source indices, lane l's 16 edges
 //                 at bytes [32l, 32l + 32)
-//   [1024, 1088)  32 uint16 row-end masks (bit u: lane l's edge u ends a row)
-//   [1088, 1152)  32 uint16 row ends in lanes before lane l
+//   [1024, 1152)  32 uint32, lane l's: bits 0-15 its row-end mask (bit u:
+//                 edge u ends a row), bits 16-31 the row ends in lanes before l
 //   [1152, 1156)  int32 subgraph row of the chunk's first edge
 constexpr int kStagedIPL = 16;
 constexpr int kStagedChunk = 32 * kStagedIPL;  // 512 edges
@@ -329,8 +329,8 @@ __global__ void staged_fill_kernel(const uint32_t* __restrict__ colf,
     uint4* dst = reinterpret_cast<uint4*>(base + lane * 32);
     dst[0] = make_uint4(packed[0], packed[1], packed[2], packed[3]);
     dst[1] = make_uint4(packed[4], packed[5], packed[6], packed[7]);
-    reinterpret_cast<uint16_t*>(base + 2 * kStagedChunk)[lane] = (uint16_t)fl;
-    reinterpret_cast<uint16_t*>(base + 2 * kStagedChunk + 64)[lane] = (uint16_t)(incl - F);
+    reinterpret_cast<uint32_t*>(base + 2 * kStagedChunk)[lane] =
+        (fl & 0xFFFFu) | ((uint32_t)(incl - F) << 16);
     if (lane == 0) {
       int32_t* tail = reinterpret_cast<int32_t*>(base + 2 * kStagedChunk + 128);
       tail[0] = first_row[c];
@@ -418,8 +418,9 @@ __device__ __forceinline__ void staged_load(const uint8_t* __restrict__ cs, int3
   const uint8_t* base = cs + (int64_t)c * kStagedChunkBytes;
   const uint4 qa = __ldcs(reinterpret_cast<const uint4*>(base + lane * 32));
   const uint4 qb = __ldcs(reinterpret_cast<const uint4*>(base + lane * 32 + 16));
-  fl = __ldcs(reinterpret_cast<const unsigned short*>(base + 2 * kStagedChunk) + lane);
-  pre = __ldcs(reinterpret_cast<const unsigned short*>(base + 2 * kStagedChunk + 64) + lane);
+  const uint32_t w = __ldcs(reinterpret_cast<const unsigned*>(base + 2 * kStagedChunk) + lane);
+  fl = w & 0xFFFFu;
+  pre = (int)(w >> 16);
   frow = __ldcs(reinterpret_cast<const int32_t*>(base + 2 * kStagedChunk + 128));
   pk[0] = qa.x; pk[1] = qa.y; pk[2] = qa.z; pk[3] = qa.w;
   pk[4] = qb.x; pk[5] = qb.y; pk[6] = qb.z; pk[7] = qb.w;
