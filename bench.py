@@ -212,7 +212,7 @@ def run_lp(args):
     gen_s = time.time() - t
     graph = P.Graph(g.offsets, g.src, cluster_mode=0)
     bounds = P.plan_bounds(graph, 1, args.plan or 16.0)
-    lp = P.LabelPropagation(graph, bounds=bounds)
+    lp = P.LabelPropagation(graph, bounds=bounds, overlap=args.overlap)
     for _ in range(args.warmup):
         lp.run(max_passes=2)
     torch.cuda.synchronize()
@@ -677,10 +677,14 @@ def main():
     ap.add_argument("--k", type=int, default=0, help="uniform segments (0: autotune)")
     ap.add_argument("--threads", type=int, default=1024, help="gather threads (with --k)")
     ap.add_argument("--ctas", type=int, default=1, help="gather blocks per SM (with --k)")
-    ap.add_argument("--table", type=int, default=0, help="shared table entries (with --k)")
+    ap.add_argument("--table", type=int, default=0,
+                    help="shared table entries (with --k; with --plan, > 0 caps the table)")
     ap.add_argument("--plan", type=float, default=0.0,
                     help="use planned bounds with this min_avg_degree (skips the autotuner)")
     ap.add_argument("--merge-block", type=int, default=512)
+    ap.add_argument("--overlap", type=int, default=0,
+                    help="warps per block serving the L1/L2 segments inside the staged launch "
+                         "(with --plan; the autotuner tries its own)")
     ap.add_argument("--sweep", action="store_true", help="k = 1..64 sweep table")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default="pagerank", choices=["pagerank", "lp", "batched", "ppr", "cf"],
@@ -725,7 +729,7 @@ def main():
 
     if args.plan:
         best = {"kind": "plan", "threads": args.threads, "ctas": args.ctas,
-                "min_avg_degree": args.plan, "table": -1}
+                "min_avg_degree": args.plan, "table": args.table or -1, "overlap": args.overlap}
         table = []
     elif args.k:
         best = {"kind": "uniform", "k": args.k, "threads": args.threads, "ctas": args.ctas,

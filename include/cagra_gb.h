@@ -135,6 +135,8 @@ typedef struct {
   int32_t gather_threads; /* threads per staged-gather block */
   int32_t staged_segments; /* leading segments served from shared memory */
   int64_t staged_edges;  /* edges of those segments */
+  int32_t gather_overlap; /* warps per block serving the L1/L2 segments inside the
+                             staged launch (0: a launch of their own) */
 } cg_segmented_info;
 
 /*
@@ -191,6 +193,22 @@ int pr_plan_bounds(const int32_t *dev_outdeg, int32_t V, int32_t smem_vertices,
  */
 int pr_set_gather_config(cg_segmented *seg, int32_t threads, int32_t ctas_per_sm,
                          int32_t table_vertices, cudaStream_t stream);
+
+/*
+ * Overlap of the two kinds of segment processing (Algorithm 3) inside one
+ * launch.  cached_warps > 0: one 1024-thread block per SM; warps
+ * [0, 32 - cached_warps) of each block work through the staged segments
+ * (shared-memory tables), the other cached_warps warps through the L1/L2
+ * segments from a chunk queue, and the staged warps join that queue when
+ * their own work runs out, so the cold segments' random L2 reads proceed
+ * while the staged warps read shared memory.  0 (the default): the staged and
+ * the L1/L2 segments get a launch each.  cached_warps in [0, 24]; needs the
+ * 1024-thread, 1-block-per-SM shape (pr_set_gather_config) and takes effect
+ * while the plan has both kinds of segment.  The row sums do not depend on it
+ * (each chunk is summed the same way whichever warp takes it).
+ * pr_set_gather_config keeps the setting.  Synchronizes the stream.
+ */
+int pr_set_gather_overlap(cg_segmented *seg, int32_t cached_warps, cudaStream_t stream);
 
 /* Shared-table capacity (entries) of the gather at ctas_per_sm blocks/SM. */
 int pr_gather_table_capacity(int32_t ctas_per_sm);

@@ -27,7 +27,7 @@ EXPORTS = [
     "cg_out_degree", "cg_inv_outdeg", "cg_cluster", "cg_relabel_csr", "cg_permute4",
     "cg_permute_rows",
     "pr_build_segments", "cg_segmented_get_info", "pr_plan_bounds", "pr_set_gather_config",
-    "pr_gather_table_capacity", "cg_segmented_export",
+    "pr_gather_table_capacity", "pr_set_gather_overlap", "cg_segmented_export",
     "cg_segmented_destroy", "cg_seg_gather", "cg_seg_gather_phases", "merge",
     "pr_init", "pr_contrib", "pr_iterate", "pr_merge_update", "pr_plain_create", "pr_plain_destroy", "pr_iterate_plain",
     "pr_iterate_plain_noalloc", "pr_noalloc_limits",
@@ -52,7 +52,7 @@ class SegInfo(ctypes.Structure):
                 ("device_bytes", ctypes.c_int64), ("gather_tiles", ctypes.c_int64),
                 ("table_vertices", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32),
                 ("gather_threads", ctypes.c_int32), ("staged_segments", ctypes.c_int32),
-                ("staged_edges", ctypes.c_int64)]
+                ("staged_edges", ctypes.c_int64), ("gather_overlap", ctypes.c_int32)]
 
 
 def load(path: str | None = None):
@@ -83,6 +83,7 @@ def load(path: str | None = None):
             "pr_plan_bounds": (ctypes.c_int, [vp, i32, i32, dbl, i32, i32, vp, vp, vp]),
             "pr_set_gather_config": (ctypes.c_int, [vp, i32, i32, i32, vp]),
             "pr_gather_table_capacity": (ctypes.c_int, [i32]),
+            "pr_set_gather_overlap": (ctypes.c_int, [vp, i32, vp]),
             "cg_segmented_export": (ctypes.c_int, [vp, vp, vp, vp, vp, vp, vp, vp, vp]),
             "cg_segmented_destroy": (ctypes.c_int, [vp]),
             "cg_seg_gather": (ctypes.c_int, [vp, i32, vp, vp, vp]),
@@ -263,6 +264,11 @@ def pr_set_gather_config(seg: Segmented, threads: int = 1024, ctas_per_sm: int =
                          table_vertices: int = -1, stream=None):
     _check(load().pr_set_gather_config(seg.handle, threads, ctas_per_sm, table_vertices,
                                        _stream(stream)), "pr_set_gather_config")
+
+
+def pr_set_gather_overlap(seg: Segmented, cached_warps: int, stream=None):
+    _check(load().pr_set_gather_overlap(seg.handle, cached_warps, _stream(stream)),
+           "pr_set_gather_overlap")
 
 
 def pr_gather_table_capacity(ctas_per_sm: int = 1) -> int:

@@ -20,9 +20,6 @@
 namespace cg {
 namespace {
 
-
-
-
 // Cache-aware merge (Algorithm 4) fused with the vertex update.
 __global__ void __launch_bounds__(kMergeWarps * 32, 6)
 merge_update_kernel(const int32_t* __restrict__ blk, const int32_t* __restrict__ idx_map,

@@ -130,10 +130,89 @@ __global__ void first_row_kernel(const int32_t* __restrict__ rp,
   }
 }
 
+// One L1/L2 chunk: 256 edges of segment-local chunk j (global chunk c) of a
+// segment whose sources start at lo; lane l holds edges [8l, 8l + 8).
+constexpr int kCachedIPL = 8;
+constexpr int kCachedChunk = 32 * kCachedIPL;  // 256 edges
+
+template <class Op>
+__device__ __forceinline__ void cached_chunk(const uint32_t* __restrict__ colf,
+                                             const typename Op::T* __restrict__ x, int32_t nx,
+                                             int32_t lo, int32_t Es, int32_t cstart, int32_t j,
+                                             int32_t c, int32_t frow,
+                                             typename Op::T* __restrict__ out,
+                                             typename Op::T* __restrict__ carry) {
+  using T = typename Op::T;
+  constexpr int IPL = kCachedIPL;
+  constexpr int CHUNK = kCachedChunk;
+  const int lane = threadIdx.x & 31;
+  const int32_t e0 = j * CHUNK;
+  const int n = Es - e0 < CHUNK ? Es - e0 : CHUNK;
+
+  // 1. this lane's 8 edges (two 16-byte streaming loads; colf is padded)
+  const uint4* p = reinterpret_cast<const uint4*>(colf + cstart + e0 + lane * IPL);
+  const uint4 qa = __ldcs(p), qb = __ldcs(p + 1);
+  const uint32_t cf[8] = {qa.x, qa.y, qa.z, qa.w, qb.x, qb.y, qb.z, qb.w};
+  T v[IPL];
+  uint32_t fl = 0;
+  const int nl = n - lane * IPL;  // valid edges of this lane
+#pragma unroll
+  for (int u = 0; u < IPL; ++u) {
+    const bool ok = u < nl;
+    const int32_t src = lo + (int32_t)(cf[u] & ~kRowEndFlag);
+    if (ok) fl |= (cf[u] >> 31) << u;
+    v[u] = (ok && (uint32_t)src < (uint32_t)nx) ? __ldg(x + src) : Op::identity();
+  }
+
+  // 2. rows ended before this lane (exclusive warp prefix of flag counts)
+  const int F = __popc(fl);
+  int incl = F;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int y = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += y;
+  }
+  const int32_t row0 = frow + (incl - F);
+
+  // 3. sequential fold; rows that start and end in this lane are final
+  T acc = Op::identity(), first_val = Op::identity();
+  int nf = 0;
+#pragma unroll
+  for (int u = 0; u < IPL; ++u) {
+    acc = Op::op(acc, v[u]);
+    if (fl & (1u << u)) {
+      if (nf == 0)
+        first_val = acc;
+      else
+        out[row0 + nf] = acc;
+      ++nf;
+      acc = Op::identity();
+    }
+  }
+
+  // 4. segmented scan of the open-row parts; completes each lane's first row
+  T S = acc;
+  int h = F > 0;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const T y = __shfl_up_sync(0xffffffffu, S, o);
+    const int g = __shfl_up_sync(0xffffffffu, h, o);
+    if (lane >= o) {
+      if (!h) S = Op::op(y, S);
+      h |= g;
+    }
+  }
+  const T P = __shfl_up_sync(0xffffffffu, S, 1);
+  if (F > 0) out[row0] = lane > 0 ? Op::op(P, first_val) : first_val;
+
+  // 5. the row open at the chunk's end (completed by the carry pieces)
+  const uint32_t lf = __shfl_sync(0xffffffffu, fl, (n - 1) / IPL);
+  if (lane == 31 && !((lf >> ((n - 1) % IPL)) & 1u)) carry[c] = S;
+}
+
 // The L1/L2 launch: every read of a segment in [ct_begin, ct_end) goes
 // through L1/L2.  Blocks take block-groups round-robin (the grid sweeps the
 // groups in order, which balances blocks when the cost per group varies).
-// A warp's chunk is 256 edges; lane l holds edges [8l, 8l + 8).
 template <class Op, int THREADS>
 __global__ void __launch_bounds__(THREADS, 2048 / THREADS)
 seg_gather_kernel(const uint32_t* __restrict__ colf, const typename Op::T* __restrict__ x,
@@ -142,11 +221,8 @@ seg_gather_kernel(const uint32_t* __restrict__ colf, const typename Op::T* __res
                   const int64_t* __restrict__ seg_chunk, const int32_t* __restrict__ seg_ctile,
                   const int32_t* __restrict__ seg_lo, int k, int32_t ct_begin, int32_t ct_end,
                   typename Op::T* __restrict__ out, typename Op::T* __restrict__ carry) {
-  using T = typename Op::T;
   constexpr int WARPS = THREADS / 32;
-  constexpr int IPL = 8;
-  constexpr int CHUNK = 32 * IPL;
-  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  const int w = threadIdx.x >> 5;
   const int32_t my_lo = ct_begin + (int32_t)blockIdx.x;
   const int32_t step = (int32_t)gridDim.x;
   if (my_lo >= ct_end) return;
@@ -172,109 +248,49 @@ seg_gather_kernel(const uint32_t* __restrict__ colf, const typename Op::T* __res
       ctnext = seg_ctile[s + 1];
     }
     const int32_t j = (ct - ctbase) * WARPS + w;  // chunk of this warp within the segment
-    const int32_t e0 = j * CHUNK;
-    if (e0 >= Es) continue;  // warp-uniform
-    const int n = Es - e0 < CHUNK ? Es - e0 : CHUNK;
-    const int32_t c = cbase + j;
-    const int32_t frow = first_row[c];
-
-    // 1. this lane's 8 edges (two 16-byte streaming loads; colf is padded)
-    const uint4* p = reinterpret_cast<const uint4*>(colf + cstart + e0 + lane * IPL);
-    const uint4 qa = __ldcs(p), qb = __ldcs(p + 1);
-    const uint32_t cf[8] = {qa.x, qa.y, qa.z, qa.w, qb.x, qb.y, qb.z, qb.w};
-    T v[IPL];
-    uint32_t fl = 0;
-    const int nl = n - lane * IPL;  // valid edges of this lane
-#pragma unroll
-    for (int u = 0; u < IPL; ++u) {
-      const bool ok = u < nl;
-      const int32_t src = lo + (int32_t)(cf[u] & ~kRowEndFlag);
-      if (ok) fl |= (cf[u] >> 31) << u;
-      v[u] = (ok && (uint32_t)src < (uint32_t)nx) ? __ldg(x + src) : Op::identity();
-    }
-
-    // 2. rows ended before this lane (exclusive warp prefix of flag counts)
-    const int F = __popc(fl);
-    int incl = F;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const int y = __shfl_up_sync(0xffffffffu, incl, o);
-      if (lane >= o) incl += y;
-    }
-    const int32_t row0 = frow + (incl - F);
-
-    // 3. sequential fold; rows that start and end in this lane are final
-    T acc = Op::identity(), first_val = Op::identity();
-    int nf = 0;
-#pragma unroll
-    for (int u = 0; u < IPL; ++u) {
-      acc = Op::op(acc, v[u]);
-      if (fl & (1u << u)) {
-        if (nf == 0)
-          first_val = acc;
-        else
-          out[row0 + nf] = acc;
-        ++nf;
-        acc = Op::identity();
-      }
-    }
-
-    // 4. segmented scan of the open-row parts; completes each lane's first row
-    T S = acc;
-    int h = F > 0;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const T y = __shfl_up_sync(0xffffffffu, S, o);
-      const int g = __shfl_up_sync(0xffffffffu, h, o);
-      if (lane >= o) {
-        if (!h) S = Op::op(y, S);
-        h |= g;
-      }
-    }
-    const T P = __shfl_up_sync(0xffffffffu, S, 1);
-    if (F > 0) out[row0] = lane > 0 ? Op::op(P, first_val) : first_val;
-
-    // 5. the row open at the chunk's end (completed by the carry pieces)
-    const uint32_t lf = __shfl_sync(0xffffffffu, fl, (n - 1) / IPL);
-    if (lane == 31 && !((lf >> ((n - 1) % IPL)) & 1u)) carry[c] = S;
+    if (j * kCachedChunk >= Es) continue;         // warp-uniform
+    cached_chunk<Op>(colf, x, nx, lo, Es, cstart, j, cbase + j, first_row[cbase + j], out,
+                     carry);
   }
 }
 
 // Copy n values into shared memory with many independent loads in flight per
 // thread (16-byte loads when the source is 16-byte aligned), so staging a
 // table costs a few memory round trips rather than one per element.
-template <typename T, int THREADS>
-__device__ __forceinline__ void stage_table(const T* __restrict__ src, int n, T* dst, int tid) {
+// nt: threads taking part (tid in [0, nt)).
+template <typename T>
+__device__ __forceinline__ void stage_table(const T* __restrict__ src, int n, T* dst, int tid,
+                                            int nt) {
   static_assert(sizeof(T) == 4, "4-byte values");
   if ((reinterpret_cast<uintptr_t>(src) & 15) == 0) {
     const int n4 = n >> 2;
     const uint4* s4 = reinterpret_cast<const uint4*>(src);
     uint4* d4 = reinterpret_cast<uint4*>(dst);
-    for (int b = 0; b < n4; b += THREADS * 4) {
+    for (int b = 0; b < n4; b += nt * 4) {
       uint4 r[4];
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
-        const int i = b + u * THREADS + tid;
+        const int i = b + u * nt + tid;
         if (i < n4) r[u] = __ldg(s4 + i);
       }
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
-        const int i = b + u * THREADS + tid;
+        const int i = b + u * nt + tid;
         if (i < n4) d4[i] = r[u];
       }
     }
-    for (int i = (n4 << 2) + tid; i < n; i += THREADS) dst[i] = src[i];
+    for (int i = (n4 << 2) + tid; i < n; i += nt) dst[i] = src[i];
   } else {
-    for (int b = 0; b < n; b += THREADS * 8) {
+    for (int b = 0; b < n; b += nt * 8) {
       T r[8];
 #pragma unroll
       for (int u = 0; u < 8; ++u) {
-        const int i = b + u * THREADS + tid;
+        const int i = b + u * nt + tid;
         if (i < n) r[u] = __ldg(src + i);
       }
 #pragma unroll
       for (int u = 0; u < 8; ++u) {
-        const int i = b + u * THREADS + tid;
+        const int i = b + u * nt + tid;
         if (i < n) dst[i] = r[u];
       }
     }
@@ -426,35 +442,42 @@ __device__ __forceinline__ void staged_load(const uint8_t* __restrict__ cs, int3
   pk[4] = qb.x; pk[5] = qb.y; pk[6] = qb.z; pk[7] = qb.w;
 }
 
-// The staged launch: segments [0, m) are read from a shared-memory copy of
-// their source values.  Work pieces of consecutive block-groups (at most
-// `piece`, shrinking towards the end) are handed out in increasing order by
-// an atomic counter of block-groups: a block's groups only move forward (so
-// it stages each segment's table at most once) and a slow block simply
-// takes fewer pieces.  A warp's chunk is 512 edges of the
-// compressed stream (lane l holds 16); while it works on one chunk the TMA
-// unit prefetches its next one into L2.
-template <class Op, int THREADS>
-__global__ void __launch_bounds__(THREADS, 1024 / THREADS)
-staged_gather_kernel(const uint8_t* __restrict__ cs, const typename Op::T* __restrict__ x,
-                     const int32_t* __restrict__ first_row, const int32_t* __restrict__ seg_E,
-                     const int64_t* __restrict__ seg_chunk, const int32_t* __restrict__ seg_ctile,
-                     const int32_t* __restrict__ seg_lo, const int32_t* __restrict__ seg_tab,
-                     int m, int32_t ct_end, int32_t piece, unsigned* __restrict__ next_piece,
-                     typename Op::T* __restrict__ out, typename Op::T* __restrict__ carry) {
+// Barrier among threads [0, nt) of the block: the whole block, or named
+// barrier 1 when only the staged warps of an overlapped launch take part.
+__device__ __forceinline__ void group_sync(int nt) {
+  if (nt == (int)blockDim.x)
+    __syncthreads();
+  else
+    asm volatile("bar.sync 1, %0;" ::"r"(nt) : "memory");
+}
+
+// The staged schedule, run by threads [0, nt) of a block: segments [0, m)
+// are read from a shared-memory copy of their source values.  Work pieces
+// of consecutive block-groups (nt/32 chunks each; at most `piece`, shrinking
+// towards the end) are handed out in increasing order by an atomic counter
+// of block-groups: a block's groups only move forward (so it stages each
+// segment's table at most once) and a slow block simply takes fewer pieces.
+// A warp's chunk is 512 edges of the compressed stream (lane l holds 16);
+// while it works on one chunk the TMA unit prefetches its next one into L2.
+template <class Op>
+__device__ __forceinline__ void staged_pieces(
+    const uint8_t* __restrict__ cs, const typename Op::T* __restrict__ x,
+    const int32_t* __restrict__ seg_E, const int64_t* __restrict__ seg_chunk,
+    const int32_t* __restrict__ seg_ctile, const int32_t* __restrict__ seg_lo,
+    const int32_t* __restrict__ seg_tab, int32_t ct_end, int32_t piece,
+    unsigned* __restrict__ next_piece, typename Op::T* __restrict__ out,
+    typename Op::T* __restrict__ carry, typename Op::T* tab, int nt, int32_t* s_piece,
+    int32_t* s_size) {
   using T = typename Op::T;
-  constexpr int WARPS = THREADS / 32;
   constexpr int CHUNK = kStagedChunk;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  __shared__ int32_t s_piece, s_size;
-  T* tab = reinterpret_cast<T*>(smem_raw);
+  const int warps = nt >> 5;
   const int tid = threadIdx.x, w = tid >> 5;
   int s = 0;
   int32_t Es = 0, cbase = 0, ctbase = 0, ctnext = -1;
   uint32_t tmax = 0;
 
   for (;;) {
-    __syncthreads();  // everyone is done with the previous piece's s_piece
+    group_sync(nt);  // everyone is done with the previous piece's s_piece
     if (tid == 0) {
       // guided self-scheduling: a piece is the remaining block-groups over
       // twice the grid, at most `piece` and at least one, so the last
@@ -462,15 +485,15 @@ staged_gather_kernel(const uint8_t* __restrict__ cs, const typename Op::T* __res
       const int32_t cur = (int32_t)*(volatile unsigned*)next_piece;
       int32_t sz = (ct_end - cur) / (2 * (int32_t)gridDim.x);
       sz = sz < 1 ? 1 : (sz > piece ? piece : sz);
-      s_piece = (int32_t)atomicAdd(next_piece, (unsigned)sz);
-      s_size = sz;
+      *s_piece = (int32_t)atomicAdd(next_piece, (unsigned)sz);
+      *s_size = sz;
     }
-    __syncthreads();
-    const int32_t my_lo = s_piece;
+    group_sync(nt);
+    const int32_t my_lo = *s_piece;
     if (my_lo >= ct_end) break;
-    const int32_t my_hi = my_lo + s_size < ct_end ? my_lo + s_size : ct_end;
+    const int32_t my_hi = my_lo + *s_size < ct_end ? my_lo + *s_size : ct_end;
     for (int32_t ct = my_lo; ct < my_hi;) {
-      if (ct >= ctnext) {  // a new segment (uniform across the block)
+      if (ct >= ctnext) {  // a new segment (uniform across the group)
         while (ct >= seg_ctile[s + 1]) ++s;
         Es = seg_E[s];
         cbase = (int32_t)seg_chunk[s];
@@ -478,16 +501,16 @@ staged_gather_kernel(const uint8_t* __restrict__ cs, const typename Op::T* __res
         ctnext = seg_ctile[s + 1];
         const int32_t lo = seg_lo[s], tn = seg_tab[s];
         tmax = tn > 0 ? (uint32_t)(tn - 1) : 0u;
-        __syncthreads();  // every warp is done reading the previous table
-        stage_table<T, THREADS>(x + lo, tn, tab, tid);
-        __syncthreads();
+        group_sync(nt);  // every warp is done reading the previous table
+        stage_table<T>(x + lo, tn, tab, tid, nt);
+        group_sync(nt);
       }
-      const int32_t j = (ct - ctbase) * WARPS + w;
+      const int32_t j = (ct - ctbase) * warps + w;
       if (j * CHUNK < Es) {  // warp-uniform
         const int32_t c = cbase + j;
         // ask the TMA unit to pull this warp's next chunk into L2 meanwhile
-        if ((threadIdx.x & 31) == 0 && ct + 1 < my_hi && (j + WARPS) * CHUNK < Es)
-          prefetch_l2(cs + (int64_t)(c + WARPS) * kStagedChunkBytes, kStagedChunkBytes);
+        if ((threadIdx.x & 31) == 0 && ct + 1 < my_hi && (j + warps) * CHUNK < Es)
+          prefetch_l2(cs + (int64_t)(c + warps) * kStagedChunkBytes, kStagedChunkBytes);
         uint32_t pk[8], fl;
         int pre;
         int32_t frow;
@@ -498,6 +521,95 @@ staged_gather_kernel(const uint8_t* __restrict__ cs, const typename Op::T* __res
       ++ct;
     }
   }
+}
+
+// The staged launch: every thread of the block runs the staged schedule.
+template <class Op, int THREADS>
+__global__ void __launch_bounds__(THREADS, 1024 / THREADS)
+staged_gather_kernel(const uint8_t* __restrict__ cs, const typename Op::T* __restrict__ x,
+                     const int32_t* __restrict__ seg_E, const int64_t* __restrict__ seg_chunk,
+                     const int32_t* __restrict__ seg_ctile, const int32_t* __restrict__ seg_lo,
+                     const int32_t* __restrict__ seg_tab, int32_t ct_end, int32_t piece,
+                     unsigned* __restrict__ next_piece, typename Op::T* __restrict__ out,
+                     typename Op::T* __restrict__ carry) {
+  using T = typename Op::T;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ int32_t s_piece, s_size;
+  staged_pieces<Op>(cs, x, seg_E, seg_chunk, seg_ctile, seg_lo, seg_tab, ct_end, piece,
+                    next_piece, out, carry, reinterpret_cast<T*>(smem_raw), THREADS, &s_piece,
+                    &s_size);
+}
+
+// L1/L2 chunks of segments [m, k) taken from a queue (a global counter of
+// chunks, kCachedGrab at a time): a warp's successive grabs only move forward,
+// so its segment is found by stepping.  The grab's chunks are prefetched into
+// L2 (TMA) when it is taken.
+constexpr int kCachedGrab = 4;
+
+template <class Op>
+__device__ __forceinline__ void cached_queue(
+    const uint32_t* __restrict__ colf, const typename Op::T* __restrict__ x, int32_t nx,
+    const int32_t* __restrict__ first_row, const int64_t* __restrict__ seg_cstart,
+    const int32_t* __restrict__ seg_E, const int64_t* __restrict__ seg_chunk,
+    const int32_t* __restrict__ seg_lo, int m, int k, unsigned* __restrict__ next_chunk,
+    typename Op::T* __restrict__ out, typename Op::T* __restrict__ carry) {
+  const int lane = threadIdx.x & 31;
+  const int32_t c_begin = (int32_t)seg_chunk[m], c_end = (int32_t)seg_chunk[k];
+  int s = m;
+  int32_t lo = 0, Es = 0, cstart = 0, cbase = 0, cnext = -1;
+  for (;;) {
+    int32_t c0 = 0;
+    if (lane == 0) c0 = (int32_t)atomicAdd(next_chunk, (unsigned)kCachedGrab);
+    c0 = __shfl_sync(0xffffffffu, c0, 0) + c_begin;
+    if (c0 >= c_end) break;
+    const int32_t c1 = c0 + kCachedGrab < c_end ? c0 + kCachedGrab : c_end;
+    if (lane < c1 - c0) {  // lane u prefetches chunk c0 + u (1 KB of colf)
+      const int32_t cu = c0 + lane;
+      int su = s;
+      while (cu >= (int32_t)seg_chunk[su + 1]) ++su;
+      prefetch_l2(colf + seg_cstart[su] + (int64_t)(cu - (int32_t)seg_chunk[su]) * kCachedChunk,
+                  kCachedChunk * 4);
+    }
+    for (int32_t c = c0; c < c1; ++c) {
+      if (c >= cnext) {
+        while (c >= (int32_t)seg_chunk[s + 1]) ++s;
+        lo = seg_lo[s];
+        Es = seg_E[s];
+        cstart = (int32_t)seg_cstart[s];
+        cbase = (int32_t)seg_chunk[s];
+        cnext = (int32_t)seg_chunk[s + 1];
+      }
+      cached_chunk<Op>(colf, x, nx, lo, Es, cstart, c - cbase, c, first_row[c], out, carry);
+    }
+  }
+}
+
+// Both kinds in one launch (one 1024-thread block per SM): threads
+// [0, staged_threads) run the staged schedule (named barrier 1 among them),
+// the other warps serve the L1/L2 segments from the chunk queue from the
+// start, and the staged warps join that queue when their pieces run out.
+// The cold segments' random reads go to L2 while the staged warps read
+// shared memory, so the two kinds of lookup proceed side by side.
+template <class Op>
+__global__ void __launch_bounds__(1024, 1)
+overlap_gather_kernel(const uint8_t* __restrict__ cs, const uint32_t* __restrict__ colf,
+                      const typename Op::T* __restrict__ x, int32_t nx,
+                      const int32_t* __restrict__ first_row,
+                      const int64_t* __restrict__ seg_cstart, const int32_t* __restrict__ seg_E,
+                      const int64_t* __restrict__ seg_chunk,
+                      const int32_t* __restrict__ seg_ctile, const int32_t* __restrict__ seg_lo,
+                      const int32_t* __restrict__ seg_tab, int m, int k, int32_t ct_end,
+                      int32_t piece, int staged_threads, unsigned* __restrict__ counters,
+                      typename Op::T* __restrict__ out, typename Op::T* __restrict__ carry) {
+  using T = typename Op::T;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ int32_t s_piece, s_size;
+  if ((int)threadIdx.x < staged_threads)
+    staged_pieces<Op>(cs, x, seg_E, seg_chunk, seg_ctile, seg_lo, seg_tab, ct_end, piece,
+                      counters, out, carry, reinterpret_cast<T*>(smem_raw), staged_threads,
+                      &s_piece, &s_size);
+  cached_queue<Op>(colf, x, nx, first_row, seg_cstart, seg_E, seg_chunk, seg_lo, m, k,
+                   counters + 1, out, carry);
 }
 
 }  // namespace
@@ -605,8 +717,17 @@ int seg_plan_configure(SegPlan* p, int threads, int ctas_per_sm, int tab_vertice
     tabmax = std::max(tabmax, size);
     ++m;
   }
-  const int chunk_a = kStagedChunk, chunk_b = 256;
-  const int warps_a = threads / 32, warps_b = 1024 / 32;
+  // one overlapped launch needs both kinds of segment and the 1024 x 1 shape
+  bool cached_edges = false;
+  for (int q = m; q < k; ++q) cached_edges |= p->edge_base[q + 1] > p->edge_base[q];
+  if (p->overlap_request > 0 && (threads != 1024 || ctas_per_sm != 1)) {
+    set_error("gather overlap needs 1024 threads and 1 block per SM (got %d x %d)", threads,
+              ctas_per_sm);
+    return CG_ERR_INVALID_ARG;
+  }
+  p->overlap = (m > 0 && cached_edges) ? p->overlap_request : 0;
+  const int chunk_a = kStagedChunk, chunk_b = kCachedChunk;
+  const int warps_a = p->overlap > 0 ? 32 - p->overlap : threads / 32, warps_b = 1024 / 32;
   std::vector<int64_t> chunk(k + 1, 0);
   std::vector<int32_t> ctile(k + 1, 0), tn(k > 0 ? k : 1, 0);
   for (int q = 0; q < k; ++q) {
@@ -714,9 +835,10 @@ int seg_plan_configure(SegPlan* p, int threads, int ctas_per_sm, int tab_vertice
   p->n_ctiles = ctile[k];
   p->grid = (int)std::max<int64_t>(
       1, std::min<int64_t>(p->ct_split, (int64_t)di.sm_count * ctas_per_sm));
+  if (p->overlap > 0) p->grid = di.sm_count;  // every SM serves the L1/L2 queue too
   // about eight pieces per block: balance without many table reloads
   p->piece = (int32_t)std::max<int64_t>(1, ceil_div(p->ct_split, 8LL * p->grid));
-  if (!p->counter) CG_CUDA(cudaMalloc((void**)&p->counter, sizeof(unsigned)));
+  if (!p->counter) CG_CUDA(cudaMalloc((void**)&p->counter, 2 * sizeof(unsigned)));
   p->grid_l2 = (int)std::max<int64_t>(
       1, std::min<int64_t>(p->n_ctiles - p->ct_split, (int64_t)di.sm_count * 2));
   return CG_OK;
@@ -768,9 +890,27 @@ static int launch_staged(const SegPlan& p, const typename Op::T* x, typename Op:
   if (smem > 48 * 1024)
     CG_CUDA(cudaFuncSetAttribute((const void*)fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)smem));
-  fn<<<p.grid, THREADS, smem, s>>>(p.cs, x, p.first_row, p.seg_E, p.seg_chunk, p.seg_ctile,
-                                   p.seg_lo, p.seg_tab, p.m, p.ct_split, p.piece, p.counter, out,
+  fn<<<p.grid, THREADS, smem, s>>>(p.cs, x, p.seg_E, p.seg_chunk, p.seg_ctile, p.seg_lo,
+                                   p.seg_tab, p.ct_split, p.piece, p.counter, out,
                                    reinterpret_cast<T*>(p.carry));
+  CG_LAUNCH_CHECK();
+  return CG_OK;
+}
+
+template <class Op>
+static int launch_overlap(const SegPlan& p, const typename Op::T* x, int32_t nx,
+                          typename Op::T* out, cudaStream_t s) {
+  using T = typename Op::T;
+  const size_t smem = (size_t)p.tab_cap * sizeof(T);
+  auto fn = overlap_gather_kernel<Op>;
+  CG_CUDA(cudaMemsetAsync(p.counter, 0, 2 * sizeof(unsigned), s));
+  if (smem > 48 * 1024)
+    CG_CUDA(cudaFuncSetAttribute((const void*)fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)smem));
+  fn<<<p.grid, 1024, smem, s>>>(p.cs, p.colf, x, nx, p.first_row, p.seg_cstart, p.seg_E,
+                                p.seg_chunk, p.seg_ctile, p.seg_lo, p.seg_tab, p.m, p.k,
+                                p.ct_split, p.piece, 1024 - 32 * p.overlap, p.counter, out,
+                                reinterpret_cast<T*>(p.carry));
   CG_LAUNCH_CHECK();
   return CG_OK;
 }
@@ -780,6 +920,10 @@ int run_seg_gather(const SegPlan& p, const typename Op::T* x, int32_t nx, typena
                    cudaStream_t s, int phases) {
   if (p.nchunks == 0) return CG_OK;
   using T = typename Op::T;
+  if (p.overlap > 0) {  // both kinds in one launch, counted as the staged phase
+    if (phases & kPhaseStaged) CG_TRY((launch_overlap<Op>(p, x, nx, out, s)));
+    phases &= ~(kPhaseStaged | kPhaseCached);
+  }
   // staged segments [0, m): read from a shared-memory copy
   if ((phases & kPhaseStaged) && p.m > 0 && p.ct_split > 0) {
     if (p.threads == 1024)

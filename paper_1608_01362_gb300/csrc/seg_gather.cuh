@@ -64,7 +64,9 @@ struct SegPlan {
   int64_t n_ctiles = 0;
   int grid = 0;             // staged launch blocks
   int32_t piece = 1;        // block-groups per work piece of the staged launch
-  unsigned* counter = nullptr;  // next staged work piece
+  unsigned* counter = nullptr;  // [2] next staged work piece, next L1/L2 chunk (overlap)
+  int overlap_request = 0;  // warps per block given to the L1/L2 segments (0: two launches)
+  int overlap = 0;          // the same, in effect (0 when one kind of segment is absent)
   int grid_l2 = 0;          // unstaged launch blocks (1024 threads, 2 per SM)
   // rows spanning chunks: runs of carries (a static structure) cut into
   // pieces of <= 32 chunks, completed in parallel (see run_seg_gather)

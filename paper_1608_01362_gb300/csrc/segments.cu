@@ -501,6 +501,7 @@ int cg_segmented_get_info(const cg_segmented* g, cg_segmented_info* info) {
   info->staged_edges = g->plan.m > 0 ? g->edge_base[g->plan.m] : 0;
   info->ctas_per_sm = g->plan.ctas_per_sm;
   info->gather_threads = g->plan.threads;
+  info->gather_overlap = g->plan.overlap;
   return CG_OK;
 }
 
@@ -509,6 +510,22 @@ int pr_set_gather_config(cg_segmented* g, int32_t threads, int32_t ctas_per_sm,
   CG_ARG(g != nullptr, "pr_set_gather_config: null handle");
   CG_ARG(table_vertices >= -1, "pr_set_gather_config: table_vertices must be >= -1");
   return seg_plan_configure(&g->plan, threads, ctas_per_sm, table_vertices, stream);
+}
+
+int pr_set_gather_overlap(cg_segmented* g, int32_t cached_warps, cudaStream_t stream) {
+  CG_ARG(g != nullptr, "pr_set_gather_overlap: null handle");
+  CG_ARG(cached_warps >= 0 && cached_warps <= 24,
+         "pr_set_gather_overlap: cached_warps must be in [0, 24] (got %d)", cached_warps);
+  const int before = g->plan.overlap_request;
+  g->plan.overlap_request = cached_warps;
+  const int rc = seg_plan_configure(&g->plan, g->plan.threads, g->plan.ctas_per_sm,
+                                    g->plan.table_request, stream);
+  if (rc != CG_OK) {  // keep the previous, valid configuration
+    g->plan.overlap_request = before;
+    seg_plan_configure(&g->plan, g->plan.threads, g->plan.ctas_per_sm, g->plan.table_request,
+                       stream);
+  }
+  return rc;
 }
 
 int pr_gather_table_capacity(int32_t ctas_per_sm) { return seg_table_capacity(ctas_per_sm); }

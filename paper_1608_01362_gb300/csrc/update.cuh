@@ -12,14 +12,22 @@ constexpr int kMergeWarps = 8;  // warps per merge / update block
 
 // ---------------------------------------------------------------------------
 // Cache-aware merge (Algorithm 4).  Each warp owns one merge block of B
-// destinations (a shared-memory accumulator of B values) and walks the
-// segments in ascending order: for segment s it adds the block's rows
-// [blk[s][b], blk[s][b+1]) of intermBuf into acc[idx_map[i] - b*B].  Inside
-// one segment the destinations are distinct, so lanes never collide; the
-// warp synchronises between segments, which keeps the per-destination order
-// fixed (deterministic).  The first rows of four segments are loaded
-// together before they are applied in order, and no block-wide barrier is
-// involved, so the k segments do not serialise k memory round trips.
+// destinations (a shared-memory accumulator of B values) and folds the
+// block's rows [blk[s][b], blk[s][b+1]) of intermBuf into
+// acc[idx_map[i] - b*B], segment after segment in ascending order, so every
+// destination receives its partial sums in segment order (deterministic).
+//
+// The rows of up to 32 segments are handled as one flattened sequence
+// (segment-major, so flattened order is segment order): lane l holds the
+// inclusive prefix of the row counts of segment s0+l, and a flattened
+// position f belongs to the segment whose prefix first exceeds f (a binary
+// search over the lanes).  A warp loads 32*U consecutive flattened rows at
+// once, then applies them 32 at a time; inside one group of 32 lanes the rows
+// of one segment have distinct destinations, and different segments are
+// applied one after the other in ascending order.  A block whose segments
+// hold a few rows each then costs one memory round trip instead of one per
+// segment, and a hub block's segments with hundreds of rows keep 32*U loads
+// in flight instead of 32.
 // ---------------------------------------------------------------------------
 
 template <class Op>
@@ -29,7 +37,8 @@ __device__ __forceinline__ void warp_merge(const int32_t* __restrict__ blk,
                                            int nb, int64_t mb, int64_t v0, int n,
                                            typename Op::T* acc) {
   using T = typename Op::T;
-  constexpr int G = 4;  // segments whose first rows are loaded together
+  constexpr int U = 4;  // groups of 32 flattened rows loaded together
+  constexpr unsigned kFull = 0xffffffffu;
   const int lane = threadIdx.x & 31;
   for (int i = lane; i < n; i += 32) acc[i] = Op::identity();
   __syncwarp();
@@ -40,34 +49,47 @@ __device__ __forceinline__ void warp_merge(const int32_t* __restrict__ blk,
       lo = __ldg(blk + (int64_t)ls * (nb + 1) + mb);
       hi = __ldg(blk + (int64_t)ls * (nb + 1) + mb + 1);
     }
-    const int cnt = k - s0 < 32 ? k - s0 : 32;
-    for (int t0 = 0; t0 < cnt; t0 += G) {
-      int32_t ii[G], hh[G], dd[G];
-      T xx[G];
+    // inclusive prefix of the row counts over the lanes' segments
+    int32_t pre = hi - lo;
 #pragma unroll
-      for (int u = 0; u < G; ++u) {  // first (up to 32) rows of G segments in flight
-        const int t = t0 + u < 31 ? t0 + u : 31;
-        ii[u] = __shfl_sync(0xffffffffu, lo, t) + lane;
-        hh[u] = t0 + u < cnt ? __shfl_sync(0xffffffffu, hi, t) : 0;
+    for (int o = 1; o < 32; o <<= 1) {
+      const int32_t t = __shfl_up_sync(kFull, pre, o);
+      if (lane >= o) pre += t;
+    }
+    const int32_t off = lo - (pre - (hi - lo));  // row index = flattened position + off
+    const int32_t total = __shfl_sync(kFull, pre, 31);
+    for (int32_t base = 0; base < total; base += 32 * U) {
+      int32_t seg[U], dd[U];
+      T xx[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int32_t f = base + u * 32 + lane;
+        int j = 0;  // number of segments whose rows all precede f
+#pragma unroll
+        for (int step = 16; step; step >>= 1)
+          if (__shfl_sync(kFull, pre, j + step - 1) <= f) j += step;
+        const int32_t row = f + __shfl_sync(kFull, off, j);
+        seg[u] = f < total ? j : 32;
         dd[u] = 0;
         xx[u] = Op::identity();
-        if (ii[u] < hh[u]) {
-          dd[u] = __ldcs(idx_map + ii[u]);
-          xx[u] = __ldcs(interm + ii[u]);
+        if (f < total) {
+          dd[u] = __ldcs(idx_map + row);
+          xx[u] = __ldcs(interm + row);
         }
       }
 #pragma unroll
-      for (int u = 0; u < G; ++u) {  // apply in segment order
-        if (ii[u] < hh[u]) {
-          const int64_t lv = (int64_t)dd[u] - v0;
-          if ((uint64_t)lv < (uint64_t)n) acc[lv] = Op::op(acc[lv], xx[u]);
+      for (int u = 0; u < U; ++u) {  // apply in flattened (= segment) order
+        unsigned pend = __ballot_sync(kFull, seg[u] < 32);
+        while (pend) {
+          const int sj = __shfl_sync(kFull, seg[u], __ffs(pend) - 1);
+          const bool mine = seg[u] == sj;
+          if (mine) {
+            const int64_t lv = (int64_t)dd[u] - v0;
+            if ((uint64_t)lv < (uint64_t)n) acc[lv] = Op::op(acc[lv], xx[u]);
+          }
+          __syncwarp();
+          pend &= ~__ballot_sync(kFull, mine);
         }
-        for (int32_t i = ii[u] + 32; i < hh[u]; i += 32) {  // segments with > 32 rows here
-          const int64_t lv = (int64_t)__ldcs(idx_map + i) - v0;
-          const T x = __ldcs(interm + i);
-          if ((uint64_t)lv < (uint64_t)n) acc[lv] = Op::op(acc[lv], x);
-        }
-        __syncwarp();
       }
     }
   }

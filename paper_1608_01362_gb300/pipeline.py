@@ -94,10 +94,14 @@ class _PageRankBase:
 
 
 def plan_bounds(graph: Graph, ctas_per_sm: int = 1, min_avg_degree: float = 64.0,
-                max_global_vertices: int = 1 << 24):
+                max_global_vertices: int = 1 << 24, table_vertices: int = -1):
     """Segment bounds for this GPU: shared-memory-sized segments over the hot
-    (clustered) head, L2-sized segments over the cold rest."""
+    (clustered) head, L2-sized segments over the cold rest.  table_vertices
+    (> 0) caps the shared table below its capacity, which leaves the rest of
+    the SM's on-chip store to L1 (and to the misses L1 keeps in flight)."""
     H = C.pr_gather_table_capacity(ctas_per_sm)
+    if table_vertices > 0:
+        H = min(H, table_vertices)
     return C.pr_plan_bounds(graph.outdeg, H, min_avg_degree, max_global_vertices)
 
 
@@ -109,7 +113,7 @@ class SegmentedPageRank(_PageRankBase):
 
     def __init__(self, graph: Graph, num_segments: int | None = None, merge_block: int = 512,
                  bounds=None, threads: int = 1024, ctas_per_sm: int = 1,
-                 table_vertices: int = -1):
+                 table_vertices: int = -1, overlap: int = 0):
         super().__init__(graph)
         if bounds is not None:
             bounds = np.asarray(bounds, dtype=np.int64)
@@ -118,6 +122,8 @@ class SegmentedPageRank(_PageRankBase):
                                        merge_block=merge_block)
         if (threads, ctas_per_sm, table_vertices) != (1024, 1, -1):
             C.pr_set_gather_config(self.seg, threads, ctas_per_sm, table_vertices)
+        if overlap:
+            C.pr_set_gather_overlap(self.seg, overlap)
 
     @property
     def info(self):
@@ -218,9 +224,9 @@ def _build(graph, cand, merge_block):
     if cand["kind"] == "uniform":
         return SegmentedPageRank(graph, cand["k"], merge_block=merge_block, threads=t,
                                  ctas_per_sm=c, table_vertices=tb)
-    b = plan_bounds(graph, c, cand["min_avg_degree"])
+    b = plan_bounds(graph, c, cand["min_avg_degree"], table_vertices=tb)
     return SegmentedPageRank(graph, bounds=b, merge_block=merge_block, threads=t, ctas_per_sm=c,
-                             table_vertices=tb)
+                             table_vertices=tb, overlap=cand.get("overlap", 0))
 
 
 def autotune_segments(graph: Graph, candidates=None, merge_block: int = 512,
@@ -262,7 +268,7 @@ class LabelPropagation:
 
     def __init__(self, graph: Graph, num_segments: int | None = None, bounds=None,
                  merge_block: int = 512, threads: int = 1024, ctas_per_sm: int = 1,
-                 table_vertices: int = -1):
+                 table_vertices: int = -1, overlap: int = 0):
         self.g = graph
         if bounds is not None:
             bounds = np.asarray(bounds, dtype=np.int64)
@@ -271,6 +277,8 @@ class LabelPropagation:
                                        merge_block=merge_block)
         if (threads, ctas_per_sm, table_vertices) != (1024, 1, -1):
             C.pr_set_gather_config(self.seg, threads, ctas_per_sm, table_vertices)
+        if overlap:
+            C.pr_set_gather_overlap(self.seg, overlap)
         V = graph.V
         self.labels = [torch.empty(V, dtype=torch.int32, device=graph.device) for _ in range(2)]
 

@@ -325,6 +325,85 @@ def test_gather_config_rejects_bad_shape(C, torch_mod, rmat16):
         C.pr_set_gather_config(pr.seg, 1024, 2, -1)
 
 
+def _overlap_graphs():
+    gs = {"rmat16": graphgen.rmat(16, 16, seed=1)}
+    gs.update({n: g for n, g in _special_graphs().items() if n in ("in_star", "out_star", "ragged")})
+    # 600 sources of out-degree 8 (a staged head) and 3000 of out-degree 1 that
+    # all point at vertex 0: a row of 3000 edges inside the L1/L2 segments, so
+    # it spans many queue chunks and is completed through their carries
+    rng = np.random.default_rng(9)
+    hot = np.repeat(np.arange(600), 8)
+    src = np.concatenate([hot, np.arange(600, 3600)])
+    dst = np.concatenate([rng.integers(1, 3600, hot.size), np.zeros(3000, dtype=np.int64)])
+    gs["cold_hub"] = graphgen.from_edges(3600, src, dst)
+    return gs
+
+
+@pytest.mark.parametrize("name", ["rmat16", "in_star", "out_star", "ragged", "cold_hub"])
+def test_gather_overlap_bit_identical(C, torch_mod, name):
+    """One launch serving staged and L1/L2 segments side by side (warps split
+    per block, a chunk queue for the L1/L2 side) gives the same row sums, bit
+    for bit, as the two launches, for every split; PageRank and min-label
+    gathers through it too."""
+    torch = torch_mod
+    from paper_1608_01362_gb300 import pipeline as P
+    g = _overlap_graphs()[name]
+    graph = P.Graph(g.offsets, g.src, cluster_mode=0)
+    # a staged head of 512-vertex segments and a cold rest of small L1/L2 segments
+    b = C.pr_plan_bounds(graph.outdeg, 512, 2.0, 3000)
+    seg = C.pr_build_segments(graph.offsets, graph.src, len(b) - 1, bounds=b)
+    info = seg.info
+    rows = info["rows"]
+    rng = np.random.default_rng(3)
+    x = _dev(torch, rng.random(graph.V).astype(np.float32), torch.float32)
+    lab = _dev(torch, rng.permutation(graph.V).astype(np.int32), torch.int32)
+    ref = torch.empty(max(rows, 1), dtype=torch.float32, device="cuda")
+    ref_i = torch.empty(max(rows, 1), dtype=torch.int32, device="cuda")
+    C.cg_seg_gather(seg, C.CG_OP_SUM_F32, x, ref)
+    C.cg_seg_gather(seg, C.CG_OP_MIN_I32, lab, ref_i)
+    both = info["staged_segments"] > 0 and info["staged_edges"] < graph.E
+    for ow in (1, 4, 8, 16, 24):
+        C.pr_set_gather_overlap(seg, ow)
+        assert seg.info["gather_overlap"] == (ow if both else 0)
+        got = torch.full_like(ref, float("nan"))
+        got_i = torch.full_like(ref_i, -7)
+        C.cg_seg_gather(seg, C.CG_OP_SUM_F32, x, got)
+        C.cg_seg_gather(seg, C.CG_OP_MIN_I32, lab, got_i)
+        assert torch.equal(got[:rows], ref[:rows]), ow
+        assert torch.equal(got_i[:rows], ref_i[:rows]), ow
+    C.pr_set_gather_overlap(seg, 0)
+    assert seg.info["gather_overlap"] == 0
+    if name in ("rmat16", "cold_hub", "ragged"):
+        assert both
+    if name == "rmat16":
+        base, rb = P.SegmentedPageRank(graph, bounds=b).run(20)
+        for ow in (4, 12):
+            rank, resid = P.SegmentedPageRank(graph, bounds=b, overlap=ow).run(20)
+            assert torch.equal(rank, base) and torch.equal(resid, rb)
+
+
+def test_gather_overlap_rejects_bad_settings(C, torch_mod, rmat16):
+    from paper_1608_01362_gb300 import pipeline as P
+    graph = P.Graph(rmat16.offsets, rmat16.src, cluster_mode=0)
+    b = C.pr_plan_bounds(graph.outdeg, 512, 2.0, 3000)
+    pr = P.SegmentedPageRank(graph, bounds=b)
+    for bad in (-1, 25, 32):
+        with pytest.raises(C.CagraError, match="cached_warps"):
+            C.pr_set_gather_overlap(pr.seg, bad)
+    C.pr_set_gather_config(pr.seg, 512, 2, -1)
+    with pytest.raises(C.CagraError, match="overlap"):
+        C.pr_set_gather_overlap(pr.seg, 8)
+    assert pr.info["gather_overlap"] == 0  # the previous, valid configuration stays
+    C.pr_set_gather_config(pr.seg, 1024, 1, -1)
+    C.pr_set_gather_overlap(pr.seg, 8)
+    assert pr.info["gather_overlap"] == 8
+    # the shape setter keeps the overlap request, and refuses shapes it cannot serve
+    with pytest.raises(C.CagraError, match="overlap"):
+        C.pr_set_gather_config(pr.seg, 512, 2, -1)
+    C.pr_set_gather_config(pr.seg, 1024, 1, 4096)
+    assert pr.info["gather_overlap"] == 8
+
+
 def test_planned_bounds(C, torch_mod, rmat16, rmat16_oracle):
     torch = torch_mod
     from paper_1608_01362_gb300 import pipeline as P
