@@ -66,6 +66,18 @@ def _peaks():
         return 6800.0, "fallback"
 
 
+def gather_peaks(C, row_bytes_and_tables, smem=False):
+    """Random-read ceilings of this GPU, measured now (the row gathers are
+    bound by these, not by a streaming copy): {(row_bytes, table_bytes):
+    GB/s}, plus shared-memory lookups in G/s when smem."""
+    out = {}
+    for rb, tb in row_bytes_and_tables:
+        out[(rb, tb)] = C.measure_row_gather(rb, tb) / 1e9
+    if smem:
+        out["smem"] = C.measure_smem_lookups() / 1e9
+    return out
+
+
 class ClockSampler:
     """nvidia-smi clock / throttle sampling during the timed region."""
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
@@ -503,6 +515,16 @@ def run_ppr(args):
     peak, peak_kind = _peaks()
     ach = alg[dom] / (phase_ms[dom] / 1e3) / 1e9
     edge_cols = g.E * 64 * ITERS
+    # the gather reads one 64-column row (BF16 hi+lo: 256 bytes) per edge from a
+    # table of the non-dangling sources' rows; its ceiling is the random-row
+    # rate of such a table (measured now); hub rows reread from L1/L2 can
+    # carry it above that rate
+    rb = 128 * pl
+    gp = gather_peaks(C, [(rb, rb * nd)])
+    a_rows = g.E * rb / (phase_ms["gather"] / 1e3) / 1e9
+    gather_rows = {"bound": "random rows", "unit": "GB/s", "row_bytes": rb,
+                   "table_bytes": rb * nd, "achieved": a_rows, "peak": gp[(rb, rb * nd)],
+                   "frac": a_rows / gp[(rb, rb * nd)]}
     line = {"metric": "batched personalised PageRank: edge-vector GTEPS (64 vectors x 20 "
                       "iterations) at BF16 hi+lo storage",
             "value": edge_cols / t_step / 1e9, "unit": "GTEPS (edge x vector)", "n_gpus": 1,
@@ -517,6 +539,7 @@ def run_ppr(args):
             "roofline": {"bound": "hbm", "kernel": dom, "achieved": ach, "peak": peak,
                          "unit": "GB/s", "frac": ach / peak, "traffic": None,
                          "peak_source": peak_kind, "algorithmic_bytes": alg[dom]},
+            "gather_row_bound": gather_rows,
             "single_vector_64_runs_ms": t_single * 1e3,
             "speedup_vs_64_single_runs": t_single / t_step,
             "rel_l1_vs_oracle_sampled_columns": {int(c): float(e) for c, e in zip(cols, err)},
@@ -638,6 +661,16 @@ def run_cf(args):
     dom = max(head["kernels_ms"], key=head["kernels_ms"].get)
     dom_bytes = 5 * R + (U + I) * K * 4
     ach = dom_bytes / (head["kernels_ms"][dom] / 1e3) / 1e9
+    # the gathers read one factor row (4K bytes) per rating at random from an
+    # L2-resident table: their ceiling is L2's random-row rate, measured now
+    rb = 4 * K
+    gp = gather_peaks(C, [(rb, I * rb), (rb, U * rb)])
+    gathers_l2 = {}
+    for nm, tb in (("user_gather", I * rb), ("item_gather", U * rb)):
+        a = R * rb / (head["kernels_ms"][nm] / 1e3) / 1e9
+        gathers_l2[nm] = {"bound": "L2 random rows", "unit": "GB/s", "row_bytes": rb,
+                          "table_bytes": tb, "achieved": a, "peak": gp[(rb, tb)],
+                          "frac": a / gp[(rb, tb)]}
     line = {"metric": "collaborative filtering sweep: ratings x sides per second (GTEPS), K=32, "
                       "BF16 hi+lo storage, RMSE diff vs FP64",
             "value": 2 * R / t_sweep / 1e9, "unit": "GTEPS (rating x side)", "n_gpus": 1,
@@ -654,6 +687,7 @@ def run_cf(args):
                          "peak_source": peak_kind, "algorithmic_bytes": dom_bytes,
                          "note": "gathers are L2-bound: every rating reads a factor row "
                                  "from L2 (factors stay resident)"},
+            "gathers_l2_bound": gathers_l2,
             "sweep_algorithmic_dram_bytes": alg,
             "clocks": head["clocks"],
             "e2e": {"value": 2 * R * SWEEPS / head["e2e_s"] / 1e9, "unit": "GTEPS (rating x side)",
@@ -863,6 +897,27 @@ def main():
     bmin = 4 * E + 28 * V
     achieved = bmin / t_iter_ev / 1e9
     traffic = _traffic_per_iteration(E)
+    # each launch against the ceiling of what it does: shared-memory lookups
+    # (staged gather), random 4-byte L2 reads from the cold sources' table
+    # (L1/L2 gather, fix-up included), HBM (merge + update: 8 B per subgraph
+    # row, 20 B per vertex)
+    staged_e = int(info["staged_edges"])
+    cold_tab = 4 * max(2, min(1 << 24, V - int(info["staged_segments"]) * int(info["table_vertices"])))
+    gp = gather_peaks(C, [(4, cold_tab)], smem=True)
+    m_bytes = 8 * rows + 20 * V
+    per_launch = {
+        "staged_gather": {"bound": "shared-memory random lookups", "unit": "G lookups/s",
+                          "achieved": staged_e / t_staged / 1e9, "peak": gp["smem"],
+                          "frac": staged_e / t_staged / 1e9 / gp["smem"]},
+        "cached_gather_and_fixup": {
+            "bound": "L2 random 4-byte reads", "unit": "GB/s", "table_bytes": cold_tab,
+            "achieved": 4 * (E - staged_e) / t_cached / 1e9, "peak": gp[(4, cold_tab)],
+            "frac": 4 * (E - staged_e) / t_cached / 1e9 / gp[(4, cold_tab)]},
+        "merge_update": {"bound": "hbm", "unit": "GB/s", "algorithmic_bytes": m_bytes,
+                         "achieved": m_bytes / t_merge / 1e9, "peak": hbm,
+                         "frac": m_bytes / t_merge / 1e9 / hbm},
+        "peaks_measured_by": "cg_measure_smem_lookups, cg_measure_row_gather in this run",
+    }
 
     line = {
         "metric": METRIC, "value": value, "unit": "GTEPS", "n_gpus": world,
@@ -888,6 +943,7 @@ def main():
         "kernels_ms": {"staged_gather": t_staged * 1e3, "cached_gather_and_fixup": t_cached * 1e3,
                        "merge_update": t_merge * 1e3, "staged_edges": int(info["staged_edges"]),
                        "subgraph_rows": rows},
+        "per_launch_bounds": per_launch,
         "gteps_at_hbm_peak": E / (bmin / (hbm * 1e9)) / 1e9,
         "comparisons": {
             "segmented_gteps": E / seg_iter_s / 1e9,

@@ -37,7 +37,7 @@ EXPORTS = [
     "ppr_batched_create", "ppr_batched_destroy", "ppr_batched_bytes", "ppr_batched_init",
     "ppr_batched_iterate", "ppr_batched_step",
     "cf_transpose", "cf_create", "cf_destroy", "cf_set_factors", "cf_get_factors", "cf_sweep",
-    "cf_sweep_phase", "cf_info",
+    "cf_sweep_phase", "cf_info", "cg_measure_row_gather", "cg_measure_smem_lookups",
 ]
 
 
@@ -124,6 +124,8 @@ def load(path: str | None = None):
             "cf_sweep": (ctypes.c_int, [vp, i32, dbl, dbl, vp, vp]),
             "cf_sweep_phase": (ctypes.c_int, [vp, i32, dbl, dbl, vp, vp]),
             "cf_info": (ctypes.c_int, [vp, vp, vp, vp, vp]),
+            "cg_measure_row_gather": (ctypes.c_int, [i32, i64, vp, vp]),
+            "cg_measure_smem_lookups": (ctypes.c_int, [vp, vp]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)
@@ -591,3 +593,20 @@ def pr_batch_set_threads(batch: Batch, threads: int):
 def pr_batch_run(batch: Batch, iterations: int, damping: float, rank, resid=None, stream=None):
     _check(load().pr_batch_run(batch.handle, iterations, damping, _ptr(rank), _ptr(resid),
                                _stream(stream)), "pr_batch_run")
+
+
+def measure_row_gather(row_bytes: int, table_bytes: int, stream=None) -> float:
+    """Bytes per second of random row reads (rows of 4, 128 or 256 bytes)
+    from a table of table_bytes on the current GPU."""
+    out = ctypes.c_double()
+    _check(load().cg_measure_row_gather(row_bytes, int(table_bytes), ctypes.byref(out),
+                                        _stream(stream)), "cg_measure_row_gather")
+    return out.value
+
+
+def measure_smem_lookups(stream=None) -> float:
+    """Random 4-byte shared-memory lookups per second on the current GPU."""
+    out = ctypes.c_double()
+    _check(load().cg_measure_smem_lookups(ctypes.byref(out), _stream(stream)),
+           "cg_measure_smem_lookups")
+    return out.value
