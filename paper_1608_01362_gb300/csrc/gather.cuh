@@ -25,15 +25,21 @@
 
 namespace cg {
 
+// kExactAnyOrder: the combination gives the same result in any order (and a
+// shared-memory atomic can apply it), so a merge need not keep segment order.
 struct SumF32 {
   using T = float;
+  static constexpr bool kExactAnyOrder = false;  // FP rounding depends on the order
   static __device__ __forceinline__ T identity() { return 0.0f; }
   static __device__ __forceinline__ T op(T a, T b) { return a + b; }
+  static __device__ __forceinline__ void atomic_op(T* p, T v) { *p = op(*p, v); }
 };
 struct MinI32 {
   using T = int32_t;
+  static constexpr bool kExactAnyOrder = true;
   static __device__ __forceinline__ T identity() { return 0x7FFFFFFF; }
   static __device__ __forceinline__ T op(T a, T b) { return a < b ? a : b; }
+  static __device__ __forceinline__ void atomic_op(T* p, T v) { atomicMin(p, v); }
 };
 
 // Read-only random load of a gathered vertex value (L1-cached).

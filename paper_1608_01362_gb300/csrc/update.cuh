@@ -24,10 +24,11 @@ constexpr int kMergeWarps = 8;  // warps per merge / update block
 // search over the lanes).  A warp loads 32*U consecutive flattened rows at
 // once, then applies them 32 at a time; inside one group of 32 lanes the rows
 // of one segment have distinct destinations, and different segments are
-// applied one after the other in ascending order.  A block whose segments
-// hold a few rows each then costs one memory round trip instead of one per
-// segment, and a hub block's segments with hundreds of rows keep 32*U loads
-// in flight instead of 32.
+// applied one after the other in ascending order.  An operator that is exact
+// in any order (min) applies a whole group at once with shared-memory
+// atomics instead.  A block whose segments hold a few rows each then costs
+// one memory round trip instead of one per segment, and a hub block's
+// segments with hundreds of rows keep 32*U loads in flight instead of 32.
 // ---------------------------------------------------------------------------
 
 template <class Op>
@@ -76,6 +77,14 @@ __device__ __forceinline__ void warp_merge(const int32_t* __restrict__ blk,
           dd[u] = __ldcs(idx_map + row);
           xx[u] = __ldcs(interm + row);
         }
+      }
+      if constexpr (Op::kExactAnyOrder) {  // e.g. min: every row at once
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          const int64_t lv = (int64_t)dd[u] - v0;
+          if (seg[u] < 32 && (uint64_t)lv < (uint64_t)n) Op::atomic_op(acc + lv, xx[u]);
+        }
+        continue;
       }
 #pragma unroll
       for (int u = 0; u < U; ++u) {  // apply in flattened (= segment) order
