@@ -223,7 +223,7 @@ def run_lp(args):
     g = graphgen.rmat(scale, 16, seed=1, symmetric=True)
     gen_s = time.time() - t
     graph = P.Graph(g.offsets, g.src, cluster_mode=0)
-    bounds = P.plan_bounds(graph, 1, args.plan or 16.0)
+    bounds = P.plan_bounds(graph, 1, args.plan or 24.0)
     lp = P.LabelPropagation(graph, bounds=bounds, overlap=args.overlap)
     for _ in range(args.warmup):
         lp.run(max_passes=2)

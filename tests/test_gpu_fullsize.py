@@ -57,7 +57,7 @@ def test_label_propagation_rmat24_full(env):
     torch, C, P = env
     g = graphgen.rmat(24, 16, seed=1, symmetric=True)
     graph = P.Graph(g.offsets, g.src, cluster_mode=0)
-    lp = P.LabelPropagation(graph, bounds=P.plan_bounds(graph, 1, 16.0))
+    lp = P.LabelPropagation(graph, bounds=P.plan_bounds(graph, 1, 24.0))
     labels, passes, changes = lp.run()
     got = labels.cpu().numpy()
     del lp, graph
