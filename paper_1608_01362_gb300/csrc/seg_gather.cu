@@ -826,7 +826,6 @@ int seg_plan_configure(SegPlan* p, int threads, int ctas_per_sm, int tab_vertice
   CG_CUDA(cudaStreamSynchronize(s));  // host vectors go out of scope
   p->threads = threads;
   p->ctas_per_sm = ctas_per_sm;
-  p->ipl_a = kStagedIPL;
   p->tab_cap = (int)((tabmax + 3) & ~3LL);
   p->table_request = tab;
   p->m = m;

@@ -56,7 +56,6 @@ struct SegPlan {
   std::vector<int64_t> h_cstart, src_bounds, edge_base, row_base;
   int threads = 1024;       // staged-segment launch shape
   int ctas_per_sm = 1;
-  int ipl_a = 8;            // edges per lane of the staged launch
   int tab_cap = 0;          // table entries of the staged launch (its largest segment)
   int table_request = 0;    // the capacity asked for
   int m = 0;                // segments [0, m) are staged in shared memory
@@ -100,7 +99,9 @@ int64_t seg_plan_bytes(const SegPlan& p);
 int seg_plan_export_col(const SegPlan& p, const int32_t* rp, int32_t* col, cudaStream_t s);
 
 // Launch phases of one pass (all by default): the staged launch, the L1/L2
-// launch and the carry fix-up, in that order.
+// launch and the carry fix-up, in that order.  With the overlap in effect one
+// launch serves both kinds of segment: it runs for kPhaseStaged and
+// kPhaseCached launches nothing.
 constexpr int kPhaseStaged = 1, kPhaseCached = 2, kPhaseFixup = 4, kPhaseAll = 7;
 
 template <class Op>
