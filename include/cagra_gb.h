@@ -171,7 +171,9 @@ int cg_segmented_get_info(const cg_segmented *seg, cg_segmented_info *info);
  * block per SM) for as long as such a segment still carries at least
  * `min_avg_degree` out-edges per vertex, i.e. enough reads to repay staging
  * it on chip; the colder rest is cut into segments of at most
- * `max_global_vertices` sources, served through L1/L2.  dev_outdeg: int32[V]
+ * `max_global_vertices` sources, served through L1/L2 (<= 0: as many 4-byte
+ * source values as fill half of this GPU's L2, from its device properties).
+ * dev_outdeg: int32[V]
  * of the (clustered) graph.  Writes k+1 bounds to host_bounds (capacity
  * k_max+1) and k to *k_out.  Synchronizes (reads the degrees on the host).
  */

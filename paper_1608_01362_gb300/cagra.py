@@ -252,7 +252,7 @@ def pr_build_segments(offsets, src, num_segments: int, bounds=None, merge_block:
 
 
 def pr_plan_bounds(outdeg, smem_vertices: int = -1, min_avg_degree: float = 64.0,
-                   max_global_vertices: int = 1 << 24, k_max: int = 1024, stream=None):
+                   max_global_vertices: int = -1, k_max: int = 1024, stream=None):
     """Segment bounds for this GPU (host int64 array of k+1 entries)."""
     out = np.empty(k_max + 1, dtype=np.int64)
     k = ctypes.c_int32()

@@ -536,7 +536,12 @@ int pr_plan_bounds(const int32_t* dev_outdeg, int32_t V, int32_t smem_vertices,
   CG_ARG(dev_outdeg && host_bounds && k_out && V >= 1, "pr_plan_bounds: bad arguments");
   CG_ARG(k_max >= 1 && k_max <= kMaxSegments, "pr_plan_bounds: k_max must be in [1, %d]",
          kMaxSegments);
-  CG_ARG(max_global_vertices >= 1, "pr_plan_bounds: max_global_vertices must be >= 1");
+  if (max_global_vertices <= 0) {  // half of this GPU's L2 in 4-byte source values
+    DeviceInfo di{};
+    CG_TRY(device_info(&di));
+    max_global_vertices = (int32_t)std::max<int64_t>(
+        1, std::min<int64_t>((int64_t)(di.l2_bytes / 8), (int64_t)0x7FFFFFFF));
+  }
   if (smem_vertices < 0) smem_vertices = seg_table_capacity(1);
   std::vector<int32_t> deg(V);
   CG_CUDA(cudaMemcpyAsync(deg.data(), dev_outdeg, sizeof(int32_t) * (size_t)V,

@@ -94,9 +94,10 @@ class _PageRankBase:
 
 
 def plan_bounds(graph: Graph, ctas_per_sm: int = 1, min_avg_degree: float = 64.0,
-                max_global_vertices: int = 1 << 24, table_vertices: int = -1):
+                max_global_vertices: int = -1, table_vertices: int = -1):
     """Segment bounds for this GPU: shared-memory-sized segments over the hot
-    (clustered) head, L2-sized segments over the cold rest.  table_vertices
+    (clustered) head, L2-sized segments over the cold rest (-1: half of the
+    L2's bytes in 4-byte source values).  table_vertices
     (> 0) caps the shared table below its capacity, which leaves the rest of
     the SM's on-chip store to L1 (and to the misses L1 keeps in flight)."""
     H = C.pr_gather_table_capacity(ctas_per_sm)

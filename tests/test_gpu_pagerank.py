@@ -428,6 +428,23 @@ def test_planned_bounds(C, torch_mod, rmat16, rmat16_oracle):
                     4096, bounds=b)
 
 
+def test_planned_bounds_default_cold_size_from_l2(C, torch_mod, rmat16):
+    """With max_global_vertices <= 0 the cold segments hold at most half of the
+    L2's bytes in 4-byte values (the L2 size read from the device)."""
+    import torch
+    from paper_1608_01362_gb300 import pipeline as P
+    graph = P.Graph(rmat16.offsets, rmat16.src, cluster_mode=0)
+    l2 = torch.cuda.get_device_properties(0).L2_cache_size
+    assert l2 > 0
+    # no shared-memory head (threshold above any degree): only L2-sized segments
+    b = C.pr_plan_bounds(graph.outdeg, -1, 1e12, -1)
+    assert b[0] == 0 and b[-1] == graph.V
+    assert np.all(np.diff(b) <= l2 // 8)
+    # a tiny explicit size still wins
+    b2 = C.pr_plan_bounds(graph.outdeg, -1, 1e12, 1000)
+    assert len(b2) - 1 == -(-graph.V // 1000) and np.all(np.diff(b2) <= 1000)
+
+
 def test_autotuner_returns_valid_choice(C, torch_mod, rmat16):
     from paper_1608_01362_gb300 import pipeline as P
     graph = P.Graph(rmat16.offsets, rmat16.src, cluster_mode=0)
