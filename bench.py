@@ -141,9 +141,12 @@ def kernel_source_hash():
     return h.hexdigest()[:16]
 
 
-def _traffic_per_iteration(E):
-    """DRAM bytes per iteration from the committed ncu summary (per edge,
-    scaled to E), when it was taken on the current kernel sources; else None."""
+def _traffic_per_iteration(E, scale=25):
+    """DRAM bytes per iteration from the committed ncu summary of the RMAT-25
+    workload (per edge, scaled to E), when it was taken on the current kernel
+    sources and the run is that workload; else None."""
+    if scale != 25:
+        return None
     try:
         with open(os.path.join(ROOT, "profiles", "pagerank_iteration_rmat25_traffic.json")) as f:
             t = json.load(f)
@@ -913,6 +916,18 @@ def main():
     plain_orig.step(plain_orig.rank[0], plain_orig.contrib[0], plain_orig.rank[1],
                     plain_orig.contrib[1], DAMPING, 2)
     t_plain_orig = P.time_iterations(plain_orig, ITERS, reps=3)
+    # the fourth variant of the paper's comparison: segmented in the original
+    # (unclustered) order, the paper's uniform split at the best uniform k the
+    # autotuner measured (4 when it did not run)
+    uni = [r for r in table if r["candidate"]["kind"] == "uniform"]
+    k_orig = int(min(uni, key=lambda r: r["s_per_iter"])["candidate"]["k"]) if uni else 4
+    seg_orig = P.SegmentedPageRank(plain_orig_graph, k_orig)
+    seg_orig.init()
+    seg_orig.step(seg_orig.rank[0], seg_orig.contrib[0], seg_orig.rank[1], seg_orig.contrib[1],
+                  DAMPING, 2)
+    t_seg_orig = P.time_iterations(seg_orig, ITERS, reps=3)
+    seg_orig.seg.close()
+    del seg_orig
     plain_cl = P.PlainPageRank(graph)
     t_plain_cl = P.time_iterations(plain_cl, ITERS, reps=3)
     probe = P.PlainPageRank(graph, probe=True)
@@ -928,7 +943,7 @@ def main():
     rows = int(info["rows"])
     bmin = 4 * E + 28 * V
     achieved = bmin / t_iter_ev / 1e9
-    traffic = _traffic_per_iteration(E)
+    traffic = _traffic_per_iteration(E, args.scale)
     # each launch against the ceiling of what it does: shared-memory lookups
     # (staged gather), random 4-byte L2 reads from the cold sources' table
     # (L1/L2 gather, fix-up included), HBM (merge + update: 8 B per subgraph
@@ -957,7 +972,9 @@ def main():
         "ms_per_step": t_max / args.steps * 1e3, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": f"pagerank_rmat{args.scale}_directed_ef16_segmented_clustered",
-                   "V": V, "E": E, "iterations_per_step": ITERS, "damping": DAMPING,
+                   "V": V, "E": E, "max_in_degree": int(np.diff(g.offsets).max()),
+                   "max_out_degree": int(graph.outdeg.max().item()),
+                   "iterations_per_step": ITERS, "damping": DAMPING,
                    "segments": best_k, "merge_block": args.merge_block, "q": info["q"],
                    "segmenting": best, "table_vertices": info["table_vertices"],
                    "staged_segments": info["staged_segments"],
@@ -980,6 +997,8 @@ def main():
         "comparisons": {
             "segmented_gteps": E / seg_iter_s / 1e9,
             "plain_original_order_gteps": E / t_plain_orig / 1e9,
+            "segmented_original_order_gteps": E / t_seg_orig / 1e9,
+            "segmented_original_order_k": k_orig,
             "plain_clustered_gteps": E / t_plain_cl / 1e9,
             "vertex0_probe_gteps": E / t_probe / 1e9,
             "speedup_vs_plain_original": t_plain_orig / seg_iter_s,
