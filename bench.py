@@ -141,16 +141,19 @@ def kernel_source_hash():
     return h.hexdigest()[:16]
 
 
-def _traffic_per_iteration(E, scale=25):
+def _traffic_per_iteration(E, scale=25, segments=None):
     """DRAM bytes per iteration from the committed ncu summary of the RMAT-25
     workload (per edge, scaled to E), when it was taken on the current kernel
-    sources and the run is that workload; else None."""
+    sources, the run is that workload and it runs the profiled plan (the same
+    segment count); else None."""
     if scale != 25:
         return None
     try:
         with open(os.path.join(ROOT, "profiles", "pagerank_iteration_rmat25_traffic.json")) as f:
             t = json.load(f)
         if t.get("kernel_source_sha") != kernel_source_hash():
+            return None
+        if segments is not None and int(t["plan"]["segments"]) != int(segments):
             return None
         return float(t["dram_bytes_per_edge"]) * E
     except Exception:
@@ -164,38 +167,79 @@ def make_graph(scale):
     return g, time.time() - t
 
 
-def cpu_baseline(g, budget_s=15.0):
-    """The FP64 oracle (plain pull PageRank, OpenMP over rows) on the host
-    cores, on a bounded sample: as many whole iterations over the full graph
-    as fit in about budget_s seconds (at least one)."""
+def cpu_model() -> str:
+    """The host CPU's model name (lscpu, else /proc/cpuinfo, else platform)."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name:"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.lower().startswith("model name"):
+                    return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    import platform
+    return platform.processor() or platform.machine()
+
+
+def oracle_solution(g):
+    """The FP64 oracle on the full graph: 20 plain-pull iterations from
+    r_0 = 1/V, with the per-vertex bound on the rounding error of any FP32
+    evaluation of them.  Each plain iteration is timed alone (the out-degree
+    pass, the allocations and the bound's own work are outside its timer).
+    Returns (rank, bound, seconds per iteration, wall seconds of the call)."""
     import oracle
+    secs = np.zeros(ITERS)
     t0 = time.time()
-    oracle.pagerank(g.offsets, g.src, iters=1)
-    t1 = time.time() - t0
-    n = max(1, min(ITERS, int(budget_s / max(t1, 1e-3)) - 1))
-    t0 = time.time()
-    oracle.pagerank(g.offsets, g.src, iters=n)
-    dt = time.time() - t0
-    return {"value": g.E * n / dt / 1e9, "unit": "GTEPS", "cores": oracle.num_threads(),
-            "kind": "oracle",
-            "sample": f"{n} FP64 plain-pull iteration(s) over the full RMAT-{int(np.log2(g.V))} "
-                      f"graph (V={g.V}, E={g.E})"}
+    want, bound = oracle.pagerank_bound(g.offsets, g.src, iters=ITERS, iter_seconds=secs)
+    return want, bound, secs, time.time() - t0
+
+
+def cpu_baseline_from(g, secs):
+    """cpu_baseline record of the oracle's timed iterations."""
+    import oracle
+    t = float(np.median(secs))
+    return {"value": g.E / t / 1e9, "unit": "GTEPS", "cores": oracle.num_threads(),
+            "cpu": cpu_model(), "kind": "oracle",
+            "sample": f"{len(secs)} FP64 plain-pull iterations over the full graph "
+                      f"(V={g.V}, E={g.E}), each timed alone (set-up excluded); "
+                      f"value = E / median iteration time",
+            "seconds_per_iteration_median": t}
+
+
+def parity_report(got, want, bound, tol_l1=1e-5):
+    """Element-by-element comparison of an FP32 rank vector with the FP64
+    oracle: relative L1 (the metric's gate), the largest error as a fraction
+    of its vertex's rounding bound, vertices outside their bound, and the
+    largest relative error."""
+    err = np.abs(np.asarray(got, np.float64) - want)
+    rl1 = float(err.sum() / np.abs(want).sum())
+    outside = int(np.count_nonzero(~(err <= bound)))
+    return {"rel_l1": rl1, "tol_rel_l1": tol_l1,
+            "max_err_over_bound": float(np.max(err / bound)),
+            "vertices_outside_bound": outside,
+            "max_rel_err": float(np.max(err / want)),
+            "ok": bool(rl1 <= tol_l1 and outside == 0)}
 
 
 def run_reference(args):
-    """--impl reference: the FP64 oracle timed on the host cores (rank 0)."""
+    """--impl reference: the FP64 oracle timed on the host cores (rank 0).
+    One step = one plain-pull iteration over the full graph, timed inside the
+    oracle (set-up excluded, the same routine as the cpu_baseline leg)."""
     rank, world, _ = _dist()
     if rank != 0:
         return
     import oracle
     g, _ = make_graph(args.scale)
-    rank0 = np.full(g.V, 1.0 / g.V)
-    for _ in range(args.warmup):
-        oracle.pagerank(g.offsets, g.src, iters=1, rank0=rank0)
-    t0 = time.time()
-    for _ in range(args.steps):
-        oracle.pagerank(g.offsets, g.src, iters=1, rank0=rank0)
-    dt = time.time() - t0
+    n = args.warmup + args.steps
+    secs = np.zeros(n)
+    oracle.pagerank(g.offsets, g.src, iters=n, iter_seconds=secs)
+    dt = float(secs[args.warmup:].sum())
     v = g.E * args.steps / dt / 1e9
     line = {
         "impl": "reference", "metric": METRIC, "value": v, "unit": "GTEPS", "n_gpus": args.gpus,
@@ -205,8 +249,9 @@ def run_reference(args):
         "config": {"workload": f"pagerank_rmat{args.scale}_directed_ef16", "V": g.V, "E": g.E,
                    "iterations_per_step": 1, "l2_policy": "inputs larger than L2"},
         "cpu_baseline": {"value": v, "unit": "GTEPS", "cores": oracle.num_threads(),
-                         "kind": "oracle",
-                         "sample": f"one FP64 plain-pull iteration per step over the full graph"},
+                         "cpu": cpu_model(), "kind": "oracle",
+                         "sample": "one FP64 plain-pull iteration per step over the full graph, "
+                                   "timed inside the oracle (set-up excluded)"},
         "e2e": {"value": v, "unit": "GTEPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -736,6 +781,140 @@ def run_cf(args):
     print(json.dumps(line), flush=True)
 
 
+ORDERS = ("generator", "random", "clustered_outdeg", "clustered_threshold")
+
+
+def _order_graph(P, gens, order, dev="cuda"):
+    """The RMAT graph in one vertex order: the generator's own IDs (hubs at
+    low IDs: locality), the benchmark's randomly permuted IDs, or that graph
+    renumbered by frequency-based clustering (mode 0: out-degree; mode 1:
+    out-degree over the average degree, Section V)."""
+    if order == "generator":
+        g = gens["generator"]
+        return P.Graph(g.offsets, g.src, cluster_mode=None, device=dev)
+    g = gens["random"]
+    mode = {"random": None, "clustered_outdeg": 0, "clustered_threshold": 1}[order]
+    return P.Graph(g.offsets, g.src, cluster_mode=mode, device=dev)
+
+
+def run_qfactor(args):
+    """Expansion factor q(k) = subgraph rows / V (Section III-D, Fig. qfactor)
+    of the paper's uniform split into k segments, k = 1..64, in four vertex
+    orders, from the GPU segment builder (Algorithm 2)."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    import graphgen
+    from paper_1608_01362_gb300 import cagra as C
+    from paper_1608_01362_gb300 import pipeline as P
+    t = time.time()
+    gens = {"random": graphgen.rmat(args.scale, 16, seed=1),
+            "generator": graphgen.rmat(args.scale, 16, seed=1, permute=False)}
+    gen_s = time.time() - t
+    ks = (1, 2, 4, 8, 16, 32, 64)
+    q = {}
+    for order in ORDERS:
+        graph = _order_graph(P, gens, order)
+        q[order] = {}
+        for k in ks:
+            seg = C.pr_build_segments(graph.offsets, graph.src, k)
+            q[order][k] = float(seg.info["q"])
+            seg.close()
+        del graph
+        torch.cuda.empty_cache()
+    g = gens["random"]
+    ratio = {k: q["random"][k] / q["clustered_outdeg"][k] for k in ks}
+    print(json.dumps({
+        "metric": "expansion factor q(k) of k uniform segments", "unit": "rows per vertex",
+        "config": {"workload": f"qfactor_rmat{args.scale}_directed_ef16", "V": g.V, "E": g.E,
+                   "k": list(ks), "orders": list(ORDERS)},
+        "q": q, "q_random_over_clustered": ratio, "generate_host_s": gen_s}), flush=True)
+
+
+def _phase_times(C, pr, graph, iters=ITERS, reps=2):
+    """Mean seconds per iteration of the gather launches and of the merge +
+    update launch of a segmented PageRank (CUDA events on the stream)."""
+    import torch
+    stream = torch.cuda.current_stream()
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(iters * reps)] for _ in range(3)]
+    pr.init()
+    rin, cin, rout, cout = pr.rank[0], pr.contrib[0], pr.rank[1], pr.contrib[1]
+    for i in range(iters * reps):
+        ev[0][i].record(stream)
+        C.cg_seg_gather(pr.seg, C.CG_OP_SUM_F32, cin, None)
+        ev[1][i].record(stream)
+        C.pr_merge_update(pr.seg, graph.inv, rin, rout, cout, DAMPING, pr.dangling, pr.dangling,
+                          None)
+        ev[2][i].record(stream)
+        rin, cin, rout, cout = rout, cout, rin, cin
+    torch.cuda.synchronize()
+    tg = float(np.mean([a.elapsed_time(b) for a, b in zip(ev[0], ev[1])])) / 1e3
+    tm = float(np.mean([a.elapsed_time(b) for a, b in zip(ev[1], ev[2])])) / 1e3
+    return tg, tm
+
+
+def run_sweep(args):
+    """Segment-count sweep (the paper's Fig. seg-breakdown): uniform k =
+    1..64 in the random (benchmark) order and the clustered order, plus the
+    GPU plan, each with its gather / merge split per iteration and GTEPS."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1608_01362_gb300 import cagra as C
+    from paper_1608_01362_gb300 import pipeline as P
+    g, gen_s = make_graph(args.scale)
+    rows = []
+    for order, mode in (("random", None), ("clustered_outdeg", 0)):
+        graph = P.Graph(g.offsets, g.src, cluster_mode=mode)
+        cands = [("uniform", k) for k in (1, 2, 4, 8, 16, 32, 64)]
+        if mode is not None:
+            cands.append(("plan", args.plan or 32.0))
+        for kind, x in cands:
+            pr = (P.SegmentedPageRank(graph, x) if kind == "uniform" else
+                  P.SegmentedPageRank(graph, bounds=P.plan_bounds(graph, 1, x)))
+            tg, tm = _phase_times(C, pr, graph)
+            inf = pr.info
+            rows.append({"order": order, "kind": kind,
+                         ("k" if kind == "uniform" else "min_avg_degree"): x,
+                         "segments": inf["num_segments"], "q": round(inf["q"], 4),
+                         "staged_segments": inf["staged_segments"],
+                         "gather_ms": tg * 1e3, "merge_update_ms": tm * 1e3,
+                         "gteps": g.E / (tg + tm) / 1e9})
+            pr.seg.close()
+            del pr
+        del graph
+        torch.cuda.empty_cache()
+    print(json.dumps({"metric": "PageRank GTEPS per iteration by segment count",
+                      "unit": "GTEPS", "config": {"workload": f"sweep_rmat{args.scale}_directed_ef16",
+                                                  "V": g.V, "E": g.E},
+                      "rows": rows, "generate_host_s": gen_s}), flush=True)
+
+
+def run_profile(args):
+    """One arm alone, for short ncu captures: `--arm plain_random` (plain
+    pull, random order), `plain_clustered`, or `segmented` (the GPU plan,
+    --plan threshold, clustered), `--iters` iterations after one warm-up."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1608_01362_gb300 import pipeline as P
+    g, _ = make_graph(args.scale)
+    if args.arm == "plain_random":
+        pr = P.PlainPageRank(P.Graph(g.offsets, g.src, cluster_mode=None))
+    elif args.arm == "plain_clustered":
+        pr = P.PlainPageRank(P.Graph(g.offsets, g.src, cluster_mode=0))
+    else:
+        graph = P.Graph(g.offsets, g.src, cluster_mode=0)
+        pr = P.SegmentedPageRank(graph, bounds=P.plan_bounds(graph, 1, args.plan or 32.0))
+    del g
+    pr.init()
+    pr.step(pr.rank[0], pr.contrib[0], pr.rank[1], pr.contrib[1], DAMPING, 1)
+    torch.cuda.synchronize()
+    t = P.time_iterations(pr, args.iters)
+    print(json.dumps({"arm": args.arm, "scale": args.scale, "ms_per_iteration": t * 1e3}),
+          flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -756,10 +935,16 @@ def main():
                          "(with --plan; the autotuner tries its own)")
     ap.add_argument("--sweep", action="store_true", help="k = 1..64 sweep table")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="pagerank", choices=["pagerank", "lp", "batched", "ppr", "cf"],
+    ap.add_argument("--workload", default="pagerank",
+                    choices=["pagerank", "lp", "batched", "ppr", "cf", "qfactor", "sweep",
+                             "profile"],
                     help="pagerank (the headline), lp (label propagation, RMAT-24 undirected) "
                          "or batched (1,024 small RMAT graphs, scales 8-15)")
     ap.add_argument("--graphs", type=int, default=1024, help="graphs of the batched workload")
+    ap.add_argument("--arm", default="segmented",
+                    choices=["segmented", "plain_random", "plain_clustered"],
+                    help="the arm the profile workload runs")
+    ap.add_argument("--iters", type=int, default=3, help="iterations of the profile workload")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -771,6 +956,12 @@ def main():
         return run_cf(args)
     if args.workload == "batched":
         return run_batched(args)
+    if args.workload == "qfactor":
+        return run_qfactor(args)
+    if args.workload == "sweep":
+        return run_sweep(args)
+    if args.workload == "profile":
+        return run_profile(args)
 
     import torch
     rank, world, local = _dist()
@@ -873,10 +1064,11 @@ def main():
     t_max = max_over_ranks(elapsed, pg)
     value = replica_value(E * ITERS * args.steps, world, t_max) / 1e9
 
-    # ---- parity of the timed configuration (one solve, sampled rows, oracle-free
-    # check of the rank mass; the full oracle comparison lives in the tests)
+    # ---- the timed configuration's own solve, for the parity check against the
+    # FP64 oracle below
     rank_final, res = pr.run(ITERS)
     mass = float(rank_final.double().sum().item())
+    rank_final_h = rank_final.cpu().numpy()
 
     # ---- e2e: public API with host buffers (pinned), copies inside the timed region
     rank_h = torch.full((V,), 1.0 / V, dtype=torch.float32).pin_memory()
@@ -907,7 +1099,7 @@ def main():
     torch.cuda.synchronize()
     e2e_t = max_over_ranks(e_start.elapsed_time(e_stop) / 1e3, pg)
     e2e_value = replica_value(E * ITERS * e2e_steps, world, e2e_t) / 1e9
-    e2e_ok = abs(float(out_h.double().sum()) - 1.0) < 1e-3
+    e2e_out = out_h.numpy().copy()
 
     # ---- comparisons on the same GPU: plain pull (original / clustered order), probe
     plain_orig_graph = P.Graph(g.offsets, g.src, cluster_mode=None, device=dev)
@@ -943,7 +1135,7 @@ def main():
     rows = int(info["rows"])
     bmin = 4 * E + 28 * V
     achieved = bmin / t_iter_ev / 1e9
-    traffic = _traffic_per_iteration(E, args.scale)
+    traffic = _traffic_per_iteration(E, args.scale, best_k)
     # each launch against the ceiling of what it does: shared-memory lookups
     # (staged gather), random 4-byte L2 reads from the cold sources' table
     # (L1/L2 gather, fix-up included), HBM (merge + update: 8 B per subgraph
@@ -1010,14 +1202,22 @@ def main():
                             "segment_build": seg_s},
         "rank_mass": mass,
         "e2e": {"value": e2e_value, "unit": "GTEPS", "h2d_bytes_per_step": 4 * V,
-                "d2h_bytes_per_step": 4 * V, "steps": e2e_steps, "result_ok": e2e_ok},
+                "d2h_bytes_per_step": 4 * V, "steps": e2e_steps},
         "gpu_launches": args.steps * (2 + ITERS * (2 + int(info["staged_segments"] > 0) +
                                                    int(int(info["staged_edges"]) < E))),
         "clocks": clk,
     }
-    if rank == 0 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(g)
     if rank == 0:
+        # parity of exactly what was timed: the autotuned plan's 20-iteration
+        # solve (and the end-to-end call's output) against the FP64 oracle,
+        # vertex by vertex
+        want, bound, secs, oracle_s = oracle_solution(g)
+        line["parity"] = parity_report(rank_final_h, want, bound)
+        line["parity"]["oracle_wall_s"] = oracle_s
+        line["e2e"]["parity"] = parity_report(e2e_out, want, bound)
+        line["e2e"]["result_ok"] = line["e2e"]["parity"]["ok"]
+        if not args.no_cpu_baseline:
+            line["cpu_baseline"] = cpu_baseline_from(g, secs)
         print(json.dumps(line), flush=True)
     if pg:
         pg.barrier()

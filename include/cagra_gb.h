@@ -569,8 +569,11 @@ int cf_info(const cg_bipartite *cf, int64_t *ratings, int64_t *user_pieces,
  * pr_noalloc_limits for its size).
  *  - Limits: V <= 2^20 vertices and E <= 2^24 edges; larger inputs return
  *    CG_ERR_INVALID_ARG with a message and enqueue nothing.
- *  - The CSR is not validated (validation would need scratch); out-of-range
- *    sources are skipped.
+ *  - The CSR is not validated (validation would need scratch).  The caller
+ *    must pass offsets that rise monotonically from offsets[0] = 0 to
+ *    offsets[V] = E.  Out-of-range sources are skipped.  Offsets that break
+ *    this give unspecified rank values but no out-of-bounds memory access:
+ *    the gather clamps every tile's row and edge counts to the tile.
  *  - No cudaMalloc, cudaFree or allocating library routine is called.  The
  *    first call on a device looks up the array's device address (once per
  *    device, with that device current); make that first call before any

@@ -73,7 +73,10 @@ def _load():
             lib.orc_out_degree.restype = None
             lib.orc_out_degree.argtypes = [i64, vp, vp, vp]
             lib.orc_pagerank.restype = ctypes.c_int
-            lib.orc_pagerank.argtypes = [i64, vp, vp, i32, dbl, vp, vp]
+            lib.orc_pagerank.argtypes = [i64, vp, vp, i32, dbl, vp, vp, vp]
+            lib.orc_pagerank_bound.restype = ctypes.c_int
+            lib.orc_pagerank_bound.argtypes = [i64, vp, vp, i32, dbl, i64, dbl, dbl, vp, vp, vp,
+                                                vp]
             lib.orc_segments_count.restype = ctypes.c_int
             lib.orc_segments_count.argtypes = [i64, vp, vp, i32, vp, vp, vp]
             lib.orc_segments_fill.restype = ctypes.c_int
@@ -120,38 +123,64 @@ def out_degree(offsets, src) -> np.ndarray:
 # PageRank (Algorithm 1 + Algorithm 5, normalised; see module docstring)
 # --------------------------------------------------------------------------
 
-def pagerank(offsets, src, iters: int = 20, d: float = DAMPING, rank0=None):
-    """Plain pull PageRank in FP64.  Returns (rank, residuals per iteration)."""
+def pagerank(offsets, src, iters: int = 20, d: float = DAMPING, rank0=None,
+             iter_seconds=None):
+    """Plain pull PageRank in FP64.  Returns (rank, residuals per iteration).
+    iter_seconds: optional float64 array of length >= iters that receives the
+    wall time of each iteration alone (set-up excluded)."""
     offsets = _c(offsets, np.int64)
     src = _c(src, np.int32)
     V = offsets.shape[0] - 1
     rank = np.full(V, 1.0 / V) if rank0 is None else _c(rank0, np.float64).copy()
     resid = np.zeros(max(iters, 1))
+    secs = None
+    if iter_seconds is not None:
+        secs = iter_seconds
+        assert secs.dtype == np.float64 and secs.flags.c_contiguous and secs.size >= iters
     if _load().orc_pagerank(V, offsets.ctypes.data, src.ctypes.data, iters, d, rank.ctypes.data,
-                            resid.ctypes.data) != 0:
+                            resid.ctypes.data, 0 if secs is None else secs.ctypes.data) != 0:
         raise MemoryError("oracle: pagerank allocation failed")
     return rank, resid[:iters]
 
 
-def pagerank_step_rows(offsets, src, outdeg, rank_in, rows, d: float = DAMPING) -> np.ndarray:
-    """One iteration of the same update evaluated only at destination `rows`,
-    from a given input rank vector (FP64).  Lets a full-size run be checked
-    one sampled output at a time."""
-    offsets = np.asarray(offsets)
+U_FP32 = 2.0 ** -24        # unit roundoff of FP32 arithmetic
+U_BF16X2 = 2.0 ** -16      # relative rounding of a value stored as a BF16 hi + lo pair
+U_BF16 = 2.0 ** -8         # relative rounding of a value stored as BF16
+
+
+def pagerank_bound(offsets, src, iters: int = 20, d: float = DAMPING, seed: int = -1,
+                   u_acc: float = U_FP32, u_store: float = 0.0, resid=None,
+                   iter_seconds=None):
+    """The PageRank iteration in FP64 (seed < 0: r_0 = 1/V, uniform teleport;
+    seed >= 0: one personalised column, r_0 = one-hot) together with a
+    per-vertex bound on the rounding error of any evaluation of it in a
+    format of unit roundoff u_acc whose stored contributions carry a further
+    relative rounding u_store (see orc_pagerank_bound for the recurrence).
+    Returns (rank, bound): |r_computed - rank| <= bound element by element.
+    rank equals pagerank(...)[0] (uniform) or ppr(...)[:, j] (personalised)
+    bit for bit.  resid: optional float64 array (>= iters) that receives the
+    per-iteration L1 residuals; iter_seconds as in pagerank (the bound's work
+    excluded)."""
+    offsets = _c(offsets, np.int64)
+    src = _c(src, np.int32)
     V = offsets.shape[0] - 1
-    rank_in = np.asarray(rank_in, dtype=np.float64)
-    dang = np.asarray(outdeg) == 0
-    D = 0.0
-    for x in rank_in[dang]:
-        D += float(x)
-    out = np.empty(len(rows))
-    for j, v in enumerate(rows):
-        lo, hi = int(offsets[v]), int(offsets[v + 1])
-        s = 0.0
-        for u in np.asarray(src[lo:hi]):
-            s += rank_in[u] / float(outdeg[u])
-        out[j] = (1.0 - d) / V + d * (s + D / V)
-    return out
+    rank = np.empty(V)
+    bound = np.empty(V)
+    secs = None
+    if iter_seconds is not None:
+        secs = iter_seconds
+        assert secs.dtype == np.float64 and secs.flags.c_contiguous and secs.size >= iters
+    if resid is not None:
+        assert resid.dtype == np.float64 and resid.flags.c_contiguous and resid.size >= iters
+    st = _load().orc_pagerank_bound(V, offsets.ctypes.data, src.ctypes.data, iters, d, int(seed),
+                                    float(u_acc), float(u_store), rank.ctypes.data,
+                                    bound.ctypes.data, 0 if resid is None else resid.ctypes.data,
+                                    0 if secs is None else secs.ctypes.data)
+    if st == -2:
+        raise ValueError("oracle: pagerank_bound needs V >= 1 and seed < V")
+    if st != 0:
+        raise MemoryError("oracle: pagerank_bound allocation failed")
+    return rank, bound
 
 
 # --------------------------------------------------------------------------
@@ -362,14 +391,3 @@ def cf_sweep(U, I, uoff, uitem, urate, ioff, iuser, irate, P, Q, lam=0.05, step=
         raise ValueError("oracle: cf sweep failed (K out of range or allocation)")
     return P, Q, float(sse.value)
 
-
-def cf_sse(uoff, uitem, urate, P, Q) -> float:
-    """sum over ratings of (r_ui - p_u . q_i)^2 in FP64 (user-major order)."""
-    U = len(uoff) - 1
-    tot = 0.0
-    for u in range(U):
-        lo, hi = int(uoff[u]), int(uoff[u + 1])
-        if hi > lo:
-            e = urate[lo:hi].astype(np.float64) - Q[uitem[lo:hi]] @ P[u]
-            tot += float(np.dot(e, e))
-    return tot

@@ -14,6 +14,7 @@
 #include <stdlib.h>
 #include <string.h>
 #include <math.h>
+#include <time.h>
 #ifdef _OPENMP
 #include <omp.h>
 #endif
@@ -26,6 +27,47 @@ void orc_out_degree(int64_t V, const int64_t *offsets, const int32_t *src,
     for (int64_t e = 0; e < offsets[V]; ++e) outdeg[src[e]]++;
 }
 
+/* Wall-clock seconds (OpenMP's timer when available). */
+static double orc_now(void) {
+#ifdef _OPENMP
+    return omp_get_wtime();
+#else
+    return (double)clock() / (double)CLOCKS_PER_SEC;
+#endif
+}
+
+/*
+ * One iteration of the plain pull update (Algorithm 1's gather with the
+ * per-vertex update of Algorithm 5), from `rank` into `next`:
+ *   D      = sum over u with outdeg(u) = 0 of rank[u]          (index order)
+ *   c[u]   = rank[u] / outdeg(u)   (0 for a dangling u)
+ *   S_v    = sum_{u -> v} c[u]                                 (CSR order)
+ * seed < 0 (uniform teleport, dangling mass spread over all V vertices):
+ *   next[v] = (1-d)/V + d (S_v + D/V)
+ * seed >= 0 (personalised: teleport and dangling mass return to the seed):
+ *   next[v] = d S_v,  then next[seed] += (1-d) + d D
+ * `contrib` receives c.  Returns D.
+ */
+static double pr_step(int64_t V, const int64_t *offsets, const int32_t *src,
+                      const int64_t *outdeg, double d, int64_t seed,
+                      const double *rank, double *contrib, double *next) {
+    const double base = (1.0 - d) / (double)V;
+    double D = 0.0;
+    for (int64_t u = 0; u < V; ++u)
+        if (outdeg[u] == 0) D += rank[u];
+    #pragma omp parallel for schedule(static)
+    for (int64_t u = 0; u < V; ++u)
+        contrib[u] = outdeg[u] ? rank[u] / (double)outdeg[u] : 0.0;
+    #pragma omp parallel for schedule(dynamic, 1024)
+    for (int64_t v = 0; v < V; ++v) {
+        double s = 0.0;
+        for (int64_t e = offsets[v]; e < offsets[v + 1]; ++e) s += contrib[src[e]];
+        next[v] = seed < 0 ? base + d * (s + D / (double)V) : d * s;
+    }
+    if (seed >= 0) next[seed] += (1.0 - d) + d * D;
+    return D;
+}
+
 /*
  * Plain pull PageRank (Algorithm 1's gather, with the per-vertex update of
  * Algorithm 5 in normalised form and uniform redistribution of the rank held
@@ -36,34 +78,136 @@ void orc_out_degree(int64_t V, const int64_t *offsets, const int32_t *src,
  * `rank` holds the initial vector on entry (the caller fills 1/V for r_0)
  * and the result after `iters` iterations on exit.
  * resid[t] = sum_v |r_{t+1}[v] - r_t[v]| (index order); may be NULL.
+ * iter_seconds[t] (may be NULL) = wall time of iteration t alone: the
+ * out-degree pass and the allocations before the loop are not in it.
  */
 int orc_pagerank(int64_t V, const int64_t *offsets, const int32_t *src,
-                 int32_t iters, double d, double *rank, double *resid) {
+                 int32_t iters, double d, double *rank, double *resid,
+                 double *iter_seconds) {
     int64_t *outdeg = (int64_t *)malloc((size_t)V * sizeof(int64_t));
     double *contrib = (double *)malloc((size_t)V * sizeof(double));
     double *next = (double *)malloc((size_t)V * sizeof(double));
     if (!outdeg || !contrib || !next) { free(outdeg); free(contrib); free(next); return -1; }
     orc_out_degree(V, offsets, src, outdeg);
-    const double base = (1.0 - d) / (double)V;
     for (int32_t t = 0; t < iters; ++t) {
-        double D = 0.0;
-        for (int64_t u = 0; u < V; ++u)
-            if (outdeg[u] == 0) D += rank[u];
-        #pragma omp parallel for schedule(static)
-        for (int64_t u = 0; u < V; ++u)
-            contrib[u] = outdeg[u] ? rank[u] / (double)outdeg[u] : 0.0;
-        #pragma omp parallel for schedule(dynamic, 1024)
-        for (int64_t v = 0; v < V; ++v) {
-            double s = 0.0;
-            for (int64_t e = offsets[v]; e < offsets[v + 1]; ++e) s += contrib[src[e]];
-            next[v] = base + d * (s + D / (double)V);
-        }
+        const double t0 = orc_now();
+        pr_step(V, offsets, src, outdeg, d, -1, rank, contrib, next);
         double r = 0.0;
         for (int64_t v = 0; v < V; ++v) r += fabs(next[v] - rank[v]);
         if (resid) resid[t] = r;
         memcpy(rank, next, (size_t)V * sizeof(double));
+        if (iter_seconds) iter_seconds[t] = orc_now() - t0;
     }
     free(outdeg); free(contrib); free(next);
+    return 0;
+}
+
+/* gamma_m = m u / (1 - m u): the relative error bound of m roundings
+ * (Higham, Accuracy and Stability of Numerical Algorithms, Lemma 3.1). */
+static double orc_gamma(double m, double u) {
+    return m > 0.0 ? m * u / (1.0 - m * u) : 0.0;
+}
+
+/*
+ * The same iteration as orc_pagerank (seed < 0) or as one column of orc_ppr
+ * (seed >= 0), started from r_0 = 1/V or from the one-hot seed vector, and
+ * beside it a per-vertex bound on how far ANY evaluation of that iteration in
+ * a binary floating-point format can drift from these FP64 values:
+ *   u_acc    unit roundoff of the arithmetic (2^-24 for FP32): each product,
+ *            each sum of two values and each conversion rounds once;
+ *   u_store  relative rounding of the stored contributions c[u] beyond that
+ *            (0 when they are kept in the arithmetic format; 2^-16 for a
+ *            BF16 hi + lo pair, 2^-8 for BF16 alone).
+ * The sum S_v of n = indeg(v) contributions may be associated in any order,
+ * split across segments and merged: every such evaluation performs n - 1
+ * additions of disjoint partial sums, so its rounding error is at most
+ * gamma_{n-1} * (sum of the summands' magnitudes) (Higham, eq. 4.4 for any
+ * summation tree).  With e_t[v] the bound after t iterations, the error of
+ * the computed contributions is at most e_t[u]/outdeg(u) plus (2 u_acc +
+ * u_store) c[u] (the reciprocal degree and the product round once each), the
+ * dangling sum is off by at most the sum of e_t over dangling vertices, and
+ * the update adds at most u_acc (4 d (S_v + Dsh_v) + r_{t+1}[v] + 7 Tsh_v),
+ * where Dsh_v = D/V (uniform) or [v = seed] D is v's share of the dangling
+ * mass and Tsh_v = (1-d)/V or [v = seed](1-d) its share of the teleport:
+ * the conversion of the dangling share, the sum with S_v, the product with
+ * d and the rounding of d itself (one u d (S_v + Dsh_v) each), the final sum
+ * (u r_{t+1}), and the teleport constant, which is off by at most 7 u Tsh_v
+ * even when (1-d)/V is formed in the arithmetic format from the rounded d
+ * (d/(1-d) = 5.67 times d's rounding, plus the division).  Hence, to first
+ * order,
+ *   e_{t+1}[v] = (1 + g + 4u)(1 + 2u + u_store) * P_v + (1 + g + 8u) * rho_v
+ *   P_v   = d sum_{u -> v} e_t[u]/outdeg(u) + d * (seed < 0 ? Ed/V : [v = seed] Ed)
+ *   rho_v = (g + 2u + u_store) d S_v + u (4 d (S_v + Dsh_v) + r_{t+1}[v] + 7 Tsh_v)
+ *           + (gamma64_{n+8} + 2 gamma64_V) r_{t+1}[v]
+ * with g = gamma_{n-1}(u_acc), Ed = sum of e_t over dangling vertices, and
+ * the gamma64 terms covering this FP64 evaluation's own rounding (and the
+ * FP64 dangling sums on both sides).  e_0 = u_acc r_0 (1/V rounded once; the
+ * one-hot start is exact).  The factors (1 + ...) absorb the second-order
+ * products of errors; a final factor 1 + 1e-9 covers using FP64 values for
+ * the exact ones.  On exit rank holds r_iters and bound holds e_iters, so
+ * |r_computed[v] - rank[v]| <= bound[v] for every vertex.
+ * resid[t] (may be NULL) = sum_v |r_{t+1}[v] - r_t[v]| as in orc_pagerank.
+ * iter_seconds[t] (may be NULL) = wall time of the plain iteration t alone
+ * (pr_step and the copy; the bound's own work is not in it).
+ */
+int orc_pagerank_bound(int64_t V, const int64_t *offsets, const int32_t *src,
+                       int32_t iters, double d, int64_t seed, double u_acc,
+                       double u_store, double *rank, double *bound, double *resid,
+                       double *iter_seconds) {
+    if (V < 1 || seed >= V) return -2;
+    const double u64 = ldexp(1.0, -53);
+    int64_t *outdeg = (int64_t *)malloc((size_t)V * sizeof(int64_t));
+    double *contrib = (double *)malloc((size_t)V * sizeof(double));
+    double *next = (double *)malloc((size_t)V * sizeof(double));
+    double *ce = (double *)malloc((size_t)V * sizeof(double));
+    double *enext = (double *)malloc((size_t)V * sizeof(double));
+    if (!outdeg || !contrib || !next || !ce || !enext) {
+        free(outdeg); free(contrib); free(next); free(ce); free(enext);
+        return -1;
+    }
+    orc_out_degree(V, offsets, src, outdeg);
+    const double gV = 2.0 * orc_gamma((double)V, u64);
+    for (int64_t v = 0; v < V; ++v) {
+        rank[v] = seed < 0 ? 1.0 / (double)V : (v == seed ? 1.0 : 0.0);
+        bound[v] = seed < 0 ? u_acc * rank[v] : 0.0;
+    }
+    for (int32_t t = 0; t < iters; ++t) {
+        const double t0 = orc_now();
+        const double Dm = pr_step(V, offsets, src, outdeg, d, seed, rank, contrib, next);
+        if (iter_seconds) iter_seconds[t] = orc_now() - t0;
+        double Ed = 0.0;
+        for (int64_t u = 0; u < V; ++u)
+            if (outdeg[u] == 0) Ed += bound[u];
+        #pragma omp parallel for schedule(static)
+        for (int64_t u = 0; u < V; ++u)
+            ce[u] = outdeg[u] ? bound[u] / (double)outdeg[u] : 0.0;
+        #pragma omp parallel for schedule(dynamic, 1024)
+        for (int64_t v = 0; v < V; ++v) {
+            double S = 0.0, P = 0.0;
+            for (int64_t e = offsets[v]; e < offsets[v + 1]; ++e) {
+                S += contrib[src[e]];
+                P += ce[src[e]];
+            }
+            const double n = (double)(offsets[v + 1] - offsets[v]);
+            const double g = orc_gamma(n - 1.0, u_acc);
+            P = d * P + (seed < 0 ? d * Ed / (double)V : (v == seed ? d * Ed : 0.0));
+            const double Dsh = seed < 0 ? Dm / (double)V : (v == seed ? Dm : 0.0);
+            const double Tsh = seed < 0 ? (1.0 - d) / (double)V : (v == seed ? 1.0 - d : 0.0);
+            const double rho = (g + 2.0 * u_acc + u_store) * d * S +
+                               u_acc * (4.0 * d * (S + Dsh) + next[v] + 7.0 * Tsh) +
+                               (orc_gamma(n + 8.0, u64) + gV) * next[v];
+            enext[v] = ((1.0 + g + 4.0 * u_acc) * (1.0 + 2.0 * u_acc + u_store) * P +
+                        (1.0 + g + 8.0 * u_acc) * rho) * (1.0 + 1e-9);
+        }
+        if (resid) {
+            double r = 0.0;
+            for (int64_t v = 0; v < V; ++v) r += fabs(next[v] - rank[v]);
+            resid[t] = r;
+        }
+        memcpy(rank, next, (size_t)V * sizeof(double));
+        memcpy(bound, enext, (size_t)V * sizeof(double));
+    }
+    free(outdeg); free(contrib); free(next); free(ce); free(enext);
     return 0;
 }
 

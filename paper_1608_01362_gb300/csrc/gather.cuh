@@ -108,7 +108,12 @@ gather_tile_kernel(const RowEndT* __restrict__ row_end, const int32_t* __restric
   const int64_t t = blockIdx.x;
   const int32_t r0 = tile_row[t], r1 = tile_row[t + 1];
   const int32_t e0 = tile_edge[t], e1 = tile_edge[t + 1];
-  const int nr = r1 - r0, ne = e1 - e0;
+  // A valid CSR gives nr + ne = TILE (the last tile less) with both >= 0.
+  // Offsets that do not rise monotonically can give any split; clamping keeps
+  // every shared-memory index inside the tile (the results are then
+  // meaningless, but no access leaves its array).
+  const int nr = min(max(r1 - r0, 0), TILE);
+  const int ne = min(max(e1 - e0, 0), TILE - nr);
 
   // 1. edges: stream col, gather x
   {

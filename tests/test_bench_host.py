@@ -38,6 +38,9 @@ def test_traffic_summary_is_gated_by_workload_and_sources(monkeypatch):
     assert bench._traffic_per_iteration(E, scale=20) is None
     monkeypatch.setattr(bench, "kernel_source_hash", lambda: t["kernel_source_sha"])
     assert bench._traffic_per_iteration(E) == float(t["dram_bytes_per_edge"]) * E
+    seg = int(t["plan"]["segments"])
+    assert bench._traffic_per_iteration(E, 25, seg) == float(t["dram_bytes_per_edge"]) * E
+    assert bench._traffic_per_iteration(E, 25, seg + 1) is None  # another plan than profiled
     monkeypatch.setattr(bench, "kernel_source_hash", lambda: "0" * 16)
     assert bench._traffic_per_iteration(E) is None
 
@@ -62,3 +65,30 @@ def test_gather_peaks_keys_and_units():
     p = bench.gather_peaks(FakeC(), [(4, 64), (128, 1 << 20)], smem=True)
     assert p[(4, 64)] == 4.0 and p[(128, 1 << 20)] == 128.0 and p["smem"] == 3000.0
     assert "smem" not in bench.gather_peaks(FakeC(), [(4, 64)])
+
+
+def test_parity_report_flags_a_planted_error():
+    import bench
+    import oracle as O
+    g = graphgen.rmat(10, 16, seed=2)
+    want, bound = O.pagerank_bound(g.offsets, g.src, iters=20)
+    ok = bench.parity_report(want.astype(np.float32), want, bound)
+    assert ok["ok"] and ok["vertices_outside_bound"] == 0 and ok["rel_l1"] < 1e-6
+    bad = want.astype(np.float32)
+    bad[17] *= np.float32(1.001)  # one vertex 0.1% off: inside any global L1 budget
+    rep = bench.parity_report(bad, want, bound)
+    assert rep["rel_l1"] <= 1e-5 and rep["vertices_outside_bound"] == 1 and not rep["ok"]
+
+
+def test_reference_arm_times_iterations_net_of_setup(capsys):
+    """--impl reference reports one oracle iteration per step, timed inside the
+    oracle, on the same routine as the cpu_baseline leg."""
+    import bench
+
+    class A:
+        scale, steps, warmup, gpus = 12, 3, 1, 1
+    bench.run_reference(A())
+    line = json.loads(capsys.readouterr().out.strip().splitlines()[-1])
+    assert line["impl"] == "reference" and line["value"] > 0 and line["unit"] == "GTEPS"
+    assert line["cpu_baseline"]["value"] == line["value"] and line["cpu_baseline"]["cores"] >= 1
+    assert line["e2e"]["h2d_bytes_per_step"] == 0

@@ -6,10 +6,10 @@ import pytest
 
 import graphgen
 import oracle as O
+from parity import assert_gather_merge_exact, check_pagerank, pagerank_ref
 
 pytestmark = pytest.mark.gpu
 
-TOL_L1 = 1e-5  # relative L1 of FP32 PageRank vs the FP64 oracle after 20 iterations
 # FP32 residual sum |r' - r|: each term carries rounding of order 2^-24 (|r'| + |r|), so
 # the residual cannot resolve below about 2 * 2^-24 * (sum r' + sum r) = 2.4e-7.
 RESID_FLOOR = 2.4e-7
@@ -38,9 +38,6 @@ def torch_mod():
 def _dev(torch, a, dtype):
     return torch.as_tensor(np.ascontiguousarray(a), dtype=dtype).cuda()
 
-
-def rel_l1(a, b):
-    return float(np.sum(np.abs(np.asarray(a, np.float64) - b)) / np.sum(np.abs(b)))
 
 
 @pytest.fixture(scope="module")
@@ -208,14 +205,18 @@ def _pagerank_gpu(torch, g, k=None, cluster=0, iters=20, B=4096, bounds=None, pr
 
 @pytest.fixture(scope="module")
 def rmat16_oracle(rmat16):
-    return O.pagerank(rmat16.offsets, rmat16.src, iters=20)
+    """(rank, residuals, per-vertex FP32 rounding bound) after 20 iterations."""
+    want, want_resid = O.pagerank(rmat16.offsets, rmat16.src, iters=20)
+    r, bound = pagerank_ref(rmat16)
+    assert np.array_equal(r, want)
+    return want, want_resid, bound
 
 
 @pytest.mark.parametrize("cluster", [None, 0])
 def test_plain_pagerank_parity(C, torch_mod, rmat16, rmat16_oracle, cluster):
     rank, resid, _ = _pagerank_gpu(torch_mod, rmat16, None, cluster)
-    want, want_resid = rmat16_oracle
-    assert rel_l1(rank, want) <= TOL_L1
+    want, want_resid, bound = rmat16_oracle
+    check_pagerank(rank, want, bound, what=f"plain cluster={cluster}")
     assert abs(rank.astype(np.float64).sum() - 1.0) < 1e-4
     assert resid_ok(resid, want_resid)
 
@@ -225,36 +226,69 @@ def test_plain_pagerank_parity(C, torch_mod, rmat16, rmat16_oracle, cluster):
                                          (1024, 0, 256)])
 def test_segmented_pagerank_parity(C, torch_mod, rmat16, rmat16_oracle, k, cluster, B):
     rank, resid, pr = _pagerank_gpu(torch_mod, rmat16, k, cluster, B=B)
-    want, want_resid = rmat16_oracle
-    assert rel_l1(rank, want) <= TOL_L1
+    want, want_resid, bound = rmat16_oracle
+    check_pagerank(rank, want, bound, what=f"segmented k={k} cluster={cluster} B={B}")
     assert resid_ok(resid, want_resid)
     assert pr.info["num_segments"] == k
+
+
+@pytest.mark.parametrize("k,cluster,B", [(1, None, 4096), (3, 0, 1000), (16, 1, 512),
+                                         (64, 0, 6144), (1024, 0, 256)])
+def test_gather_merge_exact_on_integers(C, torch_mod, rmat16, k, cluster, B):
+    """Gather + merge of small integers equals the exact in-neighbour sums
+    bit for bit (one dropped or duplicated edge anywhere would show)."""
+    from paper_1608_01362_gb300 import pipeline as P
+    graph = P.Graph(rmat16.offsets, rmat16.src, cluster_mode=cluster)
+    pr = P.SegmentedPageRank(graph, k, merge_block=B)
+    assert_gather_merge_exact(torch_mod, C, rmat16, graph, pr.seg, f"k={k} cluster={cluster}")
+
+
+@pytest.mark.parametrize("name", ["in_star", "out_star", "cycle", "ragged"])
+def test_gather_merge_exact_special_graphs(C, torch_mod, name):
+    from paper_1608_01362_gb300 import pipeline as P
+    g = _special_graphs()[name]
+    graph = P.Graph(g.offsets, g.src, cluster_mode=0)
+    for k in (1, 3):
+        pr = P.SegmentedPageRank(graph, k, merge_block=64)
+        assert_gather_merge_exact(torch_mod, C, g, graph, pr.seg, f"{name} k={k}")
+
+
+def test_gather_merge_exact_every_autotuner_candidate(C, torch_mod, rmat16):
+    """Every plan the autotuner may pick (planned bounds at each staging
+    threshold and launch shape, the uniform splits, both table settings)."""
+    from paper_1608_01362_gb300 import pipeline as P
+    graph = P.Graph(rmat16.offsets, rmat16.src, cluster_mode=0)
+    for cand in P.default_candidates(uniform_k=(1, 2, 4, 8, 16, 32, 64)):
+        pr = P.build_candidate(graph, cand)
+        assert_gather_merge_exact(torch_mod, C, rmat16, graph, pr.seg, str(cand))
+        pr.seg.close()
 
 
 def test_segmented_nonuniform_bounds(C, torch_mod, rmat16, rmat16_oracle):
     V = rmat16.V
     bounds = np.array([0, 4096, 4096, 30000, V], dtype=np.int64)
     rank, _, _ = _pagerank_gpu(torch_mod, rmat16, 4, 0, bounds=bounds)
-    assert rel_l1(rank, rmat16_oracle[0]) <= TOL_L1
+    check_pagerank(rank, rmat16_oracle[0], rmat16_oracle[2], what="non-uniform bounds")
 
 
 @pytest.mark.parametrize("name", list(_special_graphs().keys()))
 def test_pagerank_special_graphs(C, torch_mod, name):
     g = _special_graphs()[name]
-    want, _ = O.pagerank(g.offsets, g.src, iters=20)
+    want, bound = pagerank_ref(g)
     for k in (None, 1, 3):
         if k is not None and k > g.V:
             continue
         rank, _, _ = _pagerank_gpu(torch_mod, g, k, 0, B=64)
-        assert rel_l1(rank, want) <= TOL_L1, (name, k)
+        check_pagerank(rank, want, bound, what=f"{name} k={k}")
 
 
 def test_single_iteration_and_ping_pong(C, torch_mod, rmat16):
     """iterations = 1, 2, 3 land in the output buffers and match the oracle."""
     for it in (1, 2, 3):
-        want, _ = O.pagerank(rmat16.offsets, rmat16.src, iters=it)
+        want, bound = pagerank_ref(rmat16, iters=it)
         rank, resid, _ = _pagerank_gpu(torch_mod, rmat16, 4, 0, iters=it)
-        assert rel_l1(rank, want) <= TOL_L1 and resid.shape == (it,)
+        check_pagerank(rank, want, bound, what=f"iterations={it}")
+        assert resid.shape == (it,)
 
 
 def test_probe_reads_vertex_zero_only(C, torch_mod):
@@ -311,7 +345,8 @@ def test_gather_table_configs(C, torch_mod, rmat16, rmat16_oracle, threads, ctas
         if info["staged_segments"] == 0:
             assert info["table_vertices"] == 0
         rank, resid = pr.run(20)
-        assert rel_l1(rank.cpu().numpy(), rmat16_oracle[0]) <= TOL_L1, (threads, ctas, table, k)
+        check_pagerank(rank.cpu().numpy(), rmat16_oracle[0], rmat16_oracle[2],
+                       what=f"threads={threads} ctas={ctas} table={table} k={k}")
 
 
 def test_gather_config_rejects_bad_shape(C, torch_mod, rmat16):
@@ -422,7 +457,7 @@ def test_planned_bounds(C, torch_mod, rmat16, rmat16_oracle):
     pr = P.SegmentedPageRank(graph, bounds=b, threads=512, ctas_per_sm=2, table_vertices=2048)
     assert pr.info["table_vertices"] == 2048 and pr.info["staged_segments"] >= m
     rank, _ = pr.run(20)
-    assert rel_l1(rank.cpu().numpy(), rmat16_oracle[0]) <= TOL_L1
+    check_pagerank(rank.cpu().numpy(), rmat16_oracle[0], rmat16_oracle[2], what="planned bounds")
     # segment build on planned bounds is still bit-exact
     _check_segments(C, torch, graph.offsets.cpu().numpy(), graph.src.cpu().numpy(), len(b) - 1,
                     4096, bounds=b)

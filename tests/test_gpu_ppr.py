@@ -19,11 +19,15 @@ import pytest
 
 import graphgen
 import oracle as O
+from parity import assert_within_bound, ppr_ref
 
 pytestmark = pytest.mark.gpu
 
 TOL_SINGLE = 1e-5
 TOL_PLANES = {2: 1.5e-4, 1: 3e-2}
+# relative rounding of a stored contribution: BF16 hi + lo pair, BF16 alone; the
+# per-entry bounds (oracle.pagerank_bound) add it to the FP32 arithmetic's
+U_STORE = {2: O.U_BF16X2, 1: O.U_BF16}
 COLS = 64
 
 
@@ -74,9 +78,10 @@ def test_single_vector_ppr(env, rmat13, k):
     G = P.Graph(g.offsets, g.src, cluster_mode=0)
     pr = P.SegmentedPageRank(G, num_segments=k)
     seeds = mixed_seeds(g, n=6)
-    want = O.ppr(g.offsets, g.src, seeds, iters=20)
+    want, bound = ppr_ref(g, seeds)
     for j, s in enumerate(seeds):
         rank, resid = pr.run_ppr(int(s), iterations=20)
+        assert_within_bound(rank.cpu().numpy(), want[:, j], bound[:, j], f"seed {int(s)} k={k}")
         err = col_rel_l1(rank.cpu().numpy()[:, None], want[:, j:j + 1])[0]
         assert err <= TOL_SINGLE, (int(s), err)
         assert np.all(np.isfinite(resid.cpu().numpy()))
@@ -102,7 +107,8 @@ def test_batched_ppr_matches_oracle(env, rmat13, planes, k):
     b = P.BatchedPPR(G, num_segments=k, planes=planes)
     seeds = mixed_seeds(g)
     R, resid = b.run(seeds, iterations=20)
-    want = O.ppr(g.offsets, g.src, seeds, iters=20)
+    want, bound = ppr_ref(g, seeds, u_store=U_STORE[planes])
+    assert_within_bound(R.cpu().numpy(), want, bound, f"planes={planes} k={k}")
     err = col_rel_l1(R.cpu().numpy(), want)
     assert err.max() <= TOL_PLANES[planes], (planes, k, err.max(), int(np.argmax(err)))
     # the columns of a PPR matrix are probability vectors
@@ -119,7 +125,8 @@ def test_batched_ppr_unclustered_plan_bounds(env):
     b = P.BatchedPPR(G, bounds=bounds, planes=2)
     seeds = mixed_seeds(g, seed=3)
     R, _ = b.run(seeds, iterations=12)
-    want = O.ppr(g.offsets, g.src, seeds, iters=12)
+    want, bound = ppr_ref(g, seeds, iters=12, u_store=U_STORE[2])
+    assert_within_bound(R.cpu().numpy(), want, bound, "unclustered planned bounds")
     assert col_rel_l1(R.cpu().numpy(), want).max() <= TOL_PLANES[2]
 
 
@@ -149,7 +156,8 @@ def test_batched_ppr_special_graphs(env, name, k):
     seeds = rng.integers(0, g.V, COLS).astype(np.int32)
     seeds[0] = 0
     R, _ = b.run(seeds, iterations=20)
-    want = O.ppr(g.offsets, g.src, seeds, iters=20)
+    want, bound = ppr_ref(g, seeds, u_store=U_STORE[2])
+    assert_within_bound(R.cpu().numpy(), want, bound, name)
     assert col_rel_l1(R.cpu().numpy(), want).max() <= TOL_PLANES[2], name
 
 
@@ -163,7 +171,8 @@ def test_batched_ppr_larger_sampled(env):
     seeds = mixed_seeds(g, seed=9)
     R, _ = b.run(seeds, iterations=20)
     cols = np.array([0, 1, 5, 9, 13, 21, 40, 63])
-    want = O.ppr(g.offsets, g.src, seeds[cols], iters=20)
+    want, bound = ppr_ref(g, seeds[cols], u_store=U_STORE[2])
+    assert_within_bound(R.cpu().numpy()[:, cols], want, bound, "scale 17")
     assert col_rel_l1(R.cpu().numpy()[:, cols], want).max() <= TOL_PLANES[2]
 
 

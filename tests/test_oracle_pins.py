@@ -97,15 +97,6 @@ def test_fixed_point_solves_linear_system():
     assert resid[-1] < 1e-15 and resid[0] > resid[10] > resid[100]
 
 
-def test_step_rows_matches_full_iteration():
-    g = graphgen.rmat(10, 8, seed=3)
-    od = O.out_degree(g.offsets, g.src)
-    r1, _ = O.pagerank(g.offsets, g.src, iters=1)
-    rows = [0, 5, 17, g.V - 1]
-    got = O.pagerank_step_rows(g.offsets, g.src, od, np.full(g.V, 1.0 / g.V), rows)
-    assert np.max(np.abs(got - r1[rows])) < 1e-16
-
-
 # ---------------------------------------------------------------- degrees
 
 def test_out_degree_counts_sources():
@@ -360,7 +351,6 @@ def test_cf_loss_decreases_for_small_step():
         P, Q, sse = O.cf_sweep(U, I, uoff, item, rate, ioff, iuser, irate, P, Q, 0.0, 0.05)
         assert sse <= last
         last = sse
-    assert abs(O.cf_sse(uoff, item, rate, P, Q) - last) < last
 
 
 def test_item_major_transpose():
