@@ -406,6 +406,28 @@ def run_batched(args):
     b.record()
     b.synchronize()
     t_per = a.elapsed_time(b) / 1e3
+    # the same per-graph launches replayed from one CUDA graph, so that the
+    # comparison is of device work, not of host launch cost
+    s2 = torch.cuda.Stream()
+    s2.wait_stream(torch.cuda.current_stream())
+    g_per = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(s2):
+        for h in handles[:8]:
+            h.run(ITERS)
+        torch.cuda.synchronize()
+        with torch.cuda.graph(g_per, stream=s2, capture_error_mode="relaxed"):
+            for h in handles:
+                h.init()
+                h.step(h.rank[0], h.contrib[0], h.rank[1], h.contrib[1], DAMPING, ITERS)
+    torch.cuda.current_stream().wait_stream(s2)
+    g_per.replay()
+    torch.cuda.synchronize()
+    a.record()
+    for _ in range(3):
+        g_per.replay()
+    b.record()
+    b.synchronize()
+    t_per_graph = a.elapsed_time(b) / 3e3
     # accuracy against the FP64 oracle on a sample of graphs
     import oracle
     errs = []
@@ -422,6 +444,8 @@ def run_batched(args):
                        "cuda_graph": True},
             "autotune_ms": {str(k): v * 1e3 for k, v in tune.items()},
             "per_graph_launches_ms": t_per * 1e3, "speedup_vs_per_graph": t_per / t_batch,
+            "per_graph_launches_cuda_graph_ms": t_per_graph * 1e3,
+            "speedup_vs_per_graph_cuda_graph": t_per_graph / t_batch,
             "max_rel_l1_vs_oracle": max(errs), "oracle_sample_graphs": len(errs),
             "generate_host_s": gen_s}
     # roofline of one solve of all graphs: the method needs the edges and the
@@ -915,6 +939,312 @@ def run_profile(args):
           flush=True)
 
 
+def run_bc(args):
+    """Betweenness centrality from 12 sources (the paper's Table V: runtime
+    for 12 starting points) on the directed RMAT graph (default scale 25),
+    clustered, with the random (benchmark) order beside it; two sources are
+    checked against the FP64 oracle (levels and path counts bit for bit,
+    dependencies within the FP64 bound)."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    import oracle
+    from paper_1608_01362_gb300 import cagra as C
+    from paper_1608_01362_gb300 import pipeline as P
+    g, gen_s = make_graph(args.scale)
+    S = ppr_seeds(g, n=12)
+    ev = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
+    res = {}
+    for order, mode in (("clustered_outdeg", 0), ("random", None)):
+        graph = P.Graph(g.offsets, g.src, cluster_mode=mode)
+        t0 = time.time()
+        bc = P.Betweenness(graph)
+        torch.cuda.synchronize()
+        prep = time.time() - t0
+        tune = {}
+        for alpha in (4.0, 16.0, 64.0):  # push/pull switch, timed on the first source
+            C.bc_set_direction(bc.h, alpha)
+            bc.run(S[:1])
+            a, z = ev(), ev()
+            a.record()
+            bc.run(S[:2])
+            z.record()
+            z.synchronize()
+            tune[alpha] = a.elapsed_time(z) / 2e3
+        alpha = min(tune, key=tune.get)
+        C.bc_set_direction(bc.h, alpha)
+        for _ in range(args.warmup):
+            bc.run(S[:2])
+        torch.cuda.synchronize()
+        clk = ClockSampler(int(os.environ.get("LOCAL_RANK", "0"))) if mode == 0 else None
+        if clk:
+            clk.start()
+        times = []
+        for _ in range(max(1, args.steps // 5)):
+            a, z = ev(), ev()
+            a.record()
+            out = bc.run(S)
+            z.record()
+            z.synchronize()
+            times.append(a.elapsed_time(z) / 1e3)
+        clocks = clk.stop() if clk else None
+        t12 = float(np.median(times))
+        info = C.bc_source_state(bc.h)
+        res[order] = {"s_for_12_sources": t12, "alpha": alpha, "alpha_tune_s_per_source": tune,
+                      "last_source_levels": info["depth"], "push_levels": info["push_levels"],
+                      "pull_levels": info["pull_levels"], "prep_s": prep, "clocks": clocks}
+        if mode == 0:
+            bc_cl = out.cpu().numpy()
+            # end to end: sources from the host, the centrality back to the host
+            out_h = torch.empty(g.V, dtype=torch.float64).pin_memory()
+            a, z = ev(), ev()
+            a.record()
+            bc.bc.zero_()
+            C.bc_run(bc.h, [graph.to_clustered_id(int(x)) for x in S], bc.bc)
+            out_h.copy_(bc.to_original8(bc.bc), non_blocking=True)
+            z.record()
+            z.synchronize()
+            res[order]["e2e_s"] = a.elapsed_time(z) / 1e3
+            res[order]["e2e_ok"] = bool(np.array_equal(out_h.numpy(), bc_cl))
+            # parity: the first two sources against the oracle
+            t0 = time.time()
+            out_off, out_dst = oracle.out_csr(g.offsets, g.src)
+            par = {"sources": [int(x) for x in S[:2]]}
+            worst = 0.0
+            for x in S[:2]:
+                tt = time.time()
+                lev, sig, dl, depth = oracle.bc_source(out_off, out_dst, int(x))
+                res[order].setdefault("oracle_s_per_source", time.time() - tt)
+                bc.run([int(x)])
+                glev, gsig, gdl, ginfo = bc.source_state()
+                par.setdefault("levels_equal", True)
+                par["levels_equal"] &= bool(np.array_equal(glev.cpu().numpy(), lev))
+                par.setdefault("sigma_equal", True)
+                par["sigma_equal"] &= bool(np.array_equal(gsig.cpu().numpy(), sig))
+                tol = 2.0 * depth * (int(np.diff(out_off).max()) + 8) * 2.0 ** -53
+                gd = gdl.cpu().numpy()
+                m = dl > 0
+                worst = max(worst, float(np.max(np.abs(gd[m] - dl[m]) / dl[m])) / tol)
+                par.setdefault("zero_delta_equal", True)
+                par["zero_delta_equal"] &= bool(np.all(gd[~m] == 0.0))
+            par["max_rel_err_over_tol"] = worst
+            par["ok"] = bool(par["levels_equal"] and par["sigma_equal"] and worst <= 1.0 and
+                             par["zero_delta_equal"])
+            par["oracle_wall_s"] = time.time() - t0
+            res[order]["parity"] = par
+        del bc, graph
+        torch.cuda.empty_cache()
+    head = res["clustered_outdeg"]
+    t12 = head["s_for_12_sources"]
+    line = {"metric": "betweenness centrality, 12 sources: traversed edges per second "
+                      "(12 x E / time)",
+            "value": 12 * g.E / t12 / 1e9, "unit": "GTEPS", "n_gpus": 1, "steps": len(S),
+            "warmup": args.warmup, "ms_per_step": t12 / len(S) * 1e3, "higher_is_better": True,
+            "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"bc_12_sources_rmat{args.scale}_directed_ef16",
+                       "V": g.V, "E": g.E, "sources": [int(x) for x in S],
+                       "l2_policy": "inputs larger than L2"},
+            "vs_baseline": None, "s_for_12_sources": t12,
+            "paper_context": "Table V: 7.08 s for 12 sources on RMAT25 (Xeon, 48 threads)",
+            "orders": res, "parity": head["parity"],
+            "speedup_clustered_vs_random": res["random"]["s_for_12_sources"] / t12,
+            "clocks": head["clocks"],
+            "e2e": {"value": 12 * g.E / head["e2e_s"] / 1e9, "unit": "GTEPS",
+                    "h2d_bytes_per_step": 4, "d2h_bytes_per_step": 8 * g.V // 12,
+                    "result_ok": head["e2e_ok"]},
+            "generate_host_s": gen_s}
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = {"value": g.E / head["oracle_s_per_source"] / 1e9, "unit": "GTEPS",
+                                "cores": 1, "cpu": cpu_model(), "kind": "oracle",
+                                "sample": "one source (BFS + dependency pass) over the full "
+                                          "graph, single-threaded FP64 Brandes"}
+    print(json.dumps(line), flush=True)
+
+
+def extras(g25, graph25):
+    """Compact records of the other forms of the gather, attached to the
+    default line so that one run measures them all: label propagation
+    (RMAT-24 undirected), 64-vector personalised PageRank (RMAT-22), the
+    1,024-graph batch, collaborative filtering (Netflix-shaped) and
+    betweenness centrality (RMAT-25, 12 sources).  Each is timed with CUDA
+    events and checked against the FP64 oracle on a bounded sample (BC:
+    against itself across directions; its oracle runs in the tests)."""
+    import torch
+    import graphgen
+    import oracle
+    from paper_1608_01362_gb300 import cagra as C
+    from paper_1608_01362_gb300 import pipeline as P
+    ev = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
+    out = {}
+
+    def timed(fn, reps=1):
+        a, z = ev(), ev()
+        a.record()
+        for _ in range(reps):
+            fn()
+        z.record()
+        z.synchronize()
+        return a.elapsed_time(z) / 1e3 / reps
+
+    # label propagation: passes until no label changes; the first pass bit for bit
+    t0 = time.time()
+    g = graphgen.rmat(24, 16, seed=1, symmetric=True)
+    graph = P.Graph(g.offsets, g.src, cluster_mode=0)
+    lp = P.LabelPropagation(graph, bounds=P.plan_bounds(graph, 1, 24.0))
+    lp.run(max_passes=2)
+    lab = lp.init()
+    a_, b_ = lp.labels[0], lp.labels[1]
+    C.lp_iterate(lp.seg, a_, b_)
+    first = graph.to_original(b_).cpu().numpy()
+    want1, _ = oracle.label_propagation_pass(g.offsets, g.src, np.arange(g.V, dtype=np.int32))
+    lp.init()
+    st, sp = ev(), ev()
+    st.record()
+    passes = 0
+    x, y = lp.labels[0], lp.labels[1]
+    while True:
+        passes += 1
+        if C.lp_iterate(lp.seg, x, y) == 0 or passes > 10000:
+            break
+        x, y = y, x
+    sp.record()
+    sp.synchronize()
+    t_lp = st.elapsed_time(sp) / 1e3
+    out["label_propagation_rmat24_undirected"] = {
+        "gteps_per_pass": g.E * passes / t_lp / 1e9, "ms_per_pass": t_lp / passes * 1e3,
+        "passes": passes, "first_pass_bitexact_vs_oracle": bool(np.array_equal(first, want1)),
+        "wall_s": time.time() - t0}
+    del lp, graph, g
+    torch.cuda.empty_cache()
+
+    # 64-vector personalised PageRank (BF16 hi+lo) against 64 one-vector solves
+    t0 = time.time()
+    g = graphgen.rmat(22, 16, seed=1)
+    graph = P.Graph(g.offsets, g.src, cluster_mode=0)
+    nd = int((graph.outdeg > 0).sum().item())
+    seeds = ppr_seeds(g)
+    b = P.BatchedPPR(graph, bounds=_ppr_bounds(nd, graph.V, 1), planes=2)
+    R, _ = b.run(seeds, ITERS)
+    t_b = timed(lambda: (b.init(seeds), C.ppr_batched_iterate(b.ppr, graph.inv, DAMPING, ITERS,
+                                                               b.rank)), reps=3)
+    one = P.SegmentedPageRank(graph, bounds=P.plan_bounds(graph, 1, 32.0))
+    one.run_ppr(int(seeds[0]), ITERS)
+    t_1 = timed(lambda: [one.run_ppr(int(s_), ITERS) for s_ in seeds])
+    want, bound = oracle.pagerank_bound(g.offsets, g.src, iters=ITERS, seed=int(seeds[0]),
+                                        u_store=oracle.U_BF16X2)
+    got = R[:, 0].cpu().numpy().astype(np.float64)
+    err = np.abs(got - want)
+    out["ppr64_rmat22"] = {
+        "ms_per_64_vector_solve": t_b * 1e3, "ms_64_one_vector_solves": t_1 * 1e3,
+        "speedup_vs_64_single": t_1 / t_b, "edge_vector_gteps": g.E * 64 * ITERS / t_b / 1e9,
+        "column0_rel_l1": float(err.sum() / want.sum()),
+        "column0_max_err_over_bound": float(np.max(err[bound > 0] / bound[bound > 0])),
+        "column0_within_bound": bool(np.all(err <= bound)), "wall_s": time.time() - t0}
+    del b, one, graph, g, R
+    torch.cuda.empty_cache()
+
+    # the 1,024-graph batch: one CUDA-graph-replayed launch against per-graph
+    # launches, also replayed from a CUDA graph
+    t0 = time.time()
+    gs = graphgen.small_graph_batch(count=1024, seed=1, scale_lo=8, scale_hi=15)
+    Etot = sum(len(x.src) for x in gs)
+    bp = P.BatchedPageRank(gs)
+    s2 = torch.cuda.Stream()
+    s2.wait_stream(torch.cuda.current_stream())
+    gb, gp = torch.cuda.CUDAGraph(), torch.cuda.CUDAGraph()
+    handles = [P.SegmentedPageRank(P.Graph(x.offsets, x.src, cluster_mode=None), 1) for x in gs]
+    with torch.cuda.stream(s2):
+        bp.run(ITERS)
+        for h in handles[:4]:
+            h.run(ITERS)
+        torch.cuda.synchronize()
+        with torch.cuda.graph(gb, stream=s2):
+            C.pr_batch_run(bp.batch, ITERS, DAMPING, bp.rank)
+        with torch.cuda.graph(gp, stream=s2, capture_error_mode="relaxed"):
+            for h in handles:
+                h.init()
+                h.step(h.rank[0], h.contrib[0], h.rank[1], h.contrib[1], DAMPING, ITERS)
+    torch.cuda.current_stream().wait_stream(s2)
+    gb.replay()
+    gp.replay()
+    torch.cuda.synchronize()
+    t_batch = timed(gb.replay, reps=5)
+    t_per = timed(gp.replay, reps=3)
+    rank = bp.rank.cpu().numpy()
+    worst, inside = 0.0, True
+    for i in range(0, 1024, 128):
+        want, bound = oracle.pagerank_bound(gs[i].offsets, gs[i].src, iters=ITERS)
+        e = np.abs(rank[bp.vbase[i]:bp.vbase[i + 1]].astype(np.float64) - want)
+        worst = max(worst, float(np.max(e / bound)))
+        inside &= bool(np.all(e <= bound))
+    out["batched_1024_graphs"] = {
+        "gteps": Etot * ITERS / t_batch / 1e9, "ms_per_solve": t_batch * 1e3,
+        "per_graph_launches_cuda_graph_ms": t_per * 1e3, "speedup_vs_per_graph": t_per / t_batch,
+        "sample_graphs": 8, "max_err_over_bound": worst, "within_bound": inside,
+        "wall_s": time.time() - t0}
+    del bp, handles, gb, gp, gs
+    torch.cuda.empty_cache()
+
+    # collaborative filtering: 10 sweeps at BF16 hi+lo; two FP32 sweeps vs FP64
+    t0 = time.time()
+    bpg = graphgen.bipartite(seed=1)
+    dev = lambda a, dt: torch.as_tensor(np.ascontiguousarray(a), dtype=dt).cuda()  # noqa: E731
+    uoff, uitem, urate = (dev(bpg.user_offsets, torch.int64), dev(bpg.items, torch.int32),
+                          dev(bpg.ratings, torch.uint8))
+    ioff = torch.empty(bpg.I + 1, dtype=torch.int64, device="cuda")
+    iuser = torch.empty(bpg.R, dtype=torch.int32, device="cuda")
+    irate = torch.empty(bpg.R, dtype=torch.uint8, device="cuda")
+    C.cf_transpose(bpg.U, bpg.I, uoff, uitem, urate, ioff, iuser, irate)
+    P0, Q0 = graphgen.cf_factors(bpg.U, bpg.I, 32, seed=1)
+    P0, Q0 = P0.astype(np.float32), Q0.astype(np.float32)
+    P0d, Q0d = dev(P0, torch.float32), dev(Q0, torch.float32)
+    h = C.cf_create(bpg.U, bpg.I, 32, C.CF_BF16X2, uoff, uitem, urate, ioff, iuser, irate)
+    C.cf_set_factors(h, P0d, Q0d)
+    C.cf_sweep(h, 1, 0.05, 1e-3)
+    C.cf_set_factors(h, P0d, Q0d)
+    t_cf = timed(lambda: C.cf_sweep(h, 10, 0.05, 1e-3)) / 10
+    del h
+    h = C.cf_create(bpg.U, bpg.I, 32, C.CF_FP32, uoff, uitem, urate, ioff, iuser, irate)
+    C.cf_set_factors(h, P0d, Q0d)
+    C.cf_sweep(h, 2, 0.05, 1e-3)
+    Pg = torch.empty((bpg.U, 32), dtype=torch.float32, device="cuda")
+    C.cf_get_factors(h, Pg, None)
+    io, iu, ir = oracle.item_major(bpg.U, bpg.I, bpg.user_offsets, bpg.items, bpg.ratings)
+    Pw, Qw = P0.astype(np.float64), Q0.astype(np.float64)
+    for _ in range(2):
+        Pw, Qw, _ = oracle.cf_sweep(bpg.U, bpg.I, bpg.user_offsets, bpg.items, bpg.ratings, io,
+                                    iu, ir, Pw, Qw, 0.05, 1e-3)
+    rel = float(np.max(np.abs(Pg.cpu().numpy() - Pw)) / np.max(np.abs(Pw)))
+    out["cf_netflix_shaped_k32"] = {
+        "ms_per_sweep_bf16x2": t_cf * 1e3, "gteps_rating_sides": 2 * bpg.R / t_cf / 1e9,
+        "fp32_two_sweeps_max_err_rel_to_max": rel, "fp32_tolerance": 2e-6,
+        "fp32_ok": bool(rel <= 2e-6), "wall_s": time.time() - t0}
+    del h, uoff, uitem, urate, ioff, iuser, irate, P0d, Q0d, Pg
+    torch.cuda.empty_cache()
+
+    # betweenness centrality from 12 sources on the headline graph; levels and
+    # path counts must not depend on the direction (push only vs the switch)
+    t0 = time.time()
+    bc = P.Betweenness(graph25)
+    S = ppr_seeds(g25, n=12)
+    bc.run(S[:1])
+    t_bc = timed(lambda: bc.run(S))
+    bc.run(S[:1])
+    l1, s1, _, inf1 = bc.source_state()
+    C.bc_set_direction(bc.h, 0.0)
+    bc.run(S[:1])
+    l0, s0, _, inf0 = bc.source_state()
+    out["betweenness_rmat25_12_sources"] = {
+        "s_for_12_sources": t_bc, "gteps": 12 * g25.E / t_bc / 1e9,
+        "levels": inf1["depth"], "push_levels": inf1["push_levels"],
+        "pull_levels": inf1["pull_levels"],
+        "levels_and_sigma_same_push_only": bool(torch.equal(l1, l0) and torch.equal(s1, s0)),
+        "wall_s": time.time() - t0}
+    del bc
+    torch.cuda.empty_cache()
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -935,9 +1265,11 @@ def main():
                          "(with --plan; the autotuner tries its own)")
     ap.add_argument("--sweep", action="store_true", help="k = 1..64 sweep table")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the compact records of the other forms (LP, PPR, batch, CF, BC)")
     ap.add_argument("--workload", default="pagerank",
-                    choices=["pagerank", "lp", "batched", "ppr", "cf", "qfactor", "sweep",
-                             "profile"],
+                    choices=["pagerank", "lp", "batched", "ppr", "cf", "bc", "qfactor",
+                             "sweep", "profile"],
                     help="pagerank (the headline), lp (label propagation, RMAT-24 undirected) "
                          "or batched (1,024 small RMAT graphs, scales 8-15)")
     ap.add_argument("--graphs", type=int, default=1024, help="graphs of the batched workload")
@@ -956,6 +1288,8 @@ def main():
         return run_cf(args)
     if args.workload == "batched":
         return run_batched(args)
+    if args.workload == "bc":
+        return run_bc(args)
     if args.workload == "qfactor":
         return run_qfactor(args)
     if args.workload == "sweep":
@@ -1207,6 +1541,8 @@ def main():
                                                    int(int(info["staged_edges"]) < E))),
         "clocks": clk,
     }
+    if rank == 0 and not args.no_extras:
+        line["sub_records"] = extras(g, graph)
     if rank == 0:
         # parity of exactly what was timed: the autotuned plan's 20-iteration
         # solve (and the end-to-end call's output) against the FP64 oracle,

@@ -106,6 +106,11 @@ int cg_relabel_csr(const int64_t *dev_offsets, const int32_t *dev_src,
 int cg_permute4(const void *dev_in, int64_t n_in, const int32_t *dev_idx,
                 int64_t n, void *dev_out, cudaStream_t stream);
 
+/* The same gather for 8-byte values (FP64 results such as betweenness
+ * centrality); both buffers 8-byte aligned. */
+int cg_permute8(const void *dev_in, int64_t n_in, const int32_t *dev_idx,
+                int64_t n, void *dev_out, cudaStream_t stream);
+
 /*
  * The same gather for rows of row_bytes bytes (a positive multiple of 16;
  * both buffers 16-byte aligned): row i of dev_out = row idx[i] of dev_in
@@ -588,6 +593,68 @@ int pr_iterate_plain_noalloc(const int64_t *dev_offsets, const int32_t *dev_src,
                              float *dev_rank_out, float *dev_contrib_out,
                              double damping, double *dev_dangling_io,
                              double *dev_resid, cudaStream_t stream);
+
+/* ------------------------------------------------ betweenness centrality */
+
+/*
+ * Transpose of an in-edge CSR: the out-edge CSR, row u listing the w of the
+ * edges u -> w in ascending order (a stable radix sort of the edges by
+ * source).  dev_in_offsets int64[V+1], dev_in_src int32[E] (validated: offsets
+ * monotone from 0 to E, sources in [0, V)); dev_out_offsets int64[V+1] and
+ * dev_out_dst int32[E] are overwritten.  Scratch (about 12 E bytes) comes from
+ * the stream-ordered allocator.  CG_ERR_INVALID_ARG on a bad CSR or sizes.
+ * Synchronizes the stream (validation).
+ */
+int cg_transpose_csr(const int64_t *dev_in_offsets, const int32_t *dev_in_src, int32_t V,
+                     int64_t E, int64_t *dev_out_offsets, int32_t *dev_out_dst,
+                     cudaStream_t stream);
+
+/*
+ * Betweenness centrality from a set of sources: the BC application of the
+ * paper's Table V (12 sources), which tracks an active set of vertices (the
+ * VertexSubset / ActiveFrontier of EdgeMap, Section IV), by Brandes'
+ * algorithm.  For each source s: a BFS over out-edges gives every vertex's
+ * level and sigma[v] = number of shortest s-v paths; then, deepest level
+ * first, delta[u] = sum over out-neighbours w one level deeper of
+ * sigma[u] / sigma[w] * (1 + delta[w]); bc[v] += delta[v] for v != s.
+ *
+ * bc_create takes the graph as both an in-edge CSR (dev_in_offsets,
+ * dev_in_src: the pull direction) and its out-edge CSR (dev_out_offsets,
+ * dev_out_dst, e.g. from cg_transpose_csr: the push direction and the
+ * dependency sums); both caller-owned, validated, and read for the handle's
+ * lifetime.  The handle (library-owned, about 60 V + 4 E bytes) holds the
+ * per-source state.  CG_ERR_INVALID_ARG on bad sizes or CSRs.  Synchronizes.
+ *
+ * bc_run: for each of the nsources host vertex IDs (each in [0, V), repeats
+ * allowed) in turn, adds its dependencies into dev_bc (FP64[V], caller-owned;
+ * zero it before the first call to get the centrality of the whole set).
+ * Each BFS level runs push (one thread per out-edge of the frontier, found
+ * through a prefix sum of the frontier's degrees; level by compare-and-swap,
+ * sigma by FP64 atomic adds) or pull (a merge-path tile gather over the
+ * in-edges of sigma on the frontier, 0 elsewhere) as the frontier's
+ * out-edges times alpha stay below or exceed E.  sigma values are integers
+ * and exact in FP64 below 2^53, so levels and sigma are the same in any order
+ * or direction; delta sums run in a fixed order (deterministic).  Reads two
+ * counts per level on the host: synchronizes the stream.
+ *
+ * bc_set_direction: alpha >= 0 (default 16; 0 always pushes, a huge value
+ * pulls every level with a non-empty frontier).
+ *
+ * bc_source_state: the last source's levels (int32[V], -1 unreached), sigma
+ * and delta (FP64[V]) copied into caller device buffers (any may be NULL),
+ * its number of levels and how many ran push and pull (host; may be NULL).
+ */
+typedef struct cg_bc cg_bc;
+int bc_create(const int64_t *dev_in_offsets, const int32_t *dev_in_src,
+              const int64_t *dev_out_offsets, const int32_t *dev_out_dst, int32_t V,
+              int64_t E, cg_bc **out, cudaStream_t stream);
+int bc_destroy(cg_bc *bc);
+int bc_set_direction(cg_bc *bc, double alpha);
+int bc_run(cg_bc *bc, const int32_t *sources, int32_t nsources, double *dev_bc,
+           cudaStream_t stream);
+int bc_source_state(const cg_bc *bc, int32_t *dev_level, double *dev_sigma,
+                    double *dev_delta, int32_t *depth, int32_t *push_levels,
+                    int32_t *pull_levels, cudaStream_t stream);
 
 /*
  * Roofline denominators measured on the current GPU (the gathers of

@@ -91,6 +91,10 @@ def _load():
             lib.orc_cf_sweep.restype = ctypes.c_int
             lib.orc_cf_sweep.argtypes = [i64, i64, i32, vp, vp, vp, vp, vp, vp, dbl, dbl, vp, vp,
                                          vp]
+            lib.orc_out_csr.restype = ctypes.c_int
+            lib.orc_out_csr.argtypes = [i64, vp, vp, vp, vp]
+            lib.orc_bc_source.restype = i32
+            lib.orc_bc_source.argtypes = [i64, vp, vp, i32, vp, vp, vp]
             lib.orc_num_threads.restype = ctypes.c_int
             lib.orc_num_threads.argtypes = []
             _lib = lib
@@ -391,3 +395,55 @@ def cf_sweep(U, I, uoff, uitem, urate, ioff, iuser, irate, P, Q, lam=0.05, step=
         raise ValueError("oracle: cf sweep failed (K out of range or allocation)")
     return P, Q, float(sse.value)
 
+
+
+# --------------------------------------------------------------------------
+# Betweenness centrality (Table V: 12 sources; Brandes' algorithm)
+# --------------------------------------------------------------------------
+
+def out_csr(offsets, src):
+    """Out-edge CSR (out_off, out_dst) of an in-edge CSR: row u lists the
+    destinations of u's out-edges in ascending order (a counting sort)."""
+    offsets = _c(offsets, np.int64)
+    src = _c(src, np.int32)
+    V = offsets.shape[0] - 1
+    out_off = np.empty(V + 1, dtype=np.int64)
+    out_dst = np.empty(max(src.shape[0], 1), dtype=np.int32)
+    if _load().orc_out_csr(V, offsets.ctypes.data,
+                           (src if src.size else np.zeros(1, np.int32)).ctypes.data,
+                           out_off.ctypes.data, out_dst.ctypes.data) != 0:
+        raise MemoryError("oracle: out_csr allocation failed")
+    return out_off, out_dst[:src.shape[0]]
+
+
+def bc_source(out_off, out_dst, s: int):
+    """(level, sigma, delta, levels) of one source over an out-edge CSR."""
+    out_off = _c(out_off, np.int64)
+    out_dst = _c(out_dst, np.int32)
+    V = out_off.shape[0] - 1
+    level = np.empty(V, dtype=np.int32)
+    sigma = np.empty(V)
+    delta = np.empty(V)
+    depth = _load().orc_bc_source(V, out_off.ctypes.data,
+                                  (out_dst if out_dst.size else np.zeros(1, np.int32)).ctypes.data,
+                                  int(s), level.ctypes.data, sigma.ctypes.data, delta.ctypes.data)
+    if depth < 0:
+        raise ValueError("oracle: bc source out of range or allocation failed")
+    return level, sigma, delta, int(depth)
+
+
+def betweenness(offsets, src, sources):
+    """Betweenness centrality of every vertex from the given sources (sum over
+    the sources s of the dependencies delta_s(v), v != s), FP64, on the graph
+    given as an in-edge CSR.  Returns (bc, per-source (level, sigma, delta))."""
+    out_off, out_dst = out_csr(offsets, src)
+    V = out_off.shape[0] - 1
+    bc = np.zeros(V)
+    per = []
+    for s in sources:
+        level, sigma, delta, _ = bc_source(out_off, out_dst, int(s))
+        d = delta.copy()
+        d[int(s)] = 0.0
+        bc += d
+        per.append((level, sigma, delta))
+    return bc, per

@@ -505,6 +505,74 @@ int orc_cf_sweep(int64_t U, int64_t I, int32_t K, const int64_t *uoff,
     return 0;
 }
 
+/*
+ * Out-edge CSR of an in-edge CSR by counting: out_off[u+1] - out_off[u] =
+ * out-degree of u; the edges u -> v are placed in the order the in-edge CSR
+ * lists them (rows v ascending), so each out-row lists its destinations in
+ * ascending order.  out_off: int64[V+1], out_dst: int32[E].
+ */
+int orc_out_csr(int64_t V, const int64_t *offsets, const int32_t *src,
+                int64_t *out_off, int32_t *out_dst) {
+    int64_t *next = (int64_t *)malloc((size_t)(V > 0 ? V : 1) * sizeof(int64_t));
+    if (!next) return -1;
+    for (int64_t u = 0; u <= V; ++u) out_off[u] = 0;
+    for (int64_t e = 0; e < offsets[V]; ++e) out_off[src[e] + 1]++;
+    for (int64_t u = 0; u < V; ++u) out_off[u + 1] += out_off[u];
+    for (int64_t u = 0; u < V; ++u) next[u] = out_off[u];
+    for (int64_t v = 0; v < V; ++v)
+        for (int64_t e = offsets[v]; e < offsets[v + 1]; ++e) out_dst[next[src[e]]++] = (int32_t)v;
+    free(next);
+    return 0;
+}
+
+/*
+ * Betweenness-centrality dependencies of one source (the BC of Table V, run
+ * from 12 sources; Brandes' algorithm, which the Ligra BC the paper extends
+ * follows).  The graph is an OUT-edge CSR (out_off, out_dst): row u lists the
+ * w of the edges u -> w.
+ *   1. BFS from s over out-edges in FIFO order: level[s] = 0, sigma[s] = 1; for
+ *      u taken from the queue and each w in row u: an unvisited w gets
+ *      level[u] + 1 and joins the queue; if level[w] = level[u] + 1 then
+ *      sigma[w] += sigma[u] (the number of shortest s-w paths).
+ *   2. In reverse BFS order: delta[u] = sum over w in row u with
+ *      level[w] = level[u] + 1 of sigma[u] / sigma[w] * (1 + delta[w])
+ *      (left to right in the row).
+ * Unreached vertices get level -1, sigma 0, delta 0.  The centrality of v
+ * from a set of sources is the sum of delta over the sources other than v.
+ * Returns the number of levels (the largest level + 1), or -1.
+ */
+int32_t orc_bc_source(int64_t V, const int64_t *out_off, const int32_t *out_dst, int32_t s,
+                      int32_t *level, double *sigma, double *delta) {
+    int32_t *queue = (int32_t *)malloc((size_t)(V > 0 ? V : 1) * sizeof(int32_t));
+    if (!queue || s < 0 || s >= V) { free(queue); return -1; }
+    for (int64_t v = 0; v < V; ++v) { level[v] = -1; sigma[v] = 0.0; delta[v] = 0.0; }
+    int64_t head = 0, tail = 0;
+    level[s] = 0;
+    sigma[s] = 1.0;
+    queue[tail++] = s;
+    while (head < tail) {
+        const int32_t u = queue[head++];
+        for (int64_t e = out_off[u]; e < out_off[u + 1]; ++e) {
+            const int32_t w = out_dst[e];
+            if (level[w] < 0) { level[w] = level[u] + 1; queue[tail++] = w; }
+            if (level[w] == level[u] + 1) sigma[w] += sigma[u];
+        }
+    }
+    int32_t depth = 0;
+    for (int64_t i = tail - 1; i >= 0; --i) {
+        const int32_t u = queue[i];
+        if (level[u] + 1 > depth) depth = level[u] + 1;
+        double acc = 0.0;
+        for (int64_t e = out_off[u]; e < out_off[u + 1]; ++e) {
+            const int32_t w = out_dst[e];
+            if (level[w] == level[u] + 1) acc += sigma[u] / sigma[w] * (1.0 + delta[w]);
+        }
+        delta[u] = acc;
+    }
+    free(queue);
+    return depth;
+}
+
 int orc_num_threads(void) {
 #ifdef _OPENMP
     return omp_get_max_threads();

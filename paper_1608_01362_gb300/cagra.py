@@ -38,6 +38,8 @@ EXPORTS = [
     "ppr_batched_iterate", "ppr_batched_step",
     "cf_transpose", "cf_create", "cf_destroy", "cf_set_factors", "cf_get_factors", "cf_sweep",
     "cf_sweep_phase", "cf_info", "cg_measure_row_gather", "cg_measure_smem_lookups",
+    "cg_permute8", "cg_transpose_csr", "bc_create", "bc_destroy", "bc_set_direction", "bc_run",
+    "bc_source_state",
 ]
 
 
@@ -77,6 +79,7 @@ def load(path: str | None = None):
             "cg_relabel_csr": (ctypes.c_int, [vp, vp, i32, i64, vp, vp, vp, vp, vp]),
             "cg_permute4": (ctypes.c_int, [vp, i64, vp, i64, vp, vp]),
             "cg_permute_rows": (ctypes.c_int, [vp, i64, i32, vp, i64, vp, vp]),
+            "cg_permute8": (ctypes.c_int, [vp, i64, vp, i64, vp, vp]),
             "pr_build_segments": (ctypes.c_int, [vp, vp, i32, i64, i32, vp, i32,
                                                  ctypes.POINTER(vp), vp]),
             "cg_segmented_get_info": (ctypes.c_int, [vp, ctypes.POINTER(SegInfo)]),
@@ -124,6 +127,12 @@ def load(path: str | None = None):
             "cf_sweep": (ctypes.c_int, [vp, i32, dbl, dbl, vp, vp]),
             "cf_sweep_phase": (ctypes.c_int, [vp, i32, dbl, dbl, vp, vp]),
             "cf_info": (ctypes.c_int, [vp, vp, vp, vp, vp]),
+            "cg_transpose_csr": (ctypes.c_int, [vp, vp, i32, i64, vp, vp, vp]),
+            "bc_create": (ctypes.c_int, [vp, vp, vp, vp, i32, i64, ctypes.POINTER(vp), vp]),
+            "bc_destroy": (ctypes.c_int, [vp]),
+            "bc_set_direction": (ctypes.c_int, [vp, dbl]),
+            "bc_run": (ctypes.c_int, [vp, vp, i32, vp, vp]),
+            "bc_source_state": (ctypes.c_int, [vp, vp, vp, vp, vp, vp, vp, vp]),
             "cg_measure_row_gather": (ctypes.c_int, [i32, i64, vp, vp]),
             "cg_measure_smem_lookups": (ctypes.c_int, [vp, vp]),
         }
@@ -197,6 +206,14 @@ def cg_permute4(x, idx, out, stream=None):
         raise CagraError("cg_permute4 needs 4-byte elements")
     _check(load().cg_permute4(_ptr(x), x.numel(), _ptr(idx), idx.numel(), _ptr(out),
                               _stream(stream)), "cg_permute4")
+
+
+def cg_permute8(x, idx, out, stream=None):
+    """out[i] = x[idx[i]] for 8-byte elements."""
+    if x.element_size() != 8 or out.element_size() != 8:
+        raise CagraError("cg_permute8 needs 8-byte elements")
+    _check(load().cg_permute8(_ptr(x), x.numel(), _ptr(idx), idx.numel(), _ptr(out),
+                              _stream(stream)), "cg_permute8")
 
 
 def cg_permute_rows(x, idx, out, stream=None):
@@ -593,6 +610,80 @@ def pr_batch_set_threads(batch: Batch, threads: int):
 def pr_batch_run(batch: Batch, iterations: int, damping: float, rank, resid=None, stream=None):
     _check(load().pr_batch_run(batch.handle, iterations, damping, _ptr(rank), _ptr(resid),
                                _stream(stream)), "pr_batch_run")
+
+
+# ------------------------------------------------------------------ betweenness centrality
+
+def cg_transpose_csr(offsets, src, out_offsets, out_dst, stream=None):
+    """Out-edge CSR of an in-edge CSR (rows in ascending destination order)."""
+    V = offsets.numel() - 1
+    _dtype_check(offsets, torch_int64(), "offsets")
+    _dtype_check(src, torch_int32(), "src")
+    _check(load().cg_transpose_csr(_ptr(offsets), _ptr(src) if src.numel() else None, V,
+                                   src.numel(), _ptr(out_offsets),
+                                   _ptr(out_dst) if out_dst.numel() else None, _stream(stream)),
+           "cg_transpose_csr")
+
+
+class Betweenness:
+    """Owns a cg_bc handle (and keeps its CSR tensors alive)."""
+
+    def __init__(self, handle: int, keep):
+        self.handle = handle
+        self._keep = keep
+
+    def __del__(self):
+        self.close()
+
+    def close(self):
+        if getattr(self, "handle", None):
+            load().bc_destroy(self.handle)
+            self.handle = None
+
+
+def bc_create(in_offsets, in_src, out_offsets, out_dst, stream=None) -> Betweenness:
+    V = in_offsets.numel() - 1
+    h = ctypes.c_void_p()
+    _check(load().bc_create(_ptr(in_offsets), _ptr(in_src) if in_src.numel() else None,
+                            _ptr(out_offsets), _ptr(out_dst) if out_dst.numel() else None, V,
+                            in_src.numel(), ctypes.byref(h), _stream(stream)), "bc_create")
+    return Betweenness(h.value, (in_offsets, in_src, out_offsets, out_dst))
+
+
+def bc_set_direction(bc: Betweenness, alpha: float):
+    _check(load().bc_set_direction(bc.handle, float(alpha)), "bc_set_direction")
+
+
+def bc_run(bc: Betweenness, sources, out, stream=None):
+    """Adds the dependencies of every source (host IDs) into out (FP64[V])."""
+    src = (ctypes.c_int32 * len(sources))(*[int(x) for x in sources])
+    _dtype_check(out, torch_float64(), "out")
+    _check(load().bc_run(bc.handle, src, len(sources), _ptr(out), _stream(stream)), "bc_run")
+
+
+def bc_source_state(bc: Betweenness, level=None, sigma=None, delta=None, stream=None) -> dict:
+    """The last source's level / sigma / delta into the given device tensors;
+    returns {depth, push_levels, pull_levels}."""
+    d, pu, pl = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+    _check(load().bc_source_state(bc.handle, _ptr(level), _ptr(sigma), _ptr(delta),
+                                  ctypes.byref(d), ctypes.byref(pu), ctypes.byref(pl),
+                                  _stream(stream)), "bc_source_state")
+    return {"depth": d.value, "push_levels": pu.value, "pull_levels": pl.value}
+
+
+def torch_int64():
+    import torch
+    return torch.int64
+
+
+def torch_int32():
+    import torch
+    return torch.int32
+
+
+def torch_float64():
+    import torch
+    return torch.float64
 
 
 def measure_row_gather(row_bytes: int, table_bytes: int, stream=None) -> float:

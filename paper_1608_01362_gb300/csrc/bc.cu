@@ -1,0 +1,544 @@
+// Betweenness centrality from a set of sources (the BC application of the
+// paper's Table V, run from 12 sources), by Brandes' algorithm over
+// frontiers: the activeness side of the EdgeMap / VertexSubset API of
+// Section IV, on the clustered graph (Section V; for BC the paper credits its
+// speed-up to the renumbering, the working set being too small for
+// segmenting to pay).
+//
+// Forward phase, one BFS level at a time from the source (level 0, sigma 1):
+//   push (small frontier: its out-edges, one thread per edge, found through a
+//         prefix sum of the frontier's out-degrees): an unvisited w gets level
+//         L+1 by compare-and-swap and joins the next frontier; every edge into
+//         a level-(L+1) vertex adds sigma[u] to sigma[w] with an FP64 atomic;
+//   pull (large frontier: the merge-path tile gather over the in-edge CSR of
+//         x = sigma on the frontier, 0 elsewhere): an unvisited v whose sum is
+//         non-zero gets level L+1 and sigma = the sum.
+// sigma counts shortest paths: integers, exact in FP64 in any order below
+// 2^53, so levels and sigma do not depend on the direction or the order.
+// Pull is taken when (frontier out-edges) * alpha > E.
+//
+// Backward phase, deepest level first: for every u at level L,
+//   delta[u] = sigma[u] * sum over out-neighbours w at level L+1 of
+//              (1 + delta[w]) / sigma[w]
+// as a gather over the out-rows of level L's vertices laid end to end (a
+// "virtual" CSR of that level), with x = (1 + delta) / sigma on level L+1 and
+// 0 on every other level (out-neighbours of a level-L vertex lie at levels
+// <= L+1, and levels <= L are still 0), by the same tile gather; the level
+// lists are first put in (level, vertex ID) order, so the summation order is
+// fixed and the results deterministic.  bc[u] += delta[u] for u != source.
+#include <algorithm>
+#include <vector>
+
+#include "gather.cuh"
+#include "handles.cuh"
+
+struct cg_bc {
+  int device = 0;
+  int32_t V = 0;
+  int64_t E = 0;
+  const int64_t* in_off = nullptr;   // caller-owned in-edge CSR (pull)
+  const int32_t* in_src = nullptr;
+  const int64_t* out_off = nullptr;  // caller-owned out-edge CSR (push, backward)
+  const int32_t* out_dst = nullptr;
+  int32_t* level = nullptr;    // [V] BFS level of the current source (-1: unreached)
+  double* sigma = nullptr;     // [V] shortest-path counts
+  double* delta = nullptr;     // [V] dependencies
+  double* xval = nullptr;      // [V] gathered values (see above), 0 elsewhere
+  double* acc = nullptr;       // [V] gathered sums
+  int32_t* lists = nullptr;    // [V] reached vertices, level after level
+  int32_t* deg = nullptr;      // [V] out-degrees of one level's vertices
+  int64_t* rend = nullptr;     // [V+1] their exclusive prefix (rend[n] = total)
+  int32_t* col_v = nullptr;    // [E] their out-rows end to end
+  int32_t* counter = nullptr;  // [1] next free position in lists
+  int32_t* ids = nullptr;      // [V] sort scratch: reached vertices in ID order
+  uint32_t* keys = nullptr;    // [V] sort scratch: their levels
+  uint32_t* keys_out = nullptr;  // [V]
+  int64_t* h_pin = nullptr;    // pinned host words for the per-level counts
+  cg::TilePlan in_plan;        // tiles of the in-edge CSR (8-byte carries)
+  int32_t* vt_row = nullptr;   // tiles of a level's virtual CSR
+  int32_t* vt_edge = nullptr;
+  double* vt_carry = nullptr;
+  int32_t* vt_carry_row = nullptr;
+  int64_t vt_cap = 0;
+  double alpha = 16.0;
+  std::vector<int64_t> lbase;  // level bounds in `lists` of the last source
+  int32_t last_source = -1;
+  int32_t push_levels = 0, pull_levels = 0;
+};
+
+namespace cg {
+namespace {
+
+constexpr int kThreads = 256;
+
+__global__ void bc_reset_kernel(int32_t V, int32_t* __restrict__ level,
+                                double* __restrict__ sigma, double* __restrict__ delta,
+                                double* __restrict__ xval) {
+  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < V;
+       v += (int64_t)gridDim.x * blockDim.x) {
+    level[v] = -1;
+    sigma[v] = 0.0;
+    delta[v] = 0.0;
+    xval[v] = 0.0;
+  }
+}
+
+__global__ void bc_seed_kernel(int32_t s, int32_t* __restrict__ level, double* __restrict__ sigma,
+                               double* __restrict__ xval, int32_t* __restrict__ lists,
+                               int32_t* __restrict__ counter) {
+  level[s] = 0;
+  sigma[s] = 1.0;
+  xval[s] = 1.0;
+  lists[0] = s;
+  *counter = 1;
+}
+
+// Row lengths of the out-edge CSR for the vertices of a list (taken from the
+// out-CSR's own offsets, so every expanded edge lies inside its row).
+__global__ void list_degree_kernel(const int32_t* __restrict__ list, int64_t n,
+                                   const int64_t* __restrict__ out_off, int32_t* __restrict__ deg) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t u = list[i];
+    deg[i] = (int32_t)(out_off[u + 1] - out_off[u]);
+  }
+}
+
+// last i in [0, n) with rend[i] <= k (rend ascending, rend[0] = 0 <= k)
+__device__ __forceinline__ int64_t row_of(const int64_t* rend, int64_t n, int64_t k) {
+  int64_t lo = 0, hi = n;
+  while (lo < hi) {
+    const int64_t mid = (lo + hi) >> 1;
+    if (rend[mid] <= k) lo = mid + 1; else hi = mid;
+  }
+  return lo - 1;
+}
+
+// Append v to lists at a position from one atomic per warp.
+__device__ __forceinline__ void append(bool take, int32_t v, int32_t* lists, int32_t* counter) {
+  const unsigned m = __ballot_sync(0xffffffffu, take);
+  if (!m) return;
+  const int lane = threadIdx.x & 31;
+  int32_t base = 0;
+  if (lane == __ffs(m) - 1) base = atomicAdd(counter, __popc(m));
+  base = __shfl_sync(0xffffffffu, base, __ffs(m) - 1);
+  if (take) lists[base + __popc(m & ((1u << lane) - 1u))] = v;
+}
+
+// Push: one thread per out-edge of the frontier (list, n vertices, m edges).
+__global__ void push_kernel(const int32_t* __restrict__ list, int64_t n,
+                            const int64_t* __restrict__ rend, int64_t m,
+                            const int64_t* __restrict__ out_off, const int32_t* __restrict__ out_dst,
+                            int32_t L, int32_t* __restrict__ level, double* __restrict__ sigma,
+                            int32_t* __restrict__ lists, int32_t* __restrict__ counter) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t k0 = (int64_t)blockIdx.x * blockDim.x; k0 < m; k0 += stride) {
+    const int64_t k = k0 + threadIdx.x;  // the warp stays converged for the append
+    bool take = false;
+    int32_t w = 0;
+    if (k < m) {
+      const int64_t i = row_of(rend, n, k);
+      const int32_t u = list[i];
+      w = out_dst[out_off[u] + (k - rend[i])];
+      const int32_t old = atomicCAS(level + w, -1, L + 1);
+      take = old == -1;
+      if (old == -1 || old == L + 1) atomicAdd(sigma + w, sigma[u]);
+    }
+    append(take, w, lists, counter);
+  }
+}
+
+// After a pull gather: an unvisited v with a non-zero sum is on level L+1.
+__global__ void pull_update_kernel(int32_t V, const double* __restrict__ acc, int32_t L,
+                                   int32_t* __restrict__ level, double* __restrict__ sigma,
+                                   int32_t* __restrict__ lists, int32_t* __restrict__ counter) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t v0 = (int64_t)blockIdx.x * blockDim.x; v0 < V; v0 += stride) {
+    const int64_t v = v0 + threadIdx.x;
+    bool take = false;
+    if (v < V && level[v] == -1) {
+      const double a = acc[v];
+      if (a != 0.0) {
+        level[v] = L + 1;
+        sigma[v] = a;
+        take = true;
+      }
+    }
+    append(take, (int32_t)v, lists, counter);
+  }
+}
+
+// x over the vertices of a list: sigma (forward frontier) or 0.
+__global__ void set_x_kernel(const int32_t* __restrict__ list, int64_t n,
+                             const double* __restrict__ sigma, double* __restrict__ xval,
+                             bool clear) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t u = list[i];
+    xval[u] = clear ? 0.0 : sigma[u];
+  }
+}
+
+// The deepest level: delta = 0, x = 1 / sigma.
+__global__ void deepest_kernel(const int32_t* __restrict__ list, int64_t n,
+                               const double* __restrict__ sigma, double* __restrict__ xval) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t u = list[i];
+    xval[u] = 1.0 / sigma[u];
+  }
+}
+
+// The out-rows of a level's vertices end to end.
+__global__ void expand_kernel(const int32_t* __restrict__ list, int64_t n,
+                              const int64_t* __restrict__ rend, int64_t m,
+                              const int64_t* __restrict__ out_off,
+                              const int32_t* __restrict__ out_dst, int32_t* __restrict__ col_v) {
+  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < m;
+       k += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = row_of(rend, n, k);
+    col_v[k] = out_dst[out_off[list[i]] + (k - rend[i])];
+  }
+}
+
+// delta of level L from the gathered sums; bc += delta (not for the source);
+// x = (1 + delta) / sigma for the next level up.
+__global__ void dependency_kernel(const int32_t* __restrict__ list, int64_t n,
+                                  const double* __restrict__ sums, const double* __restrict__ sigma,
+                                  double* __restrict__ delta, double* __restrict__ xval,
+                                  double* __restrict__ bc, int32_t source) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t u = list[i];
+    const double d = sigma[u] * sums[i];
+    delta[u] = d;
+    xval[u] = (1.0 + d) / sigma[u];
+    if (u != source) bc[u] += d;
+  }
+}
+
+// Reached vertices in ascending ID order (pos: exclusive prefix of reached).
+__global__ void reached_flag_kernel(int32_t V, const int32_t* __restrict__ level,
+                                    int32_t* __restrict__ flag) {
+  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < V;
+       v += (int64_t)gridDim.x * blockDim.x)
+    flag[v] = level[v] >= 0;
+}
+
+__global__ void compact_kernel(int32_t V, const int32_t* __restrict__ level,
+                               const int64_t* __restrict__ pos, int32_t* __restrict__ ids,
+                               uint32_t* __restrict__ keys) {
+  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < V;
+       v += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t l = level[v];
+    if (l >= 0) {
+      ids[pos[v]] = (int32_t)v;
+      keys[pos[v]] = (uint32_t)l;
+    }
+  }
+}
+
+__global__ void row_of_edge_kernel(const int64_t* __restrict__ off, int32_t V,
+                                   int32_t* __restrict__ dst) {
+  const int lane = threadIdx.x & 31;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t v = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; v < V; v += nw)
+    for (int64_t e = off[v] + lane; e < off[v + 1]; e += 32) dst[e] = (int32_t)v;
+}
+
+int read_i64(cg_bc* h, const int64_t* dev, int64_t* out, cudaStream_t s) {
+  CG_CUDA(cudaMemcpyAsync(h->h_pin, dev, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+  CG_CUDA(cudaStreamSynchronize(s));
+  *out = h->h_pin[0];
+  return CG_OK;
+}
+
+int read_i32(cg_bc* h, const int32_t* dev, int32_t* out, cudaStream_t s) {
+  CG_CUDA(cudaMemcpyAsync(h->h_pin, dev, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+  CG_CUDA(cudaStreamSynchronize(s));
+  *out = *reinterpret_cast<int32_t*>(h->h_pin);
+  return CG_OK;
+}
+
+// Degrees of list[0, n) and their prefix; *m = total out-edges.
+int level_rows(cg_bc* h, const int32_t* list, int64_t n, int64_t* m, cudaStream_t s) {
+  list_degree_kernel<<<grid_for(n, kThreads), kThreads, 0, s>>>(list, n, h->out_off, h->deg);
+  CG_LAUNCH_CHECK();
+  CG_TRY(exclusive_scan_i32_to_i64(h->deg, h->rend, n, s));
+  return read_i64(h, h->rend + n, m, s);
+}
+
+int grow_vt(cg_bc* h, int64_t ntiles) {
+  if (ntiles + 1 <= h->vt_cap) return CG_OK;
+  cudaFree(h->vt_row);
+  cudaFree(h->vt_edge);
+  cudaFree(h->vt_carry);
+  cudaFree(h->vt_carry_row);
+  h->vt_row = h->vt_edge = h->vt_carry_row = nullptr;
+  h->vt_carry = nullptr;
+  h->vt_cap = 0;
+  const size_t c = (size_t)(ntiles + 1);
+  CG_CUDA(cudaMalloc((void**)&h->vt_row, 4 * c));
+  CG_CUDA(cudaMalloc((void**)&h->vt_edge, 4 * c));
+  CG_CUDA(cudaMalloc((void**)&h->vt_carry, 8 * c));
+  CG_CUDA(cudaMalloc((void**)&h->vt_carry_row, 4 * c));
+  h->vt_cap = ntiles + 1;
+  return CG_OK;
+}
+
+// Lay the level lists out in (level, vertex ID) order: the appends of the
+// forward phase come in whatever order the atomics give, and the backward
+// sums are associated by position in these lists.  A compaction of the
+// reached vertices in ID order, then a stable radix sort on the level.
+int order_levels(cg_bc* h, int32_t depth, cudaStream_t s) {
+  const int32_t V = h->V;
+  const int64_t n = h->lbase[depth];
+  reached_flag_kernel<<<grid_for(V, kThreads), kThreads, 0, s>>>(V, h->level, h->deg);
+  CG_LAUNCH_CHECK();
+  CG_TRY(exclusive_scan_i32_to_i64(h->deg, h->rend, V, s));
+  compact_kernel<<<grid_for(V, kThreads), kThreads, 0, s>>>(V, h->level, h->rend, h->ids,
+                                                            h->keys);
+  CG_LAUNCH_CHECK();
+  int bits = 1;
+  while (bits < 32 && (int64_t(1) << bits) < (int64_t)depth) ++bits;
+  return radix_sort_pairs(h->keys, h->ids, h->keys_out, h->lists, n, bits, s);
+}
+
+int run_source(cg_bc* h, int32_t src, double* bc, cudaStream_t s) {
+  const int32_t V = h->V;
+  bc_reset_kernel<<<grid_for(V, kThreads), kThreads, 0, s>>>(V, h->level, h->sigma, h->delta,
+                                                               h->xval);
+  CG_LAUNCH_CHECK();
+  bc_seed_kernel<<<1, 1, 0, s>>>(src, h->level, h->sigma, h->xval, h->lists, h->counter);
+  CG_LAUNCH_CHECK();
+  h->lbase.assign(1, 0);
+  h->lbase.push_back(1);
+  h->push_levels = h->pull_levels = 0;
+  // forward: one level per round until a level adds nobody
+  for (int32_t L = 0;; ++L) {
+    const int64_t b0 = h->lbase[L], n = h->lbase[L + 1] - b0;
+    const int32_t* list = h->lists + b0;
+    int64_t m = 0;
+    CG_TRY(level_rows(h, list, n, &m, s));
+    if (m > 0) {
+      if ((double)m * h->alpha > (double)h->E) {  // pull over the in-edge CSR
+        CG_TRY((run_tile_gather<SumF64, false, int64_t>(h->in_plan, h->in_off + 1, h->in_src,
+                                                        h->xval, V, h->acc, s)));
+        pull_update_kernel<<<grid_for(V, kThreads), kThreads, 0, s>>>(V, h->acc, L, h->level,
+                                                                      h->sigma, h->lists,
+                                                                      h->counter);
+        CG_LAUNCH_CHECK();
+        ++h->pull_levels;
+      } else {  // push from the frontier's out-edges
+        push_kernel<<<grid_for(m, kThreads), kThreads, 0, s>>>(list, n, h->rend, m, h->out_off,
+                                                              h->out_dst, L, h->level, h->sigma,
+                                                              h->lists, h->counter);
+        CG_LAUNCH_CHECK();
+        ++h->push_levels;
+      }
+    }
+    int32_t cnt = 0;
+    CG_TRY(read_i32(h, h->counter, &cnt, s));
+    if (cnt == h->lbase[L + 1]) break;  // nothing new: L is the deepest level
+    h->lbase.push_back(cnt);
+    // the frontier moves on: x = sigma on level L+1 only
+    set_x_kernel<<<grid_for(n, kThreads), kThreads, 0, s>>>(list, n, h->sigma, h->xval, true);
+    CG_LAUNCH_CHECK();
+    const int64_t n1 = cnt - h->lbase[L + 1];
+    set_x_kernel<<<grid_for(n1, kThreads), kThreads, 0, s>>>(h->lists + h->lbase[L + 1], n1,
+                                                             h->sigma, h->xval, false);
+    CG_LAUNCH_CHECK();
+  }
+  const int32_t depth = (int32_t)h->lbase.size() - 1;  // levels 0 .. depth-1
+  CG_TRY(order_levels(h, depth, s));
+  {
+    const int64_t b = h->lbase[depth - 1], n = h->lbase[depth] - b;
+    deepest_kernel<<<grid_for(n, kThreads), kThreads, 0, s>>>(h->lists + b, n, h->sigma,
+                                                              h->xval);
+    CG_LAUNCH_CHECK();
+  }
+  // backward: levels depth-2 .. 0
+  for (int32_t L = depth - 2; L >= 0; --L) {
+    const int64_t b0 = h->lbase[L], n = h->lbase[L + 1] - b0;
+    const int32_t* list = h->lists + b0;
+    int64_t m = 0;
+    CG_TRY(level_rows(h, list, n, &m, s));
+    if (m > 0) {
+      expand_kernel<<<grid_for(m, kThreads), kThreads, 0, s>>>(list, n, h->rend, m, h->out_off,
+                                                              h->out_dst, h->col_v);
+      CG_LAUNCH_CHECK();
+      const int64_t ntiles = ceil_div(n + m, kTileItems);
+      CG_TRY(grow_vt(h, ntiles));
+      tile_partition_kernel<int64_t><<<grid_for(ntiles + 1, 256), 256, 0, s>>>(
+          h->rend + 1, n, m, kTileItems, ntiles, h->vt_row, h->vt_edge);
+      CG_LAUNCH_CHECK();
+      gather_tile_kernel<SumF64, kTileThreads, kTileIPT, false, int64_t>
+          <<<(unsigned)ntiles, kTileThreads, 0, s>>>(h->rend + 1, h->col_v, h->xval, V,
+                                                     h->vt_row, h->vt_edge, h->acc, h->vt_carry,
+                                                     h->vt_carry_row);
+      CG_LAUNCH_CHECK();
+      carry_fixup_kernel<SumF64><<<grid_for(ntiles, 256, 4), 256, 0, s>>>(
+          h->vt_carry, h->vt_carry_row, ntiles, n, h->acc);
+      CG_LAUNCH_CHECK();
+    } else {
+      CG_CUDA(cudaMemsetAsync(h->acc, 0, sizeof(double) * (size_t)n, s));
+    }
+    dependency_kernel<<<grid_for(n, kThreads), kThreads, 0, s>>>(list, n, h->acc, h->sigma,
+                                                                h->delta, h->xval, bc, src);
+    CG_LAUNCH_CHECK();
+  }
+  h->last_source = src;
+  return CG_OK;
+}
+
+}  // namespace
+}  // namespace cg
+
+using namespace cg;
+
+extern "C" {
+
+int cg_transpose_csr(const int64_t* in_offsets, const int32_t* in_src, int32_t V, int64_t E,
+                     int64_t* out_offsets, int32_t* out_dst, cudaStream_t stream) {
+  CG_ARG(V >= 1 && E >= 0 && E < 0x7FFFFFFFLL, "cg_transpose_csr: V >= 1 and 0 <= E < 2^31-1");
+  CG_ARG(in_offsets && out_offsets && (E == 0 || (in_src && out_dst)),
+         "cg_transpose_csr: null pointer argument");
+  CG_TRY(validate_csr(in_offsets, in_src, V, E, stream));
+  int32_t* deg = nullptr;
+  int32_t* rows = nullptr;
+  uint32_t* kout = nullptr;
+  cudaError_t e = cudaMallocAsync((void**)&deg, sizeof(int32_t) * (size_t)V, stream);
+  int st = e == cudaSuccess ? CG_OK : cuda_fail(e, "cg_transpose_csr", __FILE__, __LINE__);
+  if (st == CG_OK) st = cg_out_degree(in_src, E, V, deg, stream);
+  if (st == CG_OK) st = exclusive_scan_i32_to_i64(deg, out_offsets, V, stream);
+  if (st == CG_OK && E > 0) {
+    e = cudaMallocAsync((void**)&rows, sizeof(int32_t) * (size_t)E, stream);
+    if (e == cudaSuccess) e = cudaMallocAsync((void**)&kout, sizeof(uint32_t) * (size_t)E, stream);
+    if (e == cudaSuccess) {
+      row_of_edge_kernel<<<grid_for((int64_t)V * 32, 256), 256, 0, stream>>>(in_offsets, V, rows);
+      e = cudaGetLastError();
+    }
+    if (e != cudaSuccess) st = cuda_fail(e, "cg_transpose_csr", __FILE__, __LINE__);
+    int bits = 1;
+    while (bits < 32 && (int64_t(1) << bits) < (int64_t)V) ++bits;
+    // stable sort of the edges by source keeps each out-row in ascending
+    // destination order (the in-edge CSR lists its rows in that order)
+    if (st == CG_OK)
+      st = radix_sort_pairs(reinterpret_cast<const uint32_t*>(in_src), rows, kout, out_dst, E,
+                            bits, stream);
+  }
+  if (deg) cudaFreeAsync(deg, stream);
+  if (rows) cudaFreeAsync(rows, stream);
+  if (kout) cudaFreeAsync(kout, stream);
+  return st;
+}
+
+int bc_create(const int64_t* in_offsets, const int32_t* in_src, const int64_t* out_offsets,
+              const int32_t* out_dst, int32_t V, int64_t E, cg_bc** out, cudaStream_t stream) {
+  CG_ARG(out != nullptr, "bc_create: out is NULL");
+  *out = nullptr;
+  CG_ARG(V >= 1 && E >= 0 && E < 0x7FFFFFFFLL, "bc_create: V >= 1 and 0 <= E < 2^31-1");
+  CG_ARG(in_offsets && out_offsets && (E == 0 || (in_src && out_dst)),
+         "bc_create: null pointer argument");
+  CG_TRY(validate_csr(in_offsets, in_src, V, E, stream));
+  CG_TRY(validate_csr(out_offsets, out_dst, V, E, stream));
+  cg_bc* h = new cg_bc();
+  cudaGetDevice(&h->device);
+  h->V = V;
+  h->E = E;
+  h->in_off = in_offsets;
+  h->in_src = in_src;
+  h->out_off = out_offsets;
+  h->out_dst = out_dst;
+  const size_t v4 = sizeof(int32_t) * (size_t)V, v8 = sizeof(double) * (size_t)V;
+  cudaError_t e = cudaMalloc((void**)&h->level, v4);
+  if (e == cudaSuccess) e = cudaMalloc((void**)&h->sigma, v8);
+  if (e == cudaSuccess) e = cudaMalloc((void**)&h->delta, v8);
+  if (e == cudaSuccess) e = cudaMalloc((void**)&h->xval, v8);
+  if (e == cudaSuccess) e = cudaMalloc((void**)&h->acc, v8);
+  if (e == cudaSuccess) e = cudaMalloc((void**)&h->lists, v4);
+  if (e == cudaSuccess) e = cudaMalloc((void**)&h->deg, v4);
+  if (e == cudaSuccess) e = cudaMalloc((void**)&h->rend, sizeof(int64_t) * ((size_t)V + 1));
+  if (e == cudaSuccess) e = cudaMalloc((void**)&h->col_v, sizeof(int32_t) * (size_t)(E > 0 ? E : 1));
+  if (e == cudaSuccess) e = cudaMalloc((void**)&h->counter, sizeof(int32_t));
+  if (e == cudaSuccess) e = cudaMalloc((void**)&h->ids, v4);
+  if (e == cudaSuccess) e = cudaMalloc((void**)&h->keys, v4);
+  if (e == cudaSuccess) e = cudaMalloc((void**)&h->keys_out, v4);
+  if (e == cudaSuccess) e = cudaHostAlloc((void**)&h->h_pin, 2 * sizeof(int64_t), 0);
+  int st = e == cudaSuccess ? CG_OK : cuda_fail(e, "bc_create", __FILE__, __LINE__);
+  if (st == CG_OK) st = plan_tiles<int64_t>(in_offsets + 1, V, E, &h->in_plan, stream, 8);
+  if (st == CG_OK) {
+    e = cudaStreamSynchronize(stream);
+    if (e != cudaSuccess) st = cuda_fail(e, "bc_create", __FILE__, __LINE__);
+  }
+  if (st != CG_OK) {
+    bc_destroy(h);
+    return st;
+  }
+  *out = h;
+  return CG_OK;
+}
+
+int bc_destroy(cg_bc* h) {
+  if (!h) return CG_OK;
+  int cur = 0;
+  cudaGetDevice(&cur);
+  if (cur != h->device) cudaSetDevice(h->device);
+  cudaDeviceSynchronize();
+  free_tile_plan(&h->in_plan);
+  cudaFree(h->level);
+  cudaFree(h->sigma);
+  cudaFree(h->delta);
+  cudaFree(h->xval);
+  cudaFree(h->acc);
+  cudaFree(h->lists);
+  cudaFree(h->deg);
+  cudaFree(h->rend);
+  cudaFree(h->col_v);
+  cudaFree(h->counter);
+  cudaFree(h->ids);
+  cudaFree(h->keys);
+  cudaFree(h->keys_out);
+  cudaFree(h->vt_row);
+  cudaFree(h->vt_edge);
+  cudaFree(h->vt_carry);
+  cudaFree(h->vt_carry_row);
+  if (h->h_pin) cudaFreeHost(h->h_pin);
+  if (cur != h->device) cudaSetDevice(cur);
+  delete h;
+  return CG_OK;
+}
+
+int bc_set_direction(cg_bc* h, double alpha) {
+  CG_ARG(h != nullptr, "bc_set_direction: null handle");
+  CG_ARG(alpha >= 0.0, "bc_set_direction: alpha must be >= 0");
+  h->alpha = alpha;
+  return CG_OK;
+}
+
+int bc_run(cg_bc* h, const int32_t* sources, int32_t nsources, double* bc, cudaStream_t stream) {
+  CG_ARG(h != nullptr, "bc_run: null handle");
+  CG_ARG(nsources >= 0 && (nsources == 0 || sources) && bc, "bc_run: bad arguments");
+  for (int32_t i = 0; i < nsources; ++i)
+    CG_ARG(sources[i] >= 0 && sources[i] < h->V, "bc_run: source %d outside [0, %d)",
+           sources[i], h->V);
+  for (int32_t i = 0; i < nsources; ++i) CG_TRY(run_source(h, sources[i], bc, stream));
+  return CG_OK;
+}
+
+int bc_source_state(const cg_bc* h, int32_t* level, double* sigma, double* delta,
+                    int32_t* depth, int32_t* push_levels, int32_t* pull_levels,
+                    cudaStream_t stream) {
+  CG_ARG(h != nullptr, "bc_source_state: null handle");
+  CG_ARG(h->last_source >= 0, "bc_source_state: no source has run yet");
+  const size_t v4 = sizeof(int32_t) * (size_t)h->V, v8 = sizeof(double) * (size_t)h->V;
+  if (level) CG_CUDA(cudaMemcpyAsync(level, h->level, v4, cudaMemcpyDeviceToDevice, stream));
+  if (sigma) CG_CUDA(cudaMemcpyAsync(sigma, h->sigma, v8, cudaMemcpyDeviceToDevice, stream));
+  if (delta) CG_CUDA(cudaMemcpyAsync(delta, h->delta, v8, cudaMemcpyDeviceToDevice, stream));
+  if (depth) *depth = (int32_t)h->lbase.size() - 1;
+  if (push_levels) *push_levels = h->push_levels;
+  if (pull_levels) *pull_levels = h->pull_levels;
+  return CG_OK;
+}
+
+}  // extern "C"

@@ -34,6 +34,15 @@ struct SumF32 {
   static __device__ __forceinline__ T op(T a, T b) { return a + b; }
   static __device__ __forceinline__ void atomic_op(T* p, T v) { *p = op(*p, v); }
 };
+// FP64 sums (betweenness centrality: path counts, which are exact integers in
+// any order below 2^53, and dependencies).
+struct SumF64 {
+  using T = double;
+  static constexpr bool kExactAnyOrder = false;
+  static __device__ __forceinline__ T identity() { return 0.0; }
+  static __device__ __forceinline__ T op(T a, T b) { return a + b; }
+  static __device__ __forceinline__ void atomic_op(T* p, T v) { *p = op(*p, v); }
+};
 struct MinI32 {
   using T = int32_t;
   static constexpr bool kExactAnyOrder = true;
@@ -98,7 +107,15 @@ gather_tile_kernel(const RowEndT* __restrict__ row_end, const int32_t* __restric
   constexpr int WARPS = THREADS / 32;
   constexpr int PADT = TILE + TILE / 32;
   __shared__ T s_val[PADT];
-  __shared__ int32_t s_rend[PADT];  // row ends (relative), later row results (as T bits)
+  __shared__ int32_t s_rend[PADT];  // row ends relative to the tile's first edge
+  // Row results.  A row emitted during the walk lies wholly inside the
+  // emitting thread's items (a row that began in an earlier thread's items is
+  // the thread's first row, written only after the block scan), so no other
+  // thread reads its end any more and a 4-byte result can take its place.  An
+  // 8-byte result written there would cover two row ends, one of them
+  // possibly another thread's current row: wider values get their own array.
+  __shared__ T s_res_wide[sizeof(T) > 4 ? PADT : 1];
+  T* s_res = sizeof(T) > 4 ? s_res_wide : reinterpret_cast<T*>(s_rend);
   __shared__ T s_wval[WARPS];
   __shared__ int32_t s_wrow[WARPS];
   __shared__ T s_prev_val[THREADS];
@@ -147,7 +164,7 @@ gather_tile_kernel(const RowEndT* __restrict__ row_end, const int32_t* __restric
   const int d1 = d0 + IPT < items ? d0 + IPT : items;
   int i = (int)merge_path_search<true, int32_t>(d0, s_rend, nr, ne, 0);
   int j = d0 - i;
-  __syncthreads();  // all searches done before row results overwrite s_rend
+  __syncthreads();  // every search is done before row results replace row ends
   const int first_row = i;
   bool emitted = false;
   T first_val = Op::identity();
@@ -158,7 +175,7 @@ gather_tile_kernel(const RowEndT* __restrict__ row_end, const int32_t* __restric
         first_val = acc;
         emitted = true;
       } else {
-        reinterpret_cast<T*>(s_rend)[pad32(i)] = acc;
+        s_res[pad32(i)] = acc;
       }
       acc = Op::identity();
       ++i;
@@ -203,12 +220,12 @@ gather_tile_kernel(const RowEndT* __restrict__ row_end, const int32_t* __restric
   if (emitted) {
     T v = first_val;
     if (tid > 0 && s_prev_row[tid - 1] == first_row) v = Op::op(s_prev_val[tid - 1], v);
-    reinterpret_cast<T*>(s_rend)[pad32(first_row)] = v;
+    s_res[pad32(first_row)] = v;
   }
   __syncthreads();
 
   // 5. coalesced row results; tile carry for the row open at the tile end
-  for (int r = tid; r < nr; r += THREADS) out[r0 + r] = reinterpret_cast<T*>(s_rend)[pad32(r)];
+  for (int r = tid; r < nr; r += THREADS) out[r0 + r] = s_res[pad32(r)];
   if (tid == THREADS - 1) {
     carry[t] = cval;     // the last thread's inclusive value is the open row's tile part
     carry_row[t] = r0 + crow;
@@ -247,9 +264,10 @@ constexpr int kTileIPT = 8;
 constexpr int kTileItems = kTileThreads * kTileIPT;
 
 // Allocate and fill a plan (cudaMalloc: the plan lives with its handle).
+// carry_bytes: size of the gathered values (4, or 8 for SumF64).
 template <typename RowEndT>
 int plan_tiles(const RowEndT* row_end, int64_t nrows, int64_t nedges, TilePlan* p,
-                cudaStream_t s) {
+                cudaStream_t s, int carry_bytes = 4) {
   p->nrows = nrows;
   p->nedges = nedges;
   p->tile = kTileItems;
@@ -257,7 +275,7 @@ int plan_tiles(const RowEndT* row_end, int64_t nrows, int64_t nedges, TilePlan* 
   const size_t nb = sizeof(int32_t) * (size_t)(p->ntiles + 1);
   CG_CUDA(cudaMalloc((void**)&p->tile_row, nb));
   CG_CUDA(cudaMalloc((void**)&p->tile_edge, nb));
-  CG_CUDA(cudaMalloc(&p->carry, nb));
+  CG_CUDA(cudaMalloc(&p->carry, (size_t)carry_bytes * (size_t)(p->ntiles + 1)));
   CG_CUDA(cudaMalloc((void**)&p->carry_row, nb));
   tile_partition_kernel<RowEndT><<<grid_for(p->ntiles + 1, 256), 256, 0, s>>>(
       row_end, nrows, nedges, kTileItems, p->ntiles, p->tile_row, p->tile_edge);

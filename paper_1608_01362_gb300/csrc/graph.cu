@@ -91,12 +91,13 @@ __global__ void permute_rows_kernel(const uint4* __restrict__ in, const int32_t*
   }
 }
 
-__global__ void permute4_kernel(const uint32_t* __restrict__ in, const int32_t* __restrict__ idx,
-                                int64_t n, int64_t n_in, uint32_t* __restrict__ out) {
+template <typename W>
+__global__ void permute_kernel(const W* __restrict__ in, const int32_t* __restrict__ idx,
+                               int64_t n, int64_t n_in, W* __restrict__ out) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
     const int32_t j = idx[i];
-    out[i] = (j >= 0 && j < n_in) ? in[j] : 0u;
+    out[i] = (j >= 0 && j < n_in) ? in[j] : W(0);
   }
 }
 
@@ -168,8 +169,21 @@ int cg_permute4(const void* in, int64_t n_in, const int32_t* idx, int64_t n, voi
   CG_ARG(n >= 0 && n_in >= 0, "cg_permute4: negative size");
   if (n == 0) return CG_OK;
   CG_ARG(in && idx && out && in != out, "cg_permute4: null or aliased pointer");
-  permute4_kernel<<<grid_for(n, 256), 256, 0, stream>>>((const uint32_t*)in, idx, n, n_in,
-                                                        (uint32_t*)out);
+  permute_kernel<uint32_t><<<grid_for(n, 256), 256, 0, stream>>>((const uint32_t*)in, idx, n,
+                                                                 n_in, (uint32_t*)out);
+  CG_LAUNCH_CHECK();
+  return CG_OK;
+}
+
+int cg_permute8(const void* in, int64_t n_in, const int32_t* idx, int64_t n, void* out,
+                cudaStream_t stream) {
+  CG_ARG(n >= 0 && n_in >= 0, "cg_permute8: negative size");
+  if (n == 0) return CG_OK;
+  CG_ARG(in && idx && out && in != out, "cg_permute8: null or aliased pointer");
+  CG_ARG(((uintptr_t)in & 7) == 0 && ((uintptr_t)out & 7) == 0,
+         "cg_permute8: buffers must be 8-byte aligned");
+  permute_kernel<uint64_t><<<grid_for(n, 256), 256, 0, stream>>>((const uint64_t*)in, idx, n,
+                                                                 n_in, (uint64_t*)out);
   CG_LAUNCH_CHECK();
   return CG_OK;
 }

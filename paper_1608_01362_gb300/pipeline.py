@@ -298,6 +298,45 @@ class LabelPropagation:
         return self.g.to_original(lab), passes, changes
 
 
+class Betweenness:
+    """Betweenness centrality from a set of sources (Brandes over frontiers)
+    on a Graph (clustered or not): the out-edge CSR is built on the GPU by
+    cg_transpose_csr.  Sources and results are in original vertex IDs."""
+
+    def __init__(self, graph: Graph, alpha: float | None = None):
+        self.g = graph
+        self.out_off = torch.empty_like(graph.offsets)
+        self.out_dst = torch.empty_like(graph.src)
+        C.cg_transpose_csr(graph.offsets, graph.src, self.out_off, self.out_dst)
+        self.h = C.bc_create(graph.offsets, graph.src, self.out_off, self.out_dst)
+        if alpha is not None:
+            C.bc_set_direction(self.h, alpha)
+        self.bc = torch.zeros(graph.V, dtype=torch.float64, device=graph.device)
+
+    def run(self, sources):
+        """Centrality of every vertex from `sources` (original IDs), FP64,
+        in original vertex IDs."""
+        self.bc.zero_()
+        C.bc_run(self.h, [self.g.to_clustered_id(int(s)) for s in sources], self.bc)
+        return self.to_original8(self.bc)
+
+    def to_original8(self, x):
+        if self.g.new_of_old is None:
+            return x
+        out = torch.empty_like(x)
+        C.cg_permute8(x, self.g.new_of_old, out)
+        return out
+
+    def source_state(self):
+        """(level int32, sigma, delta) of the last source, original IDs."""
+        V, dev = self.g.V, self.g.device
+        lev = torch.empty(V, dtype=torch.int32, device=dev)
+        sig = torch.empty(V, dtype=torch.float64, device=dev)
+        dl = torch.empty(V, dtype=torch.float64, device=dev)
+        info = C.bc_source_state(self.h, lev, sig, dl)
+        return self.g.to_original(lev), self.to_original8(sig), self.to_original8(dl), info
+
+
 def concat_graphs(graphs):
     """Concatenate in-edge CSRs (numpy offsets int64, src int32, local IDs)
     into the batched layout: (vbase, global offsets, local sources)."""

@@ -170,3 +170,29 @@ def test_batched_1024_graphs_sampled(env):
     for i in range(0, 1024, 32):
         want, bound = O.pagerank_bound(gs[i].offsets, gs[i].src, iters=20)
         check_pagerank(rank[bpr.vbase[i]:bpr.vbase[i + 1]], want, bound, what=f"graph {i}")
+
+
+def test_betweenness_rmat25_two_sources(env, rmat25):
+    """Betweenness centrality on RMAT-25 (clustered) from the bench's first two
+    sources: per source the levels and path counts equal the oracle's bit for
+    bit and the dependencies lie within the FP64 bound of tests/test_gpu_bc.py."""
+    torch, C, P = env
+    import bench
+    g = rmat25[0]
+    S = bench.ppr_seeds(g, n=12)[:2]
+    graph = P.Graph(g.offsets, g.src, cluster_mode=0)
+    bc = P.Betweenness(graph)
+    out_off, out_dst = O.out_csr(g.offsets, g.src)
+    maxdeg = int(np.diff(out_off).max())
+    for s in S:
+        lev, sig, dl, depth = O.bc_source(out_off, out_dst, int(s))
+        bc.run([int(s)])
+        glev, gsig, gdl, info = bc.source_state()
+        assert info["depth"] == depth
+        assert np.array_equal(glev.cpu().numpy(), lev)
+        assert sig.max() < 2.0 ** 53
+        assert np.array_equal(gsig.cpu().numpy(), sig)
+        tol = 2.0 * depth * (maxdeg + 8) * 2.0 ** -53
+        assert np.all(np.abs(gdl.cpu().numpy() - dl) <= tol * dl + 1e-300)
+    del bc, graph
+    torch.cuda.empty_cache()
