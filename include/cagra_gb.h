@@ -594,6 +594,41 @@ int pr_iterate_plain_noalloc(const int64_t *dev_offsets, const int32_t *dev_src,
                              double damping, double *dev_dangling_io,
                              double *dev_resid, cudaStream_t stream);
 
+/*
+ * Dense hub block of the batched personalised PageRank on the tensor cores.
+ * After frequency-based clustering (Section V) the hottest vertices carry the
+ * lowest IDs and the block of the adjacency matrix among vertices [0, h) is
+ * dense; its share of the batched gather becomes a contraction Y = A_H C_H
+ * (A_H: the 0/1 hub block, row = destination; C_H: the hubs' 64-column
+ * contributions in BF16 hi and lo planes), computed with tcgen05.mma (BF16
+ * operands, FP32 accumulators in tensor memory) and added by the merge as one
+ * more intermBuf row per hub destination.  Not in the paper (it extends the
+ * batched form of Algorithm 3).
+ *
+ * cg_split_hub_block: splits an in-edge CSR (validated; V >= h, h a positive
+ * multiple of 128) into the rest (dev_out_offsets int64[V+1], dev_out_src
+ * int32[E] capacity: every edge with source or destination >= h, in the input
+ * order) and the hub block as a bitmap dev_bits uint32[h][h/32] (bit u of row
+ * v set when u -> v, u, v < h; overwritten).  *host_E_rest receives the rest's
+ * edge count.  Synchronizes.
+ *
+ * ppr_batched_attach_dense: attaches such a block to a batched handle built
+ * over the rest's segmented graph (same V and vertex numbering).  dev_bits is
+ * caller-owned and must stay valid while the handle is used.  Each
+ * ppr_batched_step's gather phase then also runs the tensor-core launch (one
+ * 128-thread CTA per 128 hub destinations; 64-source chunks without an edge
+ * in a tile are skipped), and each merge phase repacks the hubs'
+ * contributions into the operand layout.  CG_ERR_UNSUPPORTED on a GPU without
+ * tcgen05 (compute capability other than 10.x); CG_ERR_INVALID_ARG on a bad h
+ * or a second attach.  A launch whose bounded waits (operand copies, tensor
+ * work) give up records a fault; the next step returns CG_ERR_TIMEOUT.
+ */
+int cg_split_hub_block(const int64_t *dev_in_offsets, const int32_t *dev_in_src, int32_t V,
+                       int64_t E, int32_t h, int64_t *dev_out_offsets, int32_t *dev_out_src,
+                       uint32_t *dev_bits, int64_t *host_E_rest, cudaStream_t stream);
+int ppr_batched_attach_dense(cg_ppr *ppr, int32_t h, const uint32_t *dev_bits,
+                             cudaStream_t stream);
+
 /* ------------------------------------------------ betweenness centrality */
 
 /*

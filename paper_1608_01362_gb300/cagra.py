@@ -39,7 +39,7 @@ EXPORTS = [
     "cf_transpose", "cf_create", "cf_destroy", "cf_set_factors", "cf_get_factors", "cf_sweep",
     "cf_sweep_phase", "cf_info", "cg_measure_row_gather", "cg_measure_smem_lookups",
     "cg_permute8", "cg_transpose_csr", "bc_create", "bc_destroy", "bc_set_direction", "bc_run",
-    "bc_source_state",
+    "bc_source_state", "cg_split_hub_block", "ppr_batched_attach_dense",
 ]
 
 
@@ -128,6 +128,9 @@ def load(path: str | None = None):
             "cf_sweep_phase": (ctypes.c_int, [vp, i32, dbl, dbl, vp, vp]),
             "cf_info": (ctypes.c_int, [vp, vp, vp, vp, vp]),
             "cg_transpose_csr": (ctypes.c_int, [vp, vp, i32, i64, vp, vp, vp]),
+            "cg_split_hub_block": (ctypes.c_int, [vp, vp, i32, i64, i32, vp, vp, vp,
+                                                  ctypes.POINTER(i64), vp]),
+            "ppr_batched_attach_dense": (ctypes.c_int, [vp, i32, vp, vp]),
             "bc_create": (ctypes.c_int, [vp, vp, vp, vp, i32, i64, ctypes.POINTER(vp), vp]),
             "bc_destroy": (ctypes.c_int, [vp]),
             "bc_set_direction": (ctypes.c_int, [vp, dbl]),
@@ -610,6 +613,24 @@ def pr_batch_set_threads(batch: Batch, threads: int):
 def pr_batch_run(batch: Batch, iterations: int, damping: float, rank, resid=None, stream=None):
     _check(load().pr_batch_run(batch.handle, iterations, damping, _ptr(rank), _ptr(resid),
                                _stream(stream)), "pr_batch_run")
+
+
+def cg_split_hub_block(offsets, src, h: int, out_offsets, out_src, bits, stream=None) -> int:
+    """Hub block [0, h) x [0, h) of an in-edge CSR into a bitmap, the rest into
+    (out_offsets, out_src); returns the rest's edge count."""
+    V = offsets.numel() - 1
+    er = ctypes.c_int64()
+    _check(load().cg_split_hub_block(_ptr(offsets), _ptr(src) if src.numel() else None, V,
+                                     src.numel(), int(h), _ptr(out_offsets),
+                                     _ptr(out_src) if out_src.numel() else None, _ptr(bits),
+                                     ctypes.byref(er), _stream(stream)), "cg_split_hub_block")
+    return int(er.value)
+
+
+def ppr_batched_attach_dense(ppr, h: int, bits, stream=None):
+    _check(load().ppr_batched_attach_dense(ppr.handle, int(h), _ptr(bits), _stream(stream)),
+           "ppr_batched_attach_dense")
+    ppr._dense_bits = bits  # keep the bitmap alive with the handle
 
 
 # ------------------------------------------------------------------ betweenness centrality

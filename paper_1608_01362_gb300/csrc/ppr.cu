@@ -30,60 +30,7 @@
 //                      rows, in segment order), applies the update and
 //                      writes C' (and R'), with per-column FP64 partials
 //                      reduced by the last block.
-#include <cuda_bf16.h>
-
-#include <algorithm>
-#include <vector>
-
-#include "handles.cuh"
-
-namespace cg {
-
-constexpr int kCols = 64;         // columns (rank vectors) per batch
-constexpr int kChunk = 128;       // edges per octet chunk in the gather
-constexpr int kTask = 16;         // destinations per octet task in the merge
-constexpr int kThreads = 256;     // threads per block of every kernel here
-constexpr uint32_t kRowEnd = 0x80000000u;
-
-struct PprSeg {
-  int64_t cstart;  // first flagged-edge entry of the segment
-  int64_t chunk0;  // first gather chunk of the segment
-  int32_t lo;      // first source vertex of the segment
-  int32_t E;       // edges of the segment
-};
-
-}  // namespace cg
-
-struct cg_ppr {
-  int device = 0;
-  const cg_segmented* seg = nullptr;
-  int32_t V = 0;
-  int32_t k = 0;
-  int32_t planes = 2;
-  int64_t rows = 0, nchunks = 0;
-  cg::PprSeg* segs = nullptr;    // [k]
-  int2* chunks = nullptr;        // [nchunks] (first subgraph row, segment)
-  float* carry = nullptr;        // [nchunks][64]
-  int4* pieces = nullptr;        // [npieces] (first chunk, chunks, run, -)
-  int4* runs = nullptr;          // [nruns] (row, first piece, pieces, -)
-  float* piece_sum = nullptr;    // [npieces][64]
-  unsigned* run_done = nullptr;  // [nruns] pieces of the run finished (last-piece detection)
-  int64_t npieces = 0, nruns = 0;
-  int32_t* dst_off = nullptr;    // [V+1] destination-major row lists
-  int32_t* dst_rows = nullptr;   // [rows]
-  float* interm = nullptr;       // [rows][64] intermBuf
-  uint4* c_hi = nullptr;         // [V][64] bf16
-  uint4* c_lo = nullptr;         // [V][64] bf16 (two planes only)
-  float* r_prev = nullptr;       // [V][64] R of the second-to-last iteration
-  int32_t* seeds = nullptr;      // [64]
-  uint32_t* seed_bits = nullptr; // [ceil(V/32)] vertices that are some column's seed
-  double* D = nullptr;           // [64] dangling mass per column
-  double* partials = nullptr;    // [merge_grid][128]
-  unsigned* counter = nullptr;
-  int merge_grid = 0, gather_grid = 0;
-  bool seeded = false;
-  int64_t bytes = 0;
-};
+#include "ppr.cuh"
 
 namespace cg {
 namespace {
@@ -592,6 +539,7 @@ int fixup_launch(cg_ppr* p, cudaStream_t s) {
 }
 
 void ppr_free(cg_ppr* p) {
+  ppr_dense_free(p);
   cudaFree(p->segs);
   cudaFree(p->chunks);
   cudaFree(p->carry);
@@ -807,6 +755,7 @@ int ppr_batched_init(cg_ppr* p, const float* inv, const int32_t* host_seeds,
                                            reinterpret_cast<__nv_bfloat16*>(p->c_lo),
                                            p->seed_bits, p->D);
   CG_LAUNCH_CHECK();
+  CG_TRY(ppr_dense_pack(p, stream));
   // host_seeds may go out of scope on return
   CG_CUDA(cudaStreamSynchronize(stream));
   p->seeded = true;
@@ -824,9 +773,15 @@ int ppr_batched_step(cg_ppr* p, const float* inv, double damping, int32_t phases
   CG_ARG(!rank_old || rank_out, "ppr_batched_step: rank_old needs rank_out");
   CG_ARG(!rank_out || (const float*)rank_out != rank_old,
          "ppr_batched_step: rank_out must not alias rank_old");
-  if (phases & 1) CG_TRY(gather_launch(p, stream));
+  if (phases & 1) {
+    CG_TRY(gather_launch(p, stream));
+    CG_TRY(ppr_dense_launch(p, stream));  // the hub block's rows (if attached)
+  }
   if (phases & 2) CG_TRY(fixup_launch(p, stream));
-  if (phases & 4) CG_TRY(merge_launch(p, inv, damping, rank_out, rank_old, resid, stream));
+  if (phases & 4) {
+    CG_TRY(merge_launch(p, inv, damping, rank_out, rank_old, resid, stream));
+    CG_TRY(ppr_dense_pack(p, stream));
+  }
   return CG_OK;
 }
 

@@ -148,17 +148,31 @@ class SegmentedPageRank(_PageRankBase):
 
 
 class BatchedPPR:
-    """64 personalised PageRank vectors through one segmented graph."""
+    """64 personalised PageRank vectors through one segmented graph.
+    dense_hubs = h > 0 takes the block among vertices [0, h) (the hottest after
+    clustering) out of the gather and onto the tensor cores."""
 
     def __init__(self, graph: Graph, num_segments: int | None = None, bounds=None,
-                 planes: int = 2, merge_block: int = 512):
+                 planes: int = 2, merge_block: int = 512, dense_hubs: int = 0):
         self.g = graph
         if bounds is not None:
             bounds = np.asarray(bounds, dtype=np.int64)
             num_segments = len(bounds) - 1
-        self.seg = C.pr_build_segments(graph.offsets, graph.src, num_segments, bounds=bounds,
+        off, src = graph.offsets, graph.src
+        self.dense_hubs = int(dense_hubs)
+        if self.dense_hubs:
+            h = self.dense_hubs
+            self.rest_off = torch.empty_like(off)
+            rest = torch.empty_like(src)
+            self.bits = torch.empty(h * (h // 32), dtype=torch.int32, device=graph.device)
+            er = C.cg_split_hub_block(off, src, h, self.rest_off, rest, self.bits)
+            self.rest_src = rest[:er].contiguous()
+            off, src = self.rest_off, self.rest_src
+        self.seg = C.pr_build_segments(off, src, num_segments, bounds=bounds,
                                        merge_block=merge_block)
         self.ppr = C.ppr_batched_create(self.seg, planes)
+        if self.dense_hubs:
+            C.ppr_batched_attach_dense(self.ppr, self.dense_hubs, self.bits)
         self.rank = torch.empty((graph.V, C.PPR_COLUMNS), dtype=torch.float32,
                                 device=graph.device)
         self.resid = torch.zeros(C.PPR_COLUMNS, dtype=torch.float64, device=graph.device)
