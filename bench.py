@@ -543,7 +543,18 @@ def run_ppr(args):
             if planes == 2 and (best is None or t < tune[f"planes2_k{best}"]["ms_per_iter"] / 1e3):
                 best = k
             del b
-    b = P.BatchedPPR(graph, bounds=_ppr_bounds(nd, graph.V, best), planes=2)
+    # the dense hub block on the tensor cores: its size (0: none)
+    best_h = args.dense if args.dense >= 0 else None
+    if best_h is None:
+        for hh in (0, 4096, 8192, 16384, 32768):
+            b = P.BatchedPPR(graph, bounds=_ppr_bounds(nd, graph.V, best), planes=2,
+                             dense_hubs=hh)
+            t = time_solve(b, reps=1, iters=5)
+            tune[f"dense_h{hh}"] = {"ms_per_iter": t * 1e3, "q": b.seg.info["q"]}
+            if best_h is None or t < tune[f"dense_h{best_h}"]["ms_per_iter"] / 1e3:
+                best_h = hh
+            del b
+    b = P.BatchedPPR(graph, bounds=_ppr_bounds(nd, graph.V, best), planes=2, dense_hubs=best_h)
     info = b.seg.info
     # timed: steps x (init + 20 iterations), inputs resident in HBM (the
     # 1 GB rank matrix and 0.5 GB BF16 planes exceed L2: no flush needed)
@@ -564,12 +575,14 @@ def run_ppr(args):
     t_step = a.elapsed_time(z) / 1e3 / args.steps
     # per launch of one iteration
     phase_ms = {}
-    for ph, name in ((1, "gather"), (2, "fixup"), (4, "merge")):
+    for ph, name in ((1, "gather"), (8, "dense_tensor_core"), (2, "fixup"), (4, "merge")):
+        if ph == 8 and not best_h:
+            continue
         b.init(seeds)
         C.ppr_batched_iterate(b.ppr, graph.inv, DAMPING, 2)
         ts = []
         for _ in range(5):
-            C.ppr_batched_step(b.ppr, graph.inv, DAMPING, 7 - ph)  # the others, untimed
+            C.ppr_batched_step(b.ppr, graph.inv, DAMPING, 15 - ph)  # the others, untimed
             e0, e1 = ev(), ev()
             e0.record()
             C.ppr_batched_step(b.ppr, graph.inv, DAMPING, ph)
@@ -587,6 +600,36 @@ def run_ppr(args):
     want = oracle.ppr(g.offsets, g.src, seeds[cols], iters=ITERS)
     oracle_s = time.time() - t0
     err = np.abs(Rh[:, cols].astype(np.float64) - want).sum(0) / np.abs(want).sum(0)
+    # per entry: the FP64 rounding bound (accumulation 2^-23 when the tensor
+    # cores add the hub block: a truncating FP32 sum at most doubles each
+    # addition's relative error)
+    u_acc = 2.0 ** -23 if best_h else oracle.U_FP32
+    worst, outside = 0.0, 0
+    for j, c in enumerate(cols):
+        _, bnd = oracle.pagerank_bound(g.offsets, g.src, iters=ITERS, seed=int(seeds[c]),
+                                       u_acc=u_acc, u_store=oracle.U_BF16X2)
+        e = np.abs(Rh[:, c].astype(np.float64) - want[:, j])
+        m = bnd > 0
+        worst = max(worst, float(np.max(e[m] / bnd[m])))
+        outside += int(np.count_nonzero(e > bnd))
+    dense_rec = None
+    if best_h:
+        # 64-source chunks with an edge in each 128-destination tile (the MMAs issued)
+        hb = b.bits.reshape(best_h // 128, 128, best_h // 64, 2)
+        nz_chunks = int((hb != 0).any(dim=3).any(dim=1).sum().item())
+        flops = nz_chunks * 128 * 64 * 64 * 2 * 2
+        t_d = phase_ms["dense_tensor_core"] / 1e3
+        try:
+            with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+                bf16_peak, bf16_kind = float(json.load(f)["bf16_tflops"]), "measured"
+        except Exception:
+            bf16_peak, bf16_kind = 1900.0, "fallback"
+        dense_rec = {"hubs": best_h, "hub_block_edges": int(g.E - b.rest_src.numel()),
+                     "hub_block_edge_share": float((g.E - b.rest_src.numel()) / g.E),
+                     "tile_chunks": nz_chunks, "mma_flops": flops,
+                     "tflops": flops / t_d / 1e12, "bf16_peak_tflops": bf16_peak,
+                     "peak_kind": bf16_kind, "frac": flops / t_d / 1e12 / bf16_peak,
+                     "ms": t_d * 1e3}
     # 64 single-vector solves through the segmented PageRank path
     cand, _ = P.autotune_segments(graph)
     sp = P.build_candidate(graph, cand)
@@ -637,7 +680,7 @@ def run_ppr(args):
             "data": "synthetic",
             "config": {"workload": f"ppr64_rmat{scale}_ef16", "V": g.V, "E": g.E,
                        "nondangling": nd, "segments": info["num_segments"], "q": info["q"],
-                       "planes": 2, "l2_flush": "inputs larger than L2"},
+                       "planes": 2, "dense_hubs": best_h, "l2_flush": "inputs larger than L2"},
             "vs_baseline": None,
             "kernels_ms_per_iteration": phase_ms,
             "roofline": {"bound": "hbm", "kernel": dom, "achieved": ach, "peak": peak,
@@ -647,6 +690,9 @@ def run_ppr(args):
             "single_vector_64_runs_ms": t_single * 1e3,
             "speedup_vs_64_single_runs": t_single / t_step,
             "rel_l1_vs_oracle_sampled_columns": {int(c): float(e) for c, e in zip(cols, err)},
+            "sampled_columns_max_err_over_bound": worst,
+            "sampled_columns_entries_outside_bound": outside,
+            "dense_hub_block": dense_rec,
             "single_vector_rel_l1_col0": err1,
             "autotune": tune, "clocks": clocks,
             "e2e": {"value": edge_cols / t_e2e / 1e9, "unit": "GTEPS (edge x vector)",
@@ -1273,6 +1319,9 @@ def main():
                     help="pagerank (the headline), lp (label propagation, RMAT-24 undirected) "
                          "or batched (1,024 small RMAT graphs, scales 8-15)")
     ap.add_argument("--graphs", type=int, default=1024, help="graphs of the batched workload")
+    ap.add_argument("--dense", type=int, default=-1,
+                    help="hub-block size for the tensor-core part of the ppr workload "
+                         "(-1: autotune over 0, 4096 .. 32768; 0: none)")
     ap.add_argument("--arm", default="segmented",
                     choices=["segmented", "plain_random", "plain_clustered"],
                     help="the arm the profile workload runs")

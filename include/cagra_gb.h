@@ -486,7 +486,9 @@ int ppr_batched_iterate(cg_ppr *ppr, const float *dev_inv, double damping,
 
 /*
  * One iteration's launches selected by `phases` (1 gather, 2 carry fix-up,
- * 4 merge + update; 7 = one whole iteration), for timing each launch.  The
+ * 4 merge + update, 8 the tensor-core hub block of ppr_batched_attach_dense;
+ * 15 = one whole iteration, 7 when no hub block is attached), for timing each
+ * launch; phases in [0, 15].  The
  * merge writes R' to dev_rank_out when non-NULL and, when dev_rank_old is
  * given, the per-column L1 distance to it in dev_resid (double[64], may be
  * NULL).
@@ -614,11 +616,11 @@ int pr_iterate_plain_noalloc(const int64_t *dev_offsets, const int32_t *dev_src,
  *
  * ppr_batched_attach_dense: attaches such a block to a batched handle built
  * over the rest's segmented graph (same V and vertex numbering).  dev_bits is
- * caller-owned and must stay valid while the handle is used.  Each
- * ppr_batched_step's gather phase then also runs the tensor-core launch (one
- * 128-thread CTA per 128 hub destinations; 64-source chunks without an edge
- * in a tile are skipped), and each merge phase repacks the hubs'
- * contributions into the operand layout.  CG_ERR_UNSUPPORTED on a GPU without
+ * caller-owned and must stay valid while the handle is used.  From then on
+ * ppr_batched_iterate also runs the tensor-core launch (phase 8 of
+ * ppr_batched_step: one 128-thread CTA per 128 hub destinations; 64-source
+ * chunks without an edge in a tile are skipped), and each merge phase repacks
+ * the hubs' contributions into the operand layout.  CG_ERR_UNSUPPORTED on a GPU without
  * tcgen05 (compute capability other than 10.x); CG_ERR_INVALID_ARG on a bad h
  * or a second attach.  A launch whose bounded waits (operand copies, tensor
  * work) give up records a fault; the next step returns CG_ERR_TIMEOUT.

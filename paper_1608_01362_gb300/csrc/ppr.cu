@@ -768,15 +768,13 @@ int ppr_batched_step(cg_ppr* p, const float* inv, double damping, int32_t phases
   CG_ARG(p && inv, "ppr_batched_step: null argument");
   CG_ARG(p->seeded, "ppr_batched_step: call ppr_batched_init first");
   CG_ARG(damping >= 0.0 && damping <= 1.0, "ppr_batched_step: damping must be in [0, 1]");
-  CG_ARG(phases >= 0 && phases <= 7, "ppr_batched_step: phases must be in [0, 7]");
+  CG_ARG(phases >= 0 && phases <= 15, "ppr_batched_step: phases must be in [0, 15]");
   CG_ARG(!resid || rank_old, "ppr_batched_step: the residual needs rank_old");
   CG_ARG(!rank_old || rank_out, "ppr_batched_step: rank_old needs rank_out");
   CG_ARG(!rank_out || (const float*)rank_out != rank_old,
          "ppr_batched_step: rank_out must not alias rank_old");
-  if (phases & 1) {
-    CG_TRY(gather_launch(p, stream));
-    CG_TRY(ppr_dense_launch(p, stream));  // the hub block's rows (if attached)
-  }
+  if (phases & 1) CG_TRY(gather_launch(p, stream));
+  if (phases & 8) CG_TRY(ppr_dense_launch(p, stream));  // the hub block's rows (if attached)
   if (phases & 2) CG_TRY(fixup_launch(p, stream));
   if (phases & 4) {
     CG_TRY(merge_launch(p, inv, damping, rank_out, rank_old, resid, stream));
@@ -796,7 +794,7 @@ int ppr_batched_iterate(cg_ppr* p, const float* inv, double damping, int32_t ite
     const bool before_last = t == iterations - 2 && resid;
     float* r_out = last ? rank_out : before_last ? p->r_prev : nullptr;
     const float* r_old = last && resid ? p->r_prev : nullptr;
-    CG_TRY(ppr_batched_step(p, inv, damping, 7, r_old, r_out, last ? resid : nullptr, stream));
+    CG_TRY(ppr_batched_step(p, inv, damping, 15, r_old, r_out, last ? resid : nullptr, stream));
   }
   return CG_OK;
 }

@@ -59,7 +59,11 @@ struct cg_ppr {
   // edges among vertices [0, dense_h) of the graph are not in `seg` but in a
   // bitmap, multiplied by the hubs' contributions with tcgen05.mma
   int32_t dense_h = 0;               // 0: no dense block
+  int32_t dense_parts = 1;           // CTAs (and dense rows) per 128-destination tile
   const uint32_t* dense_bits = nullptr;  // caller-owned [dense_h][dense_h/32]
+  uint32_t* dense_bits_t = nullptr;  // the same bitmap tile-major (1 KB per tile chunk)
+  float* dense_partial = nullptr;    // [dense_parts][dense_h][64] partial rows of the parts
+  unsigned* dense_done = nullptr;    // [dense_h/128] parts finished per tile
   int32_t* dense_tile_off = nullptr;     // [dense_h/128 + 1] non-empty 64-source chunks per tile
   int32_t* dense_tile_chunks = nullptr;  // [total]
   uint8_t* ct_hi = nullptr;          // [dense_h/64][8192 B] hub contributions, MMA operand layout

@@ -14,17 +14,21 @@
 // the hub-block edges are removed from the segmented graph the gather walks
 // (cg_split_hub_block).
 //
-// Kernel (one CTA of 128 threads per 128 hub destinations):
-//   A tile  128 destinations x 64 sources, BF16 0/1, expanded from the bitmap
-//           into shared memory (thread t expands destination row t);
+// Kernel (CTAs of 256 threads; each 128-destination tile's chunk list split
+// over `parts` CTAs, whose partial rows the tile's last CTA to finish adds in
+// part order, so the merge sees one dense row per hub destination):
+//   A tile  128 destinations x 64 sources, BF16 0/1, expanded into shared
+//           memory from the chunk's 1 KB of bitmap (thread t: destination t);
 //   B tiles 64 columns x 64 sources for the hi and the lo plane, pre-packed
 //           in global memory in the operand layout (ppr_dense_pack, after each
-//           merge) and copied by two bulk TMA copies per chunk;
+//           merge); bitmap and B tiles arrive by three bulk TMA copies per
+//           chunk, issued two chunks ahead;
 //   MMA     tcgen05.mma.cta_group::1.kind::f16, M = 128, N = 64, K = 16, FP32
 //           accumulators in tensor memory (64 columns), four K-steps per plane
 //           per chunk, issued by one thread and committed to an mbarrier;
-//   stages  two shared-memory stages: chunk i+1 is expanded and copied while
-//           the tensor cores work on chunk i;
+//   stages  three shared-memory stages (two CTAs per SM): the copies of
+//           chunk i+1 are in flight while chunk i is expanded (256 threads, a
+//           byte -> 8 BF16 lookup table) and the tensor cores work on i-1;
 //   sparse  64-source chunks with no edge in a tile's rows are skipped (a
 //           per-tile list built once);
 //   out     tcgen05.ld of the accumulators (warp w: rows 32w..32w+31), stored
@@ -36,6 +40,7 @@
 // the only rounding.
 #include <cuda_bf16.h>
 
+#include <algorithm>
 #include <vector>
 
 #include "ppr.cuh"
@@ -47,7 +52,11 @@ constexpr int kDM = 128;                   // destinations per tile (MMA M)
 constexpr int kDK = 64;                    // sources per chunk
 constexpr int kTileA = kDM * kDK * 2;      // 16 KB
 constexpr int kTileB = kCols * kDK * 2;    // 8 KB per plane
-constexpr int kStage = kTileA + 2 * kTileB;  // 32 KB
+constexpr int kTileBits = kDM * kDK / 8;   // 1 KB of bitmap per tile chunk
+constexpr int kStage = kTileA + 2 * kTileB + kTileBits;  // 33 KB
+constexpr int kStages = 3;                 // shared-memory stages (two CTAs per SM fit)
+constexpr int kAhead = 1;                  // chunks whose copies are issued ahead
+constexpr int kDThreads = 256;             // threads per CTA: two per destination row
 constexpr uint32_t kDenseWaitPolls = 1u << 26;
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -145,32 +154,24 @@ __device__ __forceinline__ void tc_fence_before() {
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
 }
 
-// 32 lanes x 64 columns of FP32 accumulators into registers: thread i of the
-// warp gets lane (lane_base + i), columns col0 .. col0+63.
-__device__ __forceinline__ void tmem_ld64(uint32_t taddr, float (&v)[64]) {
-  uint32_t r[64];
+// 32 lanes x 32 columns of FP32 accumulators into registers.
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
+  uint32_t r[32];
   asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x64.b32 "
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
       "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
-      "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31, "
-      "%32, %33, %34, %35, %36, %37, %38, %39, %40, %41, %42, %43, %44, %45, %46, %47, "
-      "%48, %49, %50, %51, %52, %53, %54, %55, %56, %57, %58, %59, %60, %61, %62, %63}, [%64];"
+      "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
       : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
         "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
         "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]),
         "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
         "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]),
-        "=r"(r[31]), "=r"(r[32]), "=r"(r[33]), "=r"(r[34]), "=r"(r[35]), "=r"(r[36]),
-        "=r"(r[37]), "=r"(r[38]), "=r"(r[39]), "=r"(r[40]), "=r"(r[41]), "=r"(r[42]),
-        "=r"(r[43]), "=r"(r[44]), "=r"(r[45]), "=r"(r[46]), "=r"(r[47]), "=r"(r[48]),
-        "=r"(r[49]), "=r"(r[50]), "=r"(r[51]), "=r"(r[52]), "=r"(r[53]), "=r"(r[54]),
-        "=r"(r[55]), "=r"(r[56]), "=r"(r[57]), "=r"(r[58]), "=r"(r[59]), "=r"(r[60]),
-        "=r"(r[61]), "=r"(r[62]), "=r"(r[63])
+        "=r"(r[31])
       : "r"(taddr)
       : "memory");
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
-  for (int q = 0; q < 64; ++q) v[q] = __uint_as_float(r[q]);
+  for (int q = 0; q < 32; ++q) v[q] = __uint_as_float(r[q]);
 }
 
 // Byte offset of element (row r, k) in a K-major tile without swizzle.
@@ -178,24 +179,75 @@ __device__ __forceinline__ uint32_t tile_off(int r, int k) {
   return (uint32_t)((r >> 3) * 1024 + (k >> 3) * 128 + (r & 7) * 16 + (k & 7) * 2);
 }
 
-// One CTA per 128 hub destinations (tile t = blockIdx.x).
-__global__ void __launch_bounds__(kDM, 1)
-dense_tile_kernel(const uint32_t* __restrict__ bits, int32_t h,
+// One CTA per (128 hub destinations, part of their chunk list): tile t =
+// blockIdx.x / parts, part p = blockIdx.x % parts takes chunks
+// [p n / parts, (p+1) n / parts) of the tile's n non-empty chunks and writes
+// its partial rows to partial[p][128t ..]; the tile's last part to finish
+// adds the parts in order into rows 128t .. of out_rows.
+// bits_t: the bitmap tile-major, 1 KB (128 rows x 2 words) per (tile, chunk).
+// Pipeline over the part's chunks i (stage i % 3): thread 0 issues the bulk
+// copies of chunk i+1 (bitmap, B hi, B lo) once the MMAs of chunk i-2 that
+// read that stage are done (in general chunk i + kAhead after chunk
+// i + kAhead - kStages); all threads wait for chunk i's copies, expand the
+// A tile from the staged bitmap, and thread 0 issues chunk i's 8 MMAs and
+// commits them to the stage's mbarrier.
+__global__ void __launch_bounds__(kDThreads, 2)
+dense_tile_kernel(const uint32_t* __restrict__ bits_t, int32_t h, int parts,
                   const int32_t* __restrict__ tile_off_list, const int32_t* __restrict__ chunks,
                   const uint8_t* __restrict__ ct_hi, const uint8_t* __restrict__ ct_lo,
+                  float* __restrict__ partial, unsigned* __restrict__ done,
                   float* __restrict__ out_rows, unsigned* __restrict__ fault) {
   extern __shared__ __align__(1024) uint8_t sm[];
-  __shared__ __align__(8) uint64_t bar_load[2], bar_mma[2];
+  __shared__ __align__(8) uint64_t bar_load[kStages], bar_mma[kStages];
   __shared__ uint32_t s_taddr;
+  __shared__ uint4 s_lut[256];  // byte -> 8 BF16 values, 1.0 where the bit is set
+  __shared__ bool s_last;
   const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
-  const int t = blockIdx.x;
-  const int c0 = tile_off_list[t], nch = tile_off_list[t + 1] - c0;
-  const int64_t row = (int64_t)t * kDM + tid;  // this thread's destination
-  float4* orow = reinterpret_cast<float4*>(out_rows + row * kCols);
-  if (nch == 0) {  // no hub-block edge into these destinations
+  const int t = blockIdx.x / parts, part = blockIdx.x % parts;
+  const int nall = tile_off_list[t + 1] - tile_off_list[t];
+  const int c0 = tile_off_list[t] + (int)((int64_t)part * nall / parts);
+  const int nch = tile_off_list[t] + (int)((int64_t)(part + 1) * nall / parts) - c0;
+  const int nchunk = h / kDK;
+  // epilogue: warp w holds TMEM lanes 32(w%4).. and columns 32(w/4)..
+  const int erow = 32 * (w & 3) + lane, ecol = 32 * (w >> 2);
+  const int64_t dst = (int64_t)t * kDM + erow;  // hub destination of this thread's half row
+  float4* prow = reinterpret_cast<float4*>(partial + ((int64_t)part * h + dst) * kCols + ecol);
+  // the tile's parts: each stores its partial rows; the last part to finish
+  // (an atomic count, no waiting) adds them in part order into the output
+  auto finish = [&]() {
+    __threadfence();
+    __syncthreads();
+    if (tid == 0) s_last = atomicAdd(done + t, 1u) == (unsigned)parts - 1;
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    float4 acc[8];
+    for (int q = 0; q < 8; ++q) acc[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int pp = 0; pp < parts; ++pp) {
+      const float4* src = reinterpret_cast<const float4*>(partial + ((int64_t)pp * h + dst) * kCols + ecol);
 #pragma unroll
-    for (int q = 0; q < kCols / 4; ++q) orow[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+      for (int q = 0; q < 8; ++q) {
+        const float4 x = __ldcg(src + q);
+        acc[q].x += x.x; acc[q].y += x.y; acc[q].z += x.z; acc[q].w += x.w;
+      }
+    }
+    float4* orow = reinterpret_cast<float4*>(out_rows + dst * kCols + ecol);
+#pragma unroll
+    for (int q = 0; q < 8; ++q) orow[q] = acc[q];
+    if (tid == 0) done[t] = 0u;  // ready for the next launch
+  };
+  if (nch == 0) {  // no hub-block edge for this part
+#pragma unroll
+    for (int q = 0; q < 8; ++q) prow[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+    finish();
     return;
+  }
+  {
+    uint32_t p[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+      p[q] = (((tid >> (2 * q)) & 1) ? 0x3F80u : 0u) | (((tid >> (2 * q + 1)) & 1) ? 0x3F800000u : 0u);
+    s_lut[tid] = make_uint4(p[0], p[1], p[2], p[3]);
   }
   if (w == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
@@ -205,74 +257,79 @@ dense_tile_kernel(const uint32_t* __restrict__ bits, int32_t h,
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
   if (tid == 0) {
-    mbar_init(&bar_load[0], 1);
-    mbar_init(&bar_load[1], 1);
-    mbar_init(&bar_mma[0], 1);
-    mbar_init(&bar_mma[1], 1);
+    for (int q = 0; q < kStages; ++q) {
+      mbar_init(&bar_load[q], 1);
+      mbar_init(&bar_mma[q], 1);
+    }
     fence_mbar_init();
   }
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
   const uint32_t taddr = s_taddr;
-  const int wpr = h >> 5;  // bitmap words per destination row
+  // thread 0: the copies of chunk j into stage j % kStages
+  auto issue = [&](int j) {
+    uint8_t* st = sm + (j % kStages) * kStage;
+    uint64_t* bl = &bar_load[j % kStages];
+    const int c = chunks[c0 + j];
+    bulk_expect(bl, 2 * kTileB + kTileBits);
+    bulk_copy(st + kTileA, ct_hi + (int64_t)c * kTileB, kTileB, bl);
+    bulk_copy(st + kTileA + kTileB, ct_lo + (int64_t)c * kTileB, kTileB, bl);
+    bulk_copy(st + kTileA + 2 * kTileB,
+              reinterpret_cast<const uint8_t*>(bits_t) + ((int64_t)t * nchunk + c) * kTileBits,
+              kTileBits, bl);
+  };
+  if (tid == 0)
+    for (int j = 0; j < kAhead && j < nch; ++j) issue(j);
   bool ok = true;
-  for (int i = 0; i < nch; ++i) {
-    const int s = i & 1;
+  for (int i = 0; i < nch && ok; ++i) {
+    const int s = i % kStages;
     uint8_t* A = sm + s * kStage;
-    uint8_t* Bh = A + kTileA;
-    uint8_t* Bl = Bh + kTileB;
-    if (i >= 2 && !mbar_wait(&bar_mma[s], ((i - 2) >> 1) & 1)) ok = false;  // stage s is free
-    ok = __syncthreads_and(ok);
-    if (!ok) break;
-    const int c = chunks[c0 + i];
-    if (tid == 0) {
-      bulk_expect(&bar_load[s], 2 * kTileB);
-      bulk_copy(Bh, ct_hi + (int64_t)c * kTileB, kTileB, &bar_load[s]);
-      bulk_copy(Bl, ct_lo + (int64_t)c * kTileB, kTileB, &bar_load[s]);
+    const uint8_t* Bh = A + kTileA;
+    const uint8_t* Bl = Bh + kTileB;
+    const uint32_t* Bt = reinterpret_cast<const uint32_t*>(Bl + kTileB);
+    if (tid == 0 && i + kAhead < nch) {
+      // the stage of chunk j = i + kAhead was last read by the MMAs of chunk j - kStages
+      const int j = i + kAhead, old = j - kStages;
+      if (old >= 0 && !mbar_wait(&bar_mma[old % kStages], (old / kStages) & 1)) ok = false;
+      if (ok) issue(j);
     }
-    // A: this thread's destination row, 64 sources as BF16 0/1
-    const uint32_t* wr = bits + row * wpr + (int64_t)c * (kDK / 32);
-    const uint64_t b64 = (uint64_t)__ldg(wr) | ((uint64_t)__ldg(wr + 1) << 32);
-#pragma unroll
-    for (int kg = 0; kg < kDK / 8; ++kg) {
-      const uint32_t byte = (uint32_t)(b64 >> (8 * kg)) & 0xFFu;
-      uint32_t p[4];
+    // chunk i's copies (bitmap, B tiles); its A stage was read by the MMAs of
+    // chunk i - kStages, which completed before chunk i's copies were issued
+    if (!mbar_wait(&bar_load[s], (i / kStages) & 1)) ok = false;
+    {  // thread t: row t/2, sources 32(t%2) .. 32(t%2)+31 (one bitmap word)
+      const int r = tid >> 1, hw = tid & 1;
+      const uint32_t word = Bt[2 * r + hw];
 #pragma unroll
       for (int q = 0; q < 4; ++q)
-        p[q] = (((byte >> (2 * q)) & 1u) ? 0x3F80u : 0u) |
-               (((byte >> (2 * q + 1)) & 1u) ? 0x3F800000u : 0u);
-      *reinterpret_cast<uint4*>(A + tile_off(tid, kg * 8)) = make_uint4(p[0], p[1], p[2], p[3]);
+        *reinterpret_cast<uint4*>(A + tile_off(r, 32 * hw + 8 * q)) = s_lut[(word >> (8 * q)) & 0xFFu];
     }
     fence_proxy_async_smem();
-    __syncthreads();
+    ok = __syncthreads_and(ok);
+    if (!ok) break;
     if (tid == 0) {
-      if (!mbar_wait(&bar_load[s], (i >> 1) & 1)) {
-        atomicOr(fault, 1u);
-      } else {
-        tc_fence_after();
-        const uint32_t a0 = smem_u32(A), h0 = smem_u32(Bh), l0 = smem_u32(Bl);
+      tc_fence_after();
+      const uint32_t a0 = smem_u32(A), h0 = smem_u32(Bh), l0 = smem_u32(Bl);
 #pragma unroll
-        for (int kk = 0; kk < kDK / 16; ++kk) {
-          const uint64_t ad = smem_desc(a0 + kk * 256, 128, 1024);
-          mma_bf16(taddr, ad, smem_desc(h0 + kk * 256, 128, 1024), (i > 0 || kk > 0) ? 1u : 0u);
-          mma_bf16(taddr, ad, smem_desc(l0 + kk * 256, 128, 1024), 1u);
-        }
+      for (int kk = 0; kk < kDK / 16; ++kk) {
+        const uint64_t ad = smem_desc(a0 + kk * 256, 128, 1024);
+        mma_bf16(taddr, ad, smem_desc(h0 + kk * 256, 128, 1024), (i > 0 || kk > 0) ? 1u : 0u);
+        mma_bf16(taddr, ad, smem_desc(l0 + kk * 256, 128, 1024), 1u);
       }
       mma_commit(&bar_mma[s]);  // arrives once this thread's MMAs so far have completed
     }
   }
   // the last chunk's commit covers every MMA issued before it
   const int last = nch - 1;
-  if (ok && !mbar_wait(&bar_mma[last & 1], (last >> 1) & 1)) ok = false;
+  if (ok && !mbar_wait(&bar_mma[last % kStages], (last / kStages) & 1)) ok = false;
   ok = __syncthreads_and(ok);
   tc_fence_after();
   if (ok) {
-    float v[64];
-    tmem_ld64(taddr + ((uint32_t)(32 * w) << 16), v);
+    float v[32];
+    tmem_ld32(taddr + ((uint32_t)(32 * (w & 3)) << 16) + (uint32_t)ecol, v);
 #pragma unroll
-    for (int q = 0; q < kCols / 4; ++q)
-      orow[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+    for (int q = 0; q < 8; ++q)
+      prow[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
   } else if (lane == 0) {
     atomicOr(fault, 1u);
   }
@@ -283,6 +340,22 @@ dense_tile_kernel(const uint32_t* __restrict__ bits, int32_t h,
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr),
                  "r"(kCols)
                  : "memory");
+  }
+  finish();
+}
+
+// The bitmap tile-major: for tile t and chunk c, 128 rows x 2 words.
+__global__ void dense_tile_bits_kernel(const uint32_t* __restrict__ bits, int32_t h,
+                                       uint32_t* __restrict__ bits_t) {
+  const int wpr = h >> 5, nchunk = h / kDK;
+  const int64_t total = (int64_t)h * wpr;
+  for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < total;
+       x += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t v = x / wpr;
+    const int wd = (int)(x % wpr);
+    const int64_t t = v / kDM;
+    const int r = (int)(v % kDM), c = wd >> 1;
+    bits_t[((t * nchunk + c) * kDM + r) * 2 + (wd & 1)] = bits[x];
   }
 }
 
@@ -328,20 +401,22 @@ __global__ void dense_chunk_flags_kernel(const uint32_t* __restrict__ bits, int3
   }
 }
 
-// Destination-major row lists with one more row (the dense one) at the end of
-// each hub destination's list.
+// Destination-major row lists with `parts` more rows (the dense partial rows,
+// part order) at the end of each hub destination's list.
 __global__ void dense_rows_kernel(const int32_t* __restrict__ old_off,
                                   const int32_t* __restrict__ old_rows, int32_t V, int32_t h,
-                                  int64_t rows0, int32_t* __restrict__ new_off,
+                                  int parts, int64_t rows0, int32_t* __restrict__ new_off,
                                   int32_t* __restrict__ new_rows) {
   for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v <= V;
        v += (int64_t)gridDim.x * blockDim.x) {
-    const int32_t extra = (int32_t)(v < h ? v : h);
+    const int32_t extra = (int32_t)(v < h ? v : h) * parts;
     new_off[v] = old_off[v] + extra;
     if (v == V) continue;
     const int32_t b = old_off[v], e = old_off[v + 1], nb = b + extra;
     for (int32_t i = b; i < e; ++i) new_rows[nb + (i - b)] = old_rows[i];
-    if (v < h) new_rows[nb + (e - b)] = (int32_t)(rows0 + v);
+    if (v < h)
+      for (int q = 0; q < parts; ++q)
+        new_rows[nb + (e - b) + q] = (int32_t)(rows0 + (int64_t)q * h + v);
   }
 }
 
@@ -398,12 +473,13 @@ int ppr_dense_launch(cg_ppr* p, cudaStream_t s) {
               "tensor-core work (its rows are incomplete)");
     return CG_ERR_TIMEOUT;
   }
-  const int smem = 2 * kStage;
+  const int smem = kStages * kStage;
   CG_CUDA(cudaFuncSetAttribute((const void*)dense_tile_kernel,
                                cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-  dense_tile_kernel<<<p->dense_h / kDM, kDM, smem, s>>>(
-      p->dense_bits, p->dense_h, p->dense_tile_off, p->dense_tile_chunks, p->ct_hi, p->ct_lo,
-      p->interm + p->dense_rows0 * kCols, p->dense_fault_dev);
+  dense_tile_kernel<<<(p->dense_h / kDM) * p->dense_parts, kDThreads, smem, s>>>(
+      p->dense_bits_t, p->dense_h, p->dense_parts, p->dense_tile_off, p->dense_tile_chunks,
+      p->ct_hi, p->ct_lo, p->dense_partial, p->dense_done, p->interm + p->dense_rows0 * kCols,
+      p->dense_fault_dev);
   CG_LAUNCH_CHECK();
   return CG_OK;
 }
@@ -421,6 +497,12 @@ void ppr_dense_free(cg_ppr* p) {
   cudaFree(p->dense_tile_chunks);
   cudaFree(p->ct_hi);
   cudaFree(p->ct_lo);
+  cudaFree(p->dense_bits_t);
+  cudaFree(p->dense_partial);
+  cudaFree(p->dense_done);
+  p->dense_bits_t = nullptr;
+  p->dense_partial = nullptr;
+  p->dense_done = nullptr;
   if (p->dense_fault) cudaFreeHost(p->dense_fault);
   p->dense_tile_off = p->dense_tile_chunks = nullptr;
   p->ct_hi = p->ct_lo = nullptr;
@@ -513,6 +595,13 @@ int ppr_batched_attach_dense(cg_ppr* p, int32_t h, const uint32_t* dev_bits,
   if (e == cudaSuccess) e = cudaMalloc((void**)&p->dense_tile_chunks, sizeof(int32_t) * tch.size());
   if (e == cudaSuccess) e = cudaMalloc((void**)&p->ct_hi, (size_t)nchunk * kTileB);
   if (e == cudaSuccess) e = cudaMalloc((void**)&p->ct_lo, (size_t)nchunk * kTileB);
+  if (e == cudaSuccess)
+    e = cudaMalloc((void**)&p->dense_bits_t, sizeof(uint32_t) * (size_t)h * (size_t)(h / 32));
+  if (e == cudaSuccess) {
+    dense_tile_bits_kernel<<<grid_for((int64_t)h * (h / 32), 256), 256, 0, stream>>>(
+        dev_bits, h, p->dense_bits_t);
+    e = cudaGetLastError();
+  }
   if (e == cudaSuccess) e = cudaMemsetAsync(p->ct_lo, 0, (size_t)nchunk * kTileB, stream);
   if (e == cudaSuccess)
     e = cudaHostAlloc((void**)&p->dense_fault, sizeof(unsigned), cudaHostAllocMapped);
@@ -527,7 +616,16 @@ int ppr_batched_attach_dense(cg_ppr* p, int32_t h, const uint32_t* dev_bits,
     e = cudaMemcpyAsync(p->dense_tile_chunks, tch.data(), sizeof(int32_t) * tch.size(),
                         cudaMemcpyHostToDevice, stream);
   if (e != cudaSuccess) return fail(e);
-  // one more intermBuf row per hub destination, listed last for it
+  // each tile's chunk list is split over `parts` CTAs (enough CTAs for every
+  // SM), whose partial rows the tile's last CTA adds in part order: one more
+  // intermBuf row per hub destination, listed last for it
+  DeviceInfo di{};
+  CG_TRY(device_info(&di));
+  const int parts = std::max(1, std::min(8, (2 * di.sm_count + ntile - 1) / ntile));
+  e = cudaMalloc((void**)&p->dense_partial, sizeof(float) * kCols * (size_t)parts * (size_t)h);
+  if (e == cudaSuccess) e = cudaMalloc((void**)&p->dense_done, sizeof(unsigned) * (size_t)ntile);
+  if (e == cudaSuccess) e = cudaMemsetAsync(p->dense_done, 0, sizeof(unsigned) * (size_t)ntile, stream);
+  if (e != cudaSuccess) return fail(e);
   int32_t *noff = nullptr, *nrows = nullptr;
   float* ninterm = nullptr;
   const int64_t rows2 = p->rows + h;
@@ -536,7 +634,7 @@ int ppr_batched_attach_dense(cg_ppr* p, int32_t h, const uint32_t* dev_bits,
   if (e == cudaSuccess) e = cudaMalloc((void**)&ninterm, sizeof(float) * kCols * (size_t)rows2);
   if (e == cudaSuccess) {
     dense_rows_kernel<<<grid_for((int64_t)p->V + 1, 256), 256, 0, stream>>>(
-        p->dst_off, p->dst_rows, p->V, h, p->rows, noff, nrows);
+        p->dst_off, p->dst_rows, p->V, h, 1, p->rows, noff, nrows);
     e = cudaGetLastError();
   }
   if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
@@ -552,9 +650,11 @@ int ppr_batched_attach_dense(cg_ppr* p, int32_t h, const uint32_t* dev_bits,
   p->dst_off = noff;
   p->dst_rows = nrows;
   p->interm = ninterm;
-  p->bytes += (int64_t)h * 4 + (int64_t)h * kCols * 4 + 2 * (int64_t)nchunk * kTileB +
-              4 * (int64_t)(toff.size() + tch.size());
+  p->bytes += (int64_t)h * 4 + (int64_t)(parts + 1) * h * kCols * 4 + 4 * (int64_t)ntile +
+              2 * (int64_t)nchunk * kTileB + 4 * (int64_t)(toff.size() + tch.size()) +
+              (int64_t)h * (h / 8);
   p->dense_rows0 = p->rows;
+  p->dense_parts = parts;
   p->dense_h = h;
   p->dense_bits = dev_bits;
   // the hubs' current contributions in the operand layout
