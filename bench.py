@@ -1309,6 +1309,9 @@ def main():
     ap.add_argument("--overlap", type=int, default=0,
                     help="warps per block serving the L1/L2 segments inside the staged launch "
                          "(with --plan; the autotuner tries its own)")
+    ap.add_argument("--affine", type=int, default=0,  # 1: head threshold = --plan
+                    help="with --plan: the nested plan (cold range in table-sized segments "
+                         "staged one block per segment)")
     ap.add_argument("--sweep", action="store_true", help="k = 1..64 sweep table")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true",
@@ -1372,7 +1375,8 @@ def main():
 
     if args.plan:
         best = {"kind": "plan", "threads": args.threads, "ctas": args.ctas,
-                "min_avg_degree": args.plan, "table": args.table or -1, "overlap": args.overlap}
+                "min_avg_degree": args.plan, "table": args.table or -1, "overlap": args.overlap,
+                "affine": args.affine}
         table = []
     elif args.k:
         best = {"kind": "uniform", "k": args.k, "threads": args.threads, "ctas": args.ctas,

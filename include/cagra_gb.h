@@ -142,6 +142,9 @@ typedef struct {
   int64_t staged_edges;  /* edges of those segments */
   int32_t gather_overlap; /* warps per block serving the L1/L2 segments inside the
                              staged launch (0: a launch of their own) */
+  int32_t affine_segments; /* segments after the staged head served from shared memory
+                              one block per segment (pr_set_gather_affine) */
+  int64_t affine_edges;  /* edges of those segments */
 } cg_segmented_info;
 
 /*
@@ -216,6 +219,24 @@ int pr_set_gather_config(cg_segmented *seg, int32_t threads, int32_t ctas_per_sm
  * pr_set_gather_config keeps the setting.  Synchronizes the stream.
  */
 int pr_set_gather_overlap(cg_segmented *seg, int32_t cached_warps, cudaStream_t stream);
+
+/*
+ * Segment-affine staging of the cold segments (the nested form of two-level
+ * segmenting, Section III-B's "smaller segments" in parallel).  With
+ * head_min_avg_degree > 0, the leading segments that fit the shared table and
+ * carry at least max(4, head_min_avg_degree) edges per source keep the staged
+ * schedule (every block sweeps them); the table-fitting segments after them
+ * (e.g. the cold source range cut into table-sized segments by pr_plan_bounds
+ * with max_global_vertices = the table capacity) are also served from shared
+ * memory, but each by ONE block, which takes whole segments from a counter,
+ * stages the segment's table once and streams all its edges.  Sources of the
+ * cold range are read once per iteration into shared memory instead of once
+ * per edge from L2, at the price of more subgraph rows (q) for the merge.
+ * 0 turns it off.  Needs the 1024-thread, 1-block-per-SM shape and no overlap
+ * (CG_ERR_INVALID_ARG otherwise; the previous configuration stays).
+ * Synchronizes.
+ */
+int pr_set_gather_affine(cg_segmented *seg, double head_min_avg_degree, cudaStream_t stream);
 
 /* Shared-table capacity (entries) of the gather at ctas_per_sm blocks/SM. */
 int pr_gather_table_capacity(int32_t ctas_per_sm);

@@ -39,7 +39,7 @@ EXPORTS = [
     "cf_transpose", "cf_create", "cf_destroy", "cf_set_factors", "cf_get_factors", "cf_sweep",
     "cf_sweep_phase", "cf_info", "cg_measure_row_gather", "cg_measure_smem_lookups",
     "cg_permute8", "cg_transpose_csr", "bc_create", "bc_destroy", "bc_set_direction", "bc_run",
-    "bc_source_state", "cg_split_hub_block", "ppr_batched_attach_dense",
+    "bc_source_state", "cg_split_hub_block", "ppr_batched_attach_dense", "pr_set_gather_affine",
 ]
 
 
@@ -54,7 +54,8 @@ class SegInfo(ctypes.Structure):
                 ("device_bytes", ctypes.c_int64), ("gather_tiles", ctypes.c_int64),
                 ("table_vertices", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32),
                 ("gather_threads", ctypes.c_int32), ("staged_segments", ctypes.c_int32),
-                ("staged_edges", ctypes.c_int64), ("gather_overlap", ctypes.c_int32)]
+                ("staged_edges", ctypes.c_int64), ("gather_overlap", ctypes.c_int32),
+                ("affine_segments", ctypes.c_int32), ("affine_edges", ctypes.c_int64)]
 
 
 def load(path: str | None = None):
@@ -87,6 +88,7 @@ def load(path: str | None = None):
             "pr_set_gather_config": (ctypes.c_int, [vp, i32, i32, i32, vp]),
             "pr_gather_table_capacity": (ctypes.c_int, [i32]),
             "pr_set_gather_overlap": (ctypes.c_int, [vp, i32, vp]),
+            "pr_set_gather_affine": (ctypes.c_int, [vp, dbl, vp]),
             "cg_segmented_export": (ctypes.c_int, [vp, vp, vp, vp, vp, vp, vp, vp, vp]),
             "cg_segmented_destroy": (ctypes.c_int, [vp]),
             "cg_seg_gather": (ctypes.c_int, [vp, i32, vp, vp, vp]),
@@ -291,6 +293,12 @@ def pr_set_gather_config(seg: Segmented, threads: int = 1024, ctas_per_sm: int =
 def pr_set_gather_overlap(seg: Segmented, cached_warps: int, stream=None):
     _check(load().pr_set_gather_overlap(seg.handle, cached_warps, _stream(stream)),
            "pr_set_gather_overlap")
+
+
+def pr_set_gather_affine(seg: Segmented, head_min_avg_degree: float, stream=None):
+    """> 0: the segment-affine plan with that head threshold; 0: off."""
+    _check(load().pr_set_gather_affine(seg.handle, float(head_min_avg_degree), _stream(stream)),
+           "pr_set_gather_affine")
 
 
 def pr_gather_table_capacity(ctas_per_sm: int = 1) -> int:

@@ -8,10 +8,10 @@
 // The segmented graph of Algorithm 2, flattened: all subgraphs concatenated
 // in segment order.  Subgraph row i (global row index over all segments)
 // holds edges [row_ptr[i], row_ptr[i+1]) (stored flagged and padded in
-// plan.colf) and its destination is idx_map[i].  blk[s*(nb+1) + b] is the
-// first (global) row of segment s whose destination is >= b*B; rows of
-// segment s inside merge block b are
-// [blk[s*(nb+1)+b], blk[s*(nb+1)+b+1]).
+// plan.colf) and its destination is idx_map[i].  blk[b*k + s] is the first
+// (global) row of segment s whose destination is >= b*B (block-major: a
+// merge block's starts of all segments are contiguous); rows of segment s
+// inside merge block b are [blk[b*k + s], blk[(b+1)*k + s]).
 struct cg_segmented {
   int device = 0;
   int32_t V = 0;
@@ -23,7 +23,7 @@ struct cg_segmented {
   std::vector<int64_t> bounds, row_base, edge_base;  // host copies, k+1 each
   int32_t* row_ptr = nullptr;  // [rows+1] (export only; the gather reads flagged edges)
   int32_t* idx_map = nullptr;  // [rows]
-  int32_t* blk = nullptr;      // [k*(nb+1)]
+  int32_t* blk = nullptr;      // [(nb+1)*k] block-major
   cg::SegPlan plan;            // flagged padded edges + chunk index + launch shape
   void* interm = nullptr;        // [rows] 4-byte values (intermBuf)
   double* partials = nullptr;    // [2*nb] per-block FP64 partial sums

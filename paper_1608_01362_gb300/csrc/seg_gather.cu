@@ -540,6 +540,52 @@ staged_gather_kernel(const uint8_t* __restrict__ cs, const typename Op::T* __res
                     &s_size);
 }
 
+// The segment-affine staged launch (the nested form of two-level segmenting:
+// the cold part of the source range, which an L2-sized segment would serve
+// with random L2 reads, cut into shared-memory-sized segments).  Each block
+// takes whole segments of [m, m2) from a counter, in order (heaviest first
+// after clustering), stages the segment's table once and streams all its
+// chunks with every warp; low-degree segments thus pay one table copy each
+// instead of one per block.
+template <class Op>
+__global__ void __launch_bounds__(1024, 1)
+affine_gather_kernel(const uint8_t* __restrict__ cs, const typename Op::T* __restrict__ x,
+                     const int32_t* __restrict__ seg_E, const int64_t* __restrict__ seg_chunk,
+                     const int32_t* __restrict__ seg_lo, const int32_t* __restrict__ seg_tab,
+                     int m, int m2, unsigned* __restrict__ next_seg,
+                     typename Op::T* __restrict__ out, typename Op::T* __restrict__ carry) {
+  using T = typename Op::T;
+  constexpr int CHUNK = kStagedChunk;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* tab = reinterpret_cast<T*>(smem_raw);
+  __shared__ int32_t s_seg;
+  const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
+  for (;;) {
+    __syncthreads();  // every warp is done with the previous table and s_seg
+    if (tid == 0) s_seg = m + (int32_t)atomicAdd(next_seg, 1u);
+    __syncthreads();
+    const int s = s_seg;
+    if (s >= m2) break;
+    const int32_t Es = seg_E[s], cbase = (int32_t)seg_chunk[s], tn = seg_tab[s];
+    const int32_t nch = (Es + CHUNK - 1) / CHUNK;
+    if (nch == 0) continue;
+    stage_table<T>(x + seg_lo[s], tn, tab, tid, 1024);
+    __syncthreads();
+    const uint32_t tmax = tn > 0 ? (uint32_t)(tn - 1) : 0u;
+    for (int32_t j = w; j < nch; j += 32) {
+      const int32_t c = cbase + j;
+      if (lane == 0 && j + 32 < nch)
+        prefetch_l2(cs + (int64_t)(c + 32) * kStagedChunkBytes, kStagedChunkBytes);
+      uint32_t pk[8], fl;
+      int pre;
+      int32_t frow;
+      staged_load(cs, c, pk, fl, pre, frow);
+      staged_chunk<Op>(pk, fl, pre, Es - j * CHUNK < CHUNK ? Es - j * CHUNK : CHUNK, c, frow, tab,
+                       tmax, out, carry);
+    }
+  }
+}
+
 // L1/L2 chunks of segments [m, k) taken from a queue (a global counter of
 // chunks, kCachedGrab at a time): a warp's successive grabs only move forward,
 // so its segment is found by stepping.  The grab's chunks are prefetched into
@@ -708,18 +754,39 @@ int seg_plan_configure(SegPlan* p, int threads, int ctas_per_sm, int tab_vertice
   const int k = p->k;
   // staged prefix: leading segments that fit the table and carry enough
   // edges (>= 4 per source) for staging them in shared memory to pay
+  // (with the segment-affine plan: >= affine_head edges per source, the
+  // rest of the table-sized segments go one block per segment)
+  const double head_deg = p->affine_head > 0.0 ? std::max(4.0, p->affine_head) : 4.0;
   int m = 0;
   int64_t tabmax = 0;
   while (m < k && tab > 0) {
     const int64_t size = p->src_bounds[m + 1] - p->src_bounds[m];
     const int64_t Eq = p->edge_base[m + 1] - p->edge_base[m];
-    if (size > tab || (double)Eq < 4.0 * (double)size) break;
+    if (size > tab || (double)Eq < head_deg * (double)size) break;
     tabmax = std::max(tabmax, size);
     ++m;
   }
+  // segment-affine staged segments [m, m2): the table-sized segments after the
+  // head, when asked for (each one's table is staged once, by one block)
+  int m2 = m;
+  if (p->affine_head > 0.0) {
+    if (threads != 1024 || ctas_per_sm != 1) {
+      set_error("segment-affine staging needs 1024 threads and 1 block per SM (got %d x %d)",
+                threads, ctas_per_sm);
+      return CG_ERR_INVALID_ARG;
+    }
+    if (p->overlap_request > 0) {
+      set_error("segment-affine staging and the overlapped gather exclude each other");
+      return CG_ERR_INVALID_ARG;
+    }
+    while (m2 < k && tab > 0 && p->src_bounds[m2 + 1] - p->src_bounds[m2] <= tab) {
+      tabmax = std::max(tabmax, p->src_bounds[m2 + 1] - p->src_bounds[m2]);
+      ++m2;
+    }
+  }
   // one overlapped launch needs both kinds of segment and the 1024 x 1 shape
   bool cached_edges = false;
-  for (int q = m; q < k; ++q) cached_edges |= p->edge_base[q + 1] > p->edge_base[q];
+  for (int q = m2; q < k; ++q) cached_edges |= p->edge_base[q + 1] > p->edge_base[q];
   if (p->overlap_request > 0 && (threads != 1024 || ctas_per_sm != 1)) {
     set_error("gather overlap needs 1024 threads and 1 block per SM (got %d x %d)", threads,
               ctas_per_sm);
@@ -732,10 +799,12 @@ int seg_plan_configure(SegPlan* p, int threads, int ctas_per_sm, int tab_vertice
   std::vector<int32_t> ctile(k + 1, 0), tn(k > 0 ? k : 1, 0);
   for (int q = 0; q < k; ++q) {
     const int64_t Eq = p->edge_base[q + 1] - p->edge_base[q];
-    const int64_t nch = ceil_div(Eq, q < m ? chunk_a : chunk_b);
+    const int64_t nch = ceil_div(Eq, q < m2 ? chunk_a : chunk_b);
     chunk[q + 1] = chunk[q] + nch;
-    ctile[q + 1] = ctile[q] + (int32_t)ceil_div(nch, q < m ? warps_a : warps_b);
-    tn[q] = q < m ? (int32_t)(p->src_bounds[q + 1] - p->src_bounds[q]) : 0;
+    // block-groups of the sweeping launches (none for the segment-affine segments)
+    ctile[q + 1] = ctile[q] + (q < m ? (int32_t)ceil_div(nch, warps_a)
+                                     : q < m2 ? 0 : (int32_t)ceil_div(nch, warps_b));
+    tn[q] = q < m2 ? (int32_t)(p->src_bounds[q + 1] - p->src_bounds[q]) : 0;
   }
   const int64_t nchunks = chunk[k];
   if (nchunks > p->chunk_cap) {
@@ -749,7 +818,7 @@ int seg_plan_configure(SegPlan* p, int threads, int ctas_per_sm, int tab_vertice
     CG_CUDA(cudaMalloc(&p->carry, sizeof(int32_t) * nc));
     p->chunk_cap = nchunks;
   }
-  const int64_t cs_bytes = chunk[m] * kStagedChunkBytes;
+  const int64_t cs_bytes = chunk[m2] * kStagedChunkBytes;
   if (cs_bytes > p->cs_cap) {
     cudaFree(p->cs);
     p->cs = nullptr;
@@ -766,13 +835,13 @@ int seg_plan_configure(SegPlan* p, int threads, int ctas_per_sm, int tab_vertice
                             s));
   if (nchunks > 0) {
     first_row_kernel<<<grid_for(nchunks, 256), 256, 0, s>>>(
-        p->rp32, p->meta, p->meta + (k + 1), p->seg_chunk, k, m, chunk_a, chunk_b, nchunks,
+        p->rp32, p->meta, p->meta + (k + 1), p->seg_chunk, k, m2, chunk_a, chunk_b, nchunks,
         p->first_row);
     CG_LAUNCH_CHECK();
   }
-  if (chunk[m] > 0) {
-    staged_fill_kernel<<<grid_for(chunk[m] * 32, 256), 256, 0, s>>>(
-        p->colf, p->seg_chunk, p->seg_cstart, p->seg_E, p->first_row, m, chunk[m], p->cs);
+  if (chunk[m2] > 0) {
+    staged_fill_kernel<<<grid_for(chunk[m2] * 32, 256), 256, 0, s>>>(
+        p->colf, p->seg_chunk, p->seg_cstart, p->seg_E, p->first_row, m2, chunk[m2], p->cs);
     CG_LAUNCH_CHECK();
   }
   // static runs of carries, cut into pieces for the parallel completion
@@ -789,7 +858,7 @@ int seg_plan_configure(SegPlan* p, int threads, int ctas_per_sm, int tab_vertice
     int32_t* orow = nullptr;
     CG_CUDA(cudaMallocAsync((void**)&orow, sizeof(int32_t) * (size_t)nchunks, s));
     open_row_kernel<<<grid_for(nchunks, 256), 256, 0, s>>>(
-        p->rp32, p->meta, p->meta + (k + 1), p->seg_chunk, k, m, chunk_a, chunk_b, nchunks, orow);
+        p->rp32, p->meta, p->meta + (k + 1), p->seg_chunk, k, m2, chunk_a, chunk_b, nchunks, orow);
     cudaError_t ce = cudaGetLastError();
     std::vector<int32_t> hc((size_t)nchunks);
     if (ce == cudaSuccess)
@@ -829,6 +898,8 @@ int seg_plan_configure(SegPlan* p, int threads, int ctas_per_sm, int tab_vertice
   p->tab_cap = (int)((tabmax + 3) & ~3LL);
   p->table_request = tab;
   p->m = m;
+  p->m2 = m2;
+  p->grid_affine = di.sm_count;
   p->nchunks = nchunks;
   p->ct_split = ctile[m];
   p->n_ctiles = ctile[k];
@@ -837,7 +908,7 @@ int seg_plan_configure(SegPlan* p, int threads, int ctas_per_sm, int tab_vertice
   if (p->overlap > 0) p->grid = di.sm_count;  // every SM serves the L1/L2 queue too
   // about eight pieces per block: balance without many table reloads
   p->piece = (int32_t)std::max<int64_t>(1, ceil_div(p->ct_split, 8LL * p->grid));
-  if (!p->counter) CG_CUDA(cudaMalloc((void**)&p->counter, 2 * sizeof(unsigned)));
+  if (!p->counter) CG_CUDA(cudaMalloc((void**)&p->counter, 3 * sizeof(unsigned)));
   p->grid_l2 = (int)std::max<int64_t>(
       1, std::min<int64_t>(p->n_ctiles - p->ct_split, (int64_t)di.sm_count * 2));
   return CG_OK;
@@ -929,6 +1000,18 @@ int run_seg_gather(const SegPlan& p, const typename Op::T* x, int32_t nx, typena
       CG_TRY((launch_staged<Op, 1024>(p, x, out, s)));
     else
       CG_TRY((launch_staged<Op, 512>(p, x, out, s)));
+  }
+  // the table-sized cold segments, one block per segment
+  if ((phases & kPhaseCached) && p.m2 > p.m) {
+    const size_t smem = (size_t)p.tab_cap * sizeof(T);
+    auto fn = affine_gather_kernel<Op>;
+    CG_CUDA(cudaMemsetAsync(p.counter + 2, 0, sizeof(unsigned), s));
+    if (smem > 48 * 1024)
+      CG_CUDA(cudaFuncSetAttribute((const void*)fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)smem));
+    fn<<<p.grid_affine, 1024, smem, s>>>(p.cs, x, p.seg_E, p.seg_chunk, p.seg_lo, p.seg_tab, p.m,
+                                         p.m2, p.counter + 2, out, reinterpret_cast<T*>(p.carry));
+    CG_LAUNCH_CHECK();
   }
   // the rest through L1/L2: no shared memory, so the whole on-chip store is L1
   if ((phases & kPhaseCached) && p.n_ctiles > p.ct_split) {

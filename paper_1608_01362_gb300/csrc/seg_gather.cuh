@@ -58,12 +58,17 @@ struct SegPlan {
   int ctas_per_sm = 1;
   int tab_cap = 0;          // table entries of the staged launch (its largest segment)
   int table_request = 0;    // the capacity asked for
-  int m = 0;                // segments [0, m) are staged in shared memory
+  int m = 0;                // segments [0, m) are staged in shared memory (all blocks sweep them)
+  int m2 = 0;               // segments [m, m2): staged too, one block per segment (affine)
+  double affine_head = 0.0;  // > 0: head threshold (edges per source) of the segment-affine
+                            // plan; the table-sized segments after the head go one per block
+  int grid_affine = 0;      // blocks of the segment-affine launch
   int32_t ct_split = 0;     // first block-group of the unstaged segments
   int64_t n_ctiles = 0;
   int grid = 0;             // staged launch blocks
   int32_t piece = 1;        // block-groups per work piece of the staged launch
-  unsigned* counter = nullptr;  // [2] next staged work piece, next L1/L2 chunk (overlap)
+  unsigned* counter = nullptr;  // [3] next staged work piece, next L1/L2 chunk (overlap),
+                                //     next segment-affine segment
   int overlap_request = 0;  // warps per block given to the L1/L2 segments (0: two launches)
   int overlap = 0;          // the same, in effect (0 when one kind of segment is absent)
   int grid_l2 = 0;          // unstaged launch blocks (1024 threads, 2 per SM)
@@ -99,7 +104,8 @@ int64_t seg_plan_bytes(const SegPlan& p);
 int seg_plan_export_col(const SegPlan& p, const int32_t* rp, int32_t* col, cudaStream_t s);
 
 // Launch phases of one pass (all by default): the staged launch, the L1/L2
-// launch and the carry fix-up, in that order.  With the overlap in effect one
+// launch (with the segment-affine staged launch before it, when configured)
+// and the carry fix-up, in that order.  With the overlap in effect one
 // launch serves both kinds of segment: it runs for kPhaseStaged and
 // kPhaseCached launches nothing.
 constexpr int kPhaseStaged = 1, kPhaseCached = 2, kPhaseFixup = 4, kPhaseAll = 7;

@@ -251,12 +251,28 @@ __global__ void to_i64_kernel(const int32_t* __restrict__ in, int64_t n,
     out[i] = in[i];
 }
 
+// Block-major merge index (blk[b*k + s]) -> segment-major local rows
+// (out[s*(nb+1) + b] = blk[b*k + s] - row_base[s]), the oracle's layout.
 __global__ void blk_local_kernel(const int32_t* __restrict__ blk, const int64_t* __restrict__ rb,
                                  int k, int nb, int32_t* __restrict__ out) {
   const int64_t n = (int64_t)k * (nb + 1);
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-       i += (int64_t)gridDim.x * blockDim.x)
-    out[i] = (int32_t)(blk[i] - rb[i / (nb + 1)]);
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t sg = i / (nb + 1), b = i % (nb + 1);
+    out[i] = (int32_t)(blk[b * k + sg] - rb[sg]);
+  }
+}
+
+// Segment-major (blk_sm[s*(nb+1) + b]) -> block-major (blk[b*k + s]): a merge
+// block's first rows of all segments are then one contiguous run.
+__global__ void blk_transpose_kernel(const int32_t* __restrict__ blk_sm, int k, int nb,
+                                     int32_t* __restrict__ blk) {
+  const int64_t n = (int64_t)k * (nb + 1);
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t b = i / k, sg = i % k;
+    blk[i] = blk_sm[sg * (nb + 1) + b];
+  }
 }
 
 struct Scratch {
@@ -372,14 +388,24 @@ int build_impl(const int64_t* offsets, const int32_t* src, int32_t V, int64_t E,
 
   // E
   g->nb = (int32_t)ceil_div(V, B);
-  CG_CUDA(cudaMalloc((void**)&g->blk, sizeof(int32_t) * (size_t)k * (g->nb + 1)));
-  blk_prefill_kernel<<<grid_for((int64_t)k * (g->nb + 1), 256), 256, 0, s>>>(d_rb, k, g->nb,
-                                                                              g->blk);
-  CG_LAUNCH_CHECK();
-  if (npairs > 0) {
-    blk_rows_kernel<<<grid_for(npairs, 256), 256, 0, s>>>(d_rb, k, g->idx_map, npairs, B, g->nb,
-                                                          g->blk);
-    CG_LAUNCH_CHECK();
+  {
+    const size_t nbk = (size_t)k * (g->nb + 1);
+    int32_t* blk_sm = nullptr;  // segment-major while it is built
+    CG_CUDA(cudaMalloc((void**)&g->blk, sizeof(int32_t) * nbk));
+    CG_CUDA(cudaMallocAsync((void**)&blk_sm, sizeof(int32_t) * nbk, s));
+    blk_prefill_kernel<<<grid_for((int64_t)nbk, 256), 256, 0, s>>>(d_rb, k, g->nb, blk_sm);
+    cudaError_t ce = cudaGetLastError();
+    if (ce == cudaSuccess && npairs > 0) {
+      blk_rows_kernel<<<grid_for(npairs, 256), 256, 0, s>>>(d_rb, k, g->idx_map, npairs, B,
+                                                            g->nb, blk_sm);
+      ce = cudaGetLastError();
+    }
+    if (ce == cudaSuccess) {
+      blk_transpose_kernel<<<grid_for((int64_t)nbk, 256), 256, 0, s>>>(blk_sm, k, g->nb, g->blk);
+      ce = cudaGetLastError();
+    }
+    cudaFreeAsync(blk_sm, s);
+    if (ce != cudaSuccess) return cuda_fail(ce, "pr_build_segments", __FILE__, __LINE__);
   }
 
   // F
@@ -502,6 +528,9 @@ int cg_segmented_get_info(const cg_segmented* g, cg_segmented_info* info) {
   info->ctas_per_sm = g->plan.ctas_per_sm;
   info->gather_threads = g->plan.threads;
   info->gather_overlap = g->plan.overlap;
+  info->affine_segments = g->plan.m2 - g->plan.m;
+  info->affine_edges = g->plan.m2 > g->plan.m ? g->edge_base[g->plan.m2] - g->edge_base[g->plan.m]
+                                              : 0;
   return CG_OK;
 }
 
@@ -522,6 +551,21 @@ int pr_set_gather_overlap(cg_segmented* g, int32_t cached_warps, cudaStream_t st
                                     g->plan.table_request, stream);
   if (rc != CG_OK) {  // keep the previous, valid configuration
     g->plan.overlap_request = before;
+    seg_plan_configure(&g->plan, g->plan.threads, g->plan.ctas_per_sm, g->plan.table_request,
+                       stream);
+  }
+  return rc;
+}
+
+int pr_set_gather_affine(cg_segmented* g, double head_min_avg_degree, cudaStream_t stream) {
+  CG_ARG(g != nullptr, "pr_set_gather_affine: null handle");
+  CG_ARG(head_min_avg_degree >= 0.0, "pr_set_gather_affine: head_min_avg_degree must be >= 0");
+  const double before = g->plan.affine_head;
+  g->plan.affine_head = head_min_avg_degree;
+  const int rc = seg_plan_configure(&g->plan, g->plan.threads, g->plan.ctas_per_sm,
+                                    g->plan.table_request, stream);
+  if (rc != CG_OK) {  // keep the previous, valid configuration
+    g->plan.affine_head = before;
     seg_plan_configure(&g->plan, g->plan.threads, g->plan.ctas_per_sm, g->plan.table_request,
                        stream);
   }
@@ -560,14 +604,21 @@ int pr_plan_bounds(const int32_t* dev_outdeg, int32_t V, int32_t smem_vertices,
     }
   }
   if (lo < V) {
-    const int64_t left_k = k_max - ((int64_t)b.size() - 1);
+    // sources without out-edges at the end of the range (all of them, after
+    // clustering) form one segment of their own: it has no edges to cut
+    int64_t end = V;
+    while (end > lo && deg[end - 1] == 0) --end;
+    const int64_t left_k = k_max - ((int64_t)b.size() - 1) - (end < V && end > lo ? 1 : 0);
     if (left_k < 1) {
       b.back() = V;  // no room: the last shared-memory segment absorbs the rest
     } else {
-      int64_t parts = std::max<int64_t>(1, ceil_div(V - lo, max_global_vertices));
-      if (parts > left_k) parts = left_k;
-      const int64_t step = ceil_div(V - lo, parts);
-      for (int64_t q = 1; q <= parts; ++q) b.push_back(std::min<int64_t>(V, lo + q * step));
+      if (end > lo) {
+        int64_t parts = std::max<int64_t>(1, ceil_div(end - lo, max_global_vertices));
+        if (parts > left_k) parts = left_k;
+        const int64_t step = ceil_div(end - lo, parts);
+        for (int64_t q = 1; q <= parts; ++q) b.push_back(std::min<int64_t>(end, lo + q * step));
+      }
+      if (b.back() < V) b.push_back(V);
     }
   }
   *k_out = (int32_t)(b.size() - 1);

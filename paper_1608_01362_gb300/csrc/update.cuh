@@ -13,7 +13,7 @@ constexpr int kMergeWarps = 8;  // warps per merge / update block
 // ---------------------------------------------------------------------------
 // Cache-aware merge (Algorithm 4).  Each warp owns one merge block of B
 // destinations (a shared-memory accumulator of B values) and folds the
-// block's rows [blk[s][b], blk[s][b+1]) of intermBuf into
+// block's rows [blk[b][s], blk[b+1][s]) of intermBuf (blk block-major) into
 // acc[idx_map[i] - b*B], segment after segment in ascending order, so every
 // destination receives its partial sums in segment order (deterministic).
 //
@@ -46,9 +46,9 @@ __device__ __forceinline__ void warp_merge(const int32_t* __restrict__ blk,
   for (int s0 = 0; s0 < k; s0 += 32) {
     const int ls = s0 + lane;
     int32_t lo = 0, hi = 0;
-    if (ls < k) {
-      lo = __ldg(blk + (int64_t)ls * (nb + 1) + mb);
-      hi = __ldg(blk + (int64_t)ls * (nb + 1) + mb + 1);
+    if (ls < k) {  // block-major: the lanes read consecutive words
+      lo = __ldg(blk + mb * k + ls);
+      hi = __ldg(blk + (mb + 1) * k + ls);
     }
     // inclusive prefix of the row counts over the lanes' segments
     int32_t pre = hi - lo;

@@ -114,7 +114,7 @@ class SegmentedPageRank(_PageRankBase):
 
     def __init__(self, graph: Graph, num_segments: int | None = None, merge_block: int = 512,
                  bounds=None, threads: int = 1024, ctas_per_sm: int = 1,
-                 table_vertices: int = -1, overlap: int = 0):
+                 table_vertices: int = -1, overlap: int = 0, affine: float = 0.0):
         super().__init__(graph)
         if bounds is not None:
             bounds = np.asarray(bounds, dtype=np.int64)
@@ -125,6 +125,8 @@ class SegmentedPageRank(_PageRankBase):
             C.pr_set_gather_config(self.seg, threads, ctas_per_sm, table_vertices)
         if overlap:
             C.pr_set_gather_overlap(self.seg, overlap)
+        if affine:
+            C.pr_set_gather_affine(self.seg, affine)
 
     @property
     def info(self):
@@ -221,16 +223,20 @@ def time_iterations(pr, iterations: int = 3, damping: float = 0.85, reps: int = 
 
 
 def default_candidates(uniform_k=(1, 4), shapes=GATHER_SHAPES, min_deg=(4.0, 16.0, 24.0, 32.0, 48.0, 64.0, 256.0),
-                       tables=(-1, 0)):
+                       tables=(-1, 0), affine_deg=(16.0, 24.0, 32.0, 48.0)):
     """Autotuner search space: the paper's uniform split into k segments, and
     the GPU plan (shared-memory segments over the hot head, L2 segments over
     the rest), at several gather launch shapes, shared-table sizes and
-    staging thresholds.  A smaller table leaves more of the SM's on-chip
+    staging thresholds; and the nested plan (the cold rest cut into
+    table-sized segments staged one block per segment) at the head
+    thresholds affine_deg.  A smaller table leaves more of the SM's on-chip
     memory to the L1 cache, which serves the reads the table does not."""
     out = [{"kind": "uniform", "k": k, "threads": 1024, "ctas": 1, "table": tb}
            for k in uniform_k for tb in tables]
     out += [{"kind": "plan", "threads": t, "ctas": c, "min_avg_degree": m, "table": -1}
             for (t, c) in shapes for m in min_deg]
+    out += [{"kind": "plan", "threads": 1024, "ctas": 1, "min_avg_degree": m, "table": -1,
+             "affine": 1} for m in affine_deg]
     return out
 
 
@@ -239,9 +245,13 @@ def _build(graph, cand, merge_block):
     if cand["kind"] == "uniform":
         return SegmentedPageRank(graph, cand["k"], merge_block=merge_block, threads=t,
                                  ctas_per_sm=c, table_vertices=tb)
-    b = plan_bounds(graph, c, cand["min_avg_degree"], table_vertices=tb)
+    # the nested plan cuts the cold range into table-sized segments, staged one
+    # block per segment after the head (head threshold = min_avg_degree)
+    affine = cand["min_avg_degree"] if cand.get("affine", 0) else 0.0
+    mg = C.pr_gather_table_capacity(c) if affine else -1
+    b = plan_bounds(graph, c, cand["min_avg_degree"], max_global_vertices=mg, table_vertices=tb)
     return SegmentedPageRank(graph, bounds=b, merge_block=merge_block, threads=t, ctas_per_sm=c,
-                             table_vertices=tb, overlap=cand.get("overlap", 0))
+                             table_vertices=tb, overlap=cand.get("overlap", 0), affine=affine)
 
 
 def autotune_segments(graph: Graph, candidates=None, merge_block: int = 512,
@@ -283,7 +293,7 @@ class LabelPropagation:
 
     def __init__(self, graph: Graph, num_segments: int | None = None, bounds=None,
                  merge_block: int = 512, threads: int = 1024, ctas_per_sm: int = 1,
-                 table_vertices: int = -1, overlap: int = 0):
+                 table_vertices: int = -1, overlap: int = 0, affine: float = 0.0):
         self.g = graph
         if bounds is not None:
             bounds = np.asarray(bounds, dtype=np.int64)
@@ -294,6 +304,8 @@ class LabelPropagation:
             C.pr_set_gather_config(self.seg, threads, ctas_per_sm, table_vertices)
         if overlap:
             C.pr_set_gather_overlap(self.seg, overlap)
+        if affine:
+            C.pr_set_gather_affine(self.seg, affine)
         V = graph.V
         self.labels = [torch.empty(V, dtype=torch.int32, device=graph.device) for _ in range(2)]
 

@@ -451,7 +451,10 @@ def test_planned_bounds(C, torch_mod, rmat16, rmat16_oracle):
     while m + 1 < len(b) and b[m + 1] - b[m] == 2048 and od[b[m]:b[m + 1]].sum() >= 8 * 2048:
         m += 1
     assert m >= 1
-    assert np.all(np.diff(b[m:]) <= 20000)
+    # cold segments of <= 20000 sources; the trailing sources without out-edges
+    # form one segment of their own, whatever its size
+    d = np.diff(b[m:])
+    assert np.all(d[:-1] <= 20000) and (d[-1] <= 20000 or od[b[-2]:].sum() == 0)
     if b[m] + 2048 <= graph.V:
         assert od[b[m]:b[m] + 2048].sum() < 8 * 2048
     pr = P.SegmentedPageRank(graph, bounds=b, threads=512, ctas_per_sm=2, table_vertices=2048)
@@ -475,9 +478,61 @@ def test_planned_bounds_default_cold_size_from_l2(C, torch_mod, rmat16):
     b = C.pr_plan_bounds(graph.outdeg, -1, 1e12, -1)
     assert b[0] == 0 and b[-1] == graph.V
     assert np.all(np.diff(b) <= l2 // 8)
-    # a tiny explicit size still wins
+    # a tiny explicit size still wins; the trailing sources without out-edges
+    # (the end of the clustered range) form one segment of their own
     b2 = C.pr_plan_bounds(graph.outdeg, -1, 1e12, 1000)
-    assert len(b2) - 1 == -(-graph.V // 1000) and np.all(np.diff(b2) <= 1000)
+    od = graph.outdeg.cpu().numpy()
+    end = int(np.flatnonzero(od > 0)[-1]) + 1
+    assert len(b2) - 1 == -(-end // 1000) + (end < graph.V)
+    assert np.all(np.diff(b2)[:-1] <= 1000) and b2[-2] == end and od[end:].sum() == 0
+
+
+@pytest.mark.parametrize("table", [2048, 8192])
+def test_affine_cold_segments(C, torch_mod, rmat16, rmat16_oracle, table):
+    """The nested plan: the cold range cut into table-sized segments, each
+    staged by one block (tables well below the capacity, so that RMAT-16 has
+    many such segments).  PageRank per vertex within the bound, the integer
+    gather + merge exact, and label propagation through it bit for bit."""
+    torch = torch_mod
+    from paper_1608_01362_gb300 import pipeline as P
+    graph = P.Graph(rmat16.offsets, rmat16.src, cluster_mode=0)
+    H = table
+    b = P.plan_bounds(graph, 1, 24.0, max_global_vertices=H, table_vertices=table)
+    pr = P.SegmentedPageRank(graph, bounds=b, table_vertices=table, affine=24.0)
+    info = pr.info
+    assert info["affine_segments"] >= 1 and info["affine_edges"] > 0
+    assert info["staged_edges"] + info["affine_edges"] <= graph.E
+    rank, _ = pr.run(20)
+    check_pagerank(rank.cpu().numpy(), rmat16_oracle[0], rmat16_oracle[2], what=f"affine {table}")
+    assert_gather_merge_exact(torch, C, rmat16, graph, pr.seg, f"affine {table}")
+    C.pr_set_gather_affine(pr.seg, 0)  # back to the L1/L2 launch for the same segments
+    assert pr.info["affine_segments"] == 0
+    assert_gather_merge_exact(torch, C, rmat16, graph, pr.seg, f"affine off {table}")
+    gs = graphgen.rmat(14, 8, seed=2, symmetric=True)
+    gg = P.Graph(gs.offsets, gs.src, cluster_mode=0)
+    lb = P.plan_bounds(gg, 1, 24.0, max_global_vertices=H, table_vertices=table)
+    lp = P.LabelPropagation(gg, bounds=lb, table_vertices=table, affine=24.0)
+    labels, passes, changes = lp.run()
+    want, wp, wc = O.label_propagation(gs.offsets, gs.src, np.arange(gs.V, dtype=np.int32))
+    assert passes == wp and np.array_equal(np.asarray(changes[:passes]), wc)
+    assert np.array_equal(labels.cpu().numpy(), want)
+
+
+def test_affine_rejects_bad_settings(C, torch_mod, rmat16):
+    from paper_1608_01362_gb300 import pipeline as P
+    graph = P.Graph(rmat16.offsets, rmat16.src, cluster_mode=0)
+    H = C.pr_gather_table_capacity(1)
+    pr = P.SegmentedPageRank(graph, bounds=P.plan_bounds(graph, 1, 24.0, max_global_vertices=H))
+    C.pr_set_gather_config(pr.seg, 512, 2, -1)
+    with pytest.raises(C.CagraError, match="1024 threads"):
+        C.pr_set_gather_affine(pr.seg, 24.0)
+    assert pr.info["affine_segments"] == 0
+    C.pr_set_gather_config(pr.seg, 1024, 1, -1)
+    C.pr_set_gather_overlap(pr.seg, 4)
+    with pytest.raises(C.CagraError, match="exclude"):
+        C.pr_set_gather_affine(pr.seg, 24.0)
+    with pytest.raises(C.CagraError, match="head_min_avg_degree"):
+        C.pr_set_gather_affine(pr.seg, -1.0)
 
 
 def test_autotuner_returns_valid_choice(C, torch_mod, rmat16):
