@@ -66,16 +66,21 @@ def _peaks():
         return 6800.0, "fallback"
 
 
-def gather_peaks(C, row_bytes_and_tables, smem=False):
-    """Random-read ceilings of this GPU, measured now (the row gathers are
-    bound by these, not by a streaming copy): {(row_bytes, table_bytes):
-    GB/s}, plus shared-memory lookups in G/s when smem."""
+def gather_peaks(probes, row_bytes_and_tables, smem=False):
+    """Random-read ceilings of this GPU, measured now by the probe library (the
+    row gathers are bound by these, not by a streaming copy): {(row_bytes,
+    table_bytes): GB/s}, plus shared-memory lookups in G/s when smem."""
     out = {}
     for rb, tb in row_bytes_and_tables:
-        out[(rb, tb)] = C.measure_row_gather(rb, tb) / 1e9
+        out[(rb, tb)] = probes.measure_row_gather(rb, tb) / 1e9
     if smem:
-        out["smem"] = C.measure_smem_lookups() / 1e9
+        out["smem"] = probes.measure_smem_lookups() / 1e9
     return out
+
+
+def _probes():
+    from paper_1608_01362_gb300 import probes
+    return probes
 
 
 class ClockSampler:
@@ -667,7 +672,7 @@ def run_ppr(args):
     # rate of such a table (measured now); hub rows reread from L1/L2 can
     # carry it above that rate
     rb = 128 * pl
-    gp = gather_peaks(C, [(rb, rb * nd)])
+    gp = gather_peaks(_probes(), [(rb, rb * nd)])
     a_rows = g.E * rb / (phase_ms["gather"] / 1e3) / 1e9
     gather_rows = {"bound": "random rows", "unit": "GB/s", "row_bytes": rb,
                    "table_bytes": rb * nd, "achieved": a_rows, "peak": gp[(rb, rb * nd)],
@@ -814,7 +819,7 @@ def run_cf(args):
     # the gathers read one factor row (4K bytes) per rating at random from an
     # L2-resident table: their ceiling is L2's random-row rate, measured now
     rb = 4 * K
-    gp = gather_peaks(C, [(rb, I * rb), (rb, U * rb)])
+    gp = gather_peaks(_probes(), [(rb, I * rb), (rb, U * rb)])
     gathers_l2 = {}
     for nm, tb in (("user_gather", I * rb), ("item_gather", U * rb)):
         a = R * rb / (head["kernels_ms"][nm] / 1e3) / 1e9
@@ -1529,7 +1534,7 @@ def main():
     # row, 20 B per vertex)
     staged_e = int(info["staged_edges"])
     cold_tab = 4 * max(2, min(1 << 24, V - int(info["staged_segments"]) * int(info["table_vertices"])))
-    gp = gather_peaks(C, [(4, cold_tab)], smem=True)
+    gp = gather_peaks(_probes(), [(4, cold_tab)], smem=True)
     m_bytes = 8 * rows + 20 * V
     per_launch = {
         "staged_gather": {"bound": "shared-memory random lookups", "unit": "G lookups/s",

@@ -18,6 +18,8 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libcagra_gb.so")
+PROBES = os.path.join(PKG, "probes")
+PROBES_LIB = os.path.join(PKG, "libcagra_probes.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -53,22 +55,32 @@ def _compile(src: str, verbose_ptxas: bool) -> str:
     return obj
 
 
-def build(verbose_ptxas: bool = False, jobs: int | None = None) -> str:
-    """Compile every csrc/*.cu and link libcagra_gb.so; returns its path."""
-    os.makedirs(BUILD, exist_ok=True)
-    srcs = sorted(glob.glob(os.path.join(CSRC, "*.cu")))
-    jobs = jobs or min(len(srcs), os.cpu_count() or 4)
-    with cf.ThreadPoolExecutor(max_workers=jobs) as ex:
-        objs = list(ex.map(lambda s: _compile(s, verbose_ptxas), srcs))
-    if os.path.exists(LIB) and all(os.path.getmtime(LIB) >= os.path.getmtime(o) for o in objs):
-        return LIB
-    tmp = LIB + f".tmp{os.getpid()}"
+def _link(lib: str, objs) -> str:
+    if os.path.exists(lib) and all(os.path.getmtime(lib) >= os.path.getmtime(o) for o in objs):
+        return lib
+    tmp = lib + f".tmp{os.getpid()}"
     cmd = [nvcc(), *ARCH, "-shared", "-o", tmp, *objs]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stderr}")
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
+
+
+def build(verbose_ptxas: bool = False, jobs: int | None = None) -> str:
+    """Compile every csrc/*.cu and link libcagra_gb.so (the product library),
+    and the benchmark's measurement probes (probes/*.cu with csrc/common.cu)
+    into libcagra_probes.so; returns the product library's path."""
+    os.makedirs(BUILD, exist_ok=True)
+    srcs = sorted(glob.glob(os.path.join(CSRC, "*.cu")))
+    psrcs = sorted(glob.glob(os.path.join(PROBES, "*.cu")))
+    jobs = jobs or min(len(srcs) + len(psrcs), os.cpu_count() or 4)
+    with cf.ThreadPoolExecutor(max_workers=jobs) as ex:
+        objs = list(ex.map(lambda s: _compile(s, verbose_ptxas), srcs + psrcs))
+    lib = _link(LIB, objs[:len(srcs)])
+    common = [o for o in objs[:len(srcs)] if os.path.basename(o) == "common.cu.o"]
+    _link(PROBES_LIB, objs[len(srcs):] + common)
+    return lib
 
 
 if __name__ == "__main__":

@@ -37,7 +37,7 @@ EXPORTS = [
     "ppr_batched_create", "ppr_batched_destroy", "ppr_batched_bytes", "ppr_batched_init",
     "ppr_batched_iterate", "ppr_batched_step",
     "cf_transpose", "cf_create", "cf_destroy", "cf_set_factors", "cf_get_factors", "cf_sweep",
-    "cf_sweep_phase", "cf_info", "cg_measure_row_gather", "cg_measure_smem_lookups",
+    "cf_sweep_phase", "cf_info",
     "cg_permute8", "cg_transpose_csr", "bc_create", "bc_destroy", "bc_set_direction", "bc_run",
     "bc_source_state", "cg_split_hub_block", "ppr_batched_attach_dense", "pr_set_gather_affine",
 ]
@@ -138,8 +138,6 @@ def load(path: str | None = None):
             "bc_set_direction": (ctypes.c_int, [vp, dbl]),
             "bc_run": (ctypes.c_int, [vp, vp, i32, vp, vp]),
             "bc_source_state": (ctypes.c_int, [vp, vp, vp, vp, vp, vp, vp, vp]),
-            "cg_measure_row_gather": (ctypes.c_int, [i32, i64, vp, vp]),
-            "cg_measure_smem_lookups": (ctypes.c_int, [vp, vp]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)
@@ -715,18 +713,3 @@ def torch_float64():
     return torch.float64
 
 
-def measure_row_gather(row_bytes: int, table_bytes: int, stream=None) -> float:
-    """Bytes per second of random row reads (rows of 4, 128 or 256 bytes)
-    from a table of table_bytes on the current GPU."""
-    out = ctypes.c_double()
-    _check(load().cg_measure_row_gather(row_bytes, int(table_bytes), ctypes.byref(out),
-                                        _stream(stream)), "cg_measure_row_gather")
-    return out.value
-
-
-def measure_smem_lookups(stream=None) -> float:
-    """Random 4-byte shared-memory lookups per second on the current GPU."""
-    out = ctypes.c_double()
-    _check(load().cg_measure_smem_lookups(ctypes.byref(out), _stream(stream)),
-           "cg_measure_smem_lookups")
-    return out.value

@@ -11,9 +11,9 @@ import pytest
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
-def _declared():
+def _declared(header="cagra_gb.h"):
     names = []
-    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+    for h in glob.glob(os.path.join(ROOT, "include", header)):
         txt = open(h).read()
         txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
         names += re.findall(r"^\s*(?:const\s+)?[A-Za-z_][\w \*]*?\b([A-Za-z_]\w*)\s*\(", txt,
@@ -37,6 +37,20 @@ def test_every_declared_symbol_is_exported(lib):
     for name in declared:
         assert hasattr(lib, name), f"{name} declared in include/ but not exported"
     assert sorted(cagra.EXPORTS) == declared
+
+
+def test_probe_library_is_separate(lib):
+    """The benchmark's measurement probes live in libcagra_probes.so, declared
+    in include/cagra_probes.h; the product library does not export them."""
+    from paper_1608_01362_gb300 import build, probes
+    plib = ctypes.CDLL(build.PROBES_LIB)
+    declared = _declared("cagra_probes.h")
+    assert declared == sorted(probes.EXPORTS)
+    for name in declared:
+        assert hasattr(plib, name)
+        assert not hasattr(lib, name), f"{name} exported by the product library"
+    assert sorted(set(glob.glob(os.path.join(ROOT, "include", "*.h")))) == sorted(
+        os.path.join(ROOT, "include", h) for h in ("cagra_gb.h", "cagra_probes.h"))
 
 
 def test_status_strings_without_gpu(lib):

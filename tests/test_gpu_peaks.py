@@ -1,6 +1,6 @@
-"""The roofline denominators measured on the GPU (random-row reads, shared-
-memory lookups): plausible magnitudes, the L2-resident table no slower than
-the HBM-sized one, and argument checks."""
+"""The roofline denominators measured on the GPU by the benchmark's probe
+library (random-row reads, shared-memory lookups): plausible magnitudes, the
+L2-resident table no slower than the HBM-sized one, and argument checks."""
 import pytest
 
 pytestmark = pytest.mark.gpu
@@ -10,10 +10,11 @@ pytestmark = pytest.mark.gpu
 def C():
     import torch
     assert torch.cuda.is_available()
-    from paper_1608_01362_gb300 import build, cagra
+    from paper_1608_01362_gb300 import build, cagra, probes
     build.build()
-    cagra.load()
-    return cagra
+    probes.load()
+    probes.CagraError = cagra.CagraError
+    return probes
 
 
 def test_row_gather_rates(C):
