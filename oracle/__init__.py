@@ -396,6 +396,105 @@ def cf_sweep(U, I, uoff, uitem, urate, ioff, iuser, irate, P, Q, lam=0.05, step=
     return P, Q, float(sse.value)
 
 
+def _gam(n, u=U_FP32):
+    n = np.asarray(n, dtype=np.float64)
+    return n * u / (1.0 - n * u)
+
+
+def _side_bound(off, nbr, val, X, Y, Xn, lam, step, u, u_store, sel=None):
+    """Per-entry bound of one side of a CF sweep (own factors X, neighbour
+    factors Y, FP64 result Xn) at the vertices `sel` (None: all); see
+    cf_sweep_bound.  Also returns per vertex the FP64 sum of e^2 and its error
+    bound's two sums."""
+    off = np.asarray(off, np.int64)
+    if sel is not None:  # the selected vertices' rating lists as one CSR
+        sel = np.asarray(sel, np.int64)
+        sdeg = off[sel + 1] - off[sel]
+        soff = np.zeros(len(sel) + 1, np.int64)
+        np.cumsum(sdeg, out=soff[1:])
+        idx = np.repeat(off[sel] - soff[:-1], sdeg) + np.arange(soff[-1])
+        off, nbr, val = soff, np.asarray(nbr)[idx], np.asarray(val)[idx]
+        X, Xn = X[sel], Xn[sel]
+    n, K = X.shape
+    deg = np.diff(off)
+    rows = np.repeat(np.arange(n), deg)
+    Yr = Y[np.asarray(nbr, np.int64)]
+    prod = X[rows] * Yr
+    S = np.abs(prod).sum(axis=1)
+    e = np.asarray(val, np.float64) - prod.sum(axis=1)
+    gK = _gam(K, u)
+    de = gK * S + u * (np.abs(e) + gK * S)  # |fl(e) - e|: K-term dot, then r - dot
+
+    def per_vertex(a):
+        out = np.zeros((n,) + a.shape[1:])
+        nz = deg > 0
+        if nz.any():
+            out[nz] = np.add.reduceat(a, off[:-1][nz], axis=0)
+        return out
+
+    absY = np.abs(Yr)
+    G = per_vertex(e[:, None] * Yr)
+    A1 = per_vertex(de[:, None] * absY)
+    A2 = per_vertex((np.abs(e) + de)[:, None] * absY) * (1.0 + 1e-12)
+    g2 = _gam(2, u)
+    dg = np.maximum(deg, 1).astype(np.float64)[:, None]
+    Eg = A1 + _gam(deg, u)[:, None] * A2           # any tree over deg products
+    Ea = (Eg / dg) * (1.0 + g2) + g2 * np.abs(G) / dg  # times a rounded 1/deg
+    Eb = g2 * lam * np.abs(X)                       # rounded lambda, one product
+    c = G / dg - lam * X
+    Ec = Ea + Eb + u * (np.abs(c) + Ea + Eb)
+    Ed = step * ((1.0 + g2) * Ec + g2 * np.abs(c))  # rounded step, one product
+    Ex = Ed + u * (np.abs(Xn) + Ed)                 # x + d
+    slack = 2.0 ** -44 * (np.abs(X) + step * (np.abs(c) + A2 / dg + lam * np.abs(X)))
+    bound = Ex + u_store * (np.abs(Xn) + Ex) + slack
+    sse_v = per_vertex(e * e)
+    sse_err_v = per_vertex(2.0 * np.abs(e) * de + de * de)
+    return bound, deg, sse_v, sse_err_v
+
+
+def cf_sweep_bound(U, I, uoff, uitem, urate, ioff, iuser, irate, P, Q, lam=0.05, step=1e-3,
+                   u_store=0.0, piece=None, u=U_FP32, users=None, items=None):
+    """One FP64 sweep (cf_sweep) and, per entry of P' and Q', a bound on how
+    far a reduced-precision evaluation of the same sweep from the same P, Q
+    can land from it; and a bound on its sum of squared errors.
+
+    The evaluation it covers computes in arithmetic of unit roundoff u (FP32
+    by default): each rating's dot product p_u . q_i with any summation tree
+    (fused or separate multiply-adds), e = r - dot with one rounding, each
+    vertex's gradient sum of e * y over its ratings with any summation tree,
+    the division by deg as a rounded reciprocal and a product, lambda and the
+    step rounded to that arithmetic, and x + step (g/deg - lambda x) with one
+    rounding per operation; then it stores x' in a format of relative
+    rounding u_store (0: FP32; U_BF16: BF16; U_BF16X2: a BF16 hi + lo pair).
+    Standard bounds (Higham, Accuracy and Stability of Numerical Algorithms,
+    Lemma 3.1 and Sec. 3.1): a sum of n terms in any tree has error at most
+    gamma_{n-1} times the sum of the absolute terms, gamma_n = n u / (1 - n u).
+    Per rating (S = sum_j |p_uj q_ij|):
+        |fl(e) - e| <= gamma_K S + u (|e| + gamma_K S) =: de
+    per vertex v and dimension k (the terms are e y_k; G = sum e y_k):
+        |fl(G) - G| <= sum de |y_k| + gamma_deg sum (|e| + de) |y_k|
+    and through the update, each rounding adding u times the magnitude of its
+    result plus the error carried in.  The SSE is formed in partial sums of at
+    most `piece` ratings of one user (None: all of them) in that arithmetic,
+    combined in FP64.  Returns (P', Q', sse, bound_P, bound_Q, bound_sse);
+    with `users` (`items`) given, bound_P (bound_Q) holds only those rows, in
+    that order, and bound_sse is None unless every user is covered."""
+    P64 = _c(P, np.float64)
+    Q64 = _c(Q, np.float64)
+    Pn, Qn, sse = cf_sweep(U, I, uoff, uitem, urate, ioff, iuser, irate, P64, Q64, lam, step)
+    bP, udeg, sse_u, sse_err_u = _side_bound(uoff, uitem, urate, P64, Q64, Pn, lam, step, u,
+                                             u_store, users)
+    bQ = _side_bound(ioff, iuser, irate, Q64, P64, Qn, lam, step, u, u_store, items)[0]
+    if users is not None:
+        return Pn, Qn, sse, bP, bQ, None
+    m = udeg if piece is None else np.minimum(udeg, piece)
+    gm = _gam(m, u)
+    b_sse = float(np.sum(sse_err_u * (1.0 + gm) + gm * sse_u))
+    # FP64 combination of the partials, and the FP64 sum above
+    b_sse += _gam(int(np.sum(udeg)) + len(udeg) + 4096, 2.0 ** -53) * float(np.sum(sse_u) + b_sse)
+    return Pn, Qn, sse, bP, bQ, b_sse
+
+
 
 # --------------------------------------------------------------------------
 # Betweenness centrality (Table V: 12 sources; Brandes' algorithm)

@@ -1,17 +1,23 @@
 """Collaborative filtering sweeps on the GPU (through the C ABI) against the
-FP64 oracle: the item-major transpose bit for bit, factors and squared error
-per sweep within bounds derived from each storage precision.
+FP64 oracle: the item-major transpose bit for bit; every sweep entry by
+entry within the oracle's rounding bound (oracle.cf_sweep_bound) from the
+factors the GPU holds before it; and the drift of several sweeps from the
+oracle's own trajectory within bounds derived from each storage precision.
 
-Bounds.  A sweep moves a factor by step * (g - lambda x) (step 1e-3) and
-stores it back.  FP32 storage rounds it with relative error 2^-24 and the
-FP32 gradient sums add a few more units: after T sweeps the factors stay
-within about (T + 1) * 8 * 2^-24 of the largest entry (bound used 2e-6).
-BF16 storage (8 significant bits, unit roundoff 2^-8) rounds every entry
-once at load and once per sweep: |x_gpu - x_64| <= (T + 1) * 2^-8 * max|x|;
-two planes (hi + lo: |x - hi| <= 2^-8 |x|, then |x - hi - lo| <= 2^-8
-|x - hi| <= 2^-16 |x|) give (T + 1) * 2^-16 * max|x|, plus the FP32 terms.
-The squared error sums e^2 over a piece in FP32 (at most 64 terms per lane, then 32
-lanes): relative 1e-5 at FP32 storage.
+Per sweep (the bound's derivation is in oracle.cf_sweep_bound): the GPU's
+stored factors are read back (decoded to FP32, exactly what the next sweep
+reads), one FP64 sweep runs from them, and every entry of the GPU's next
+factors must lie within the bound of an FP32 evaluation plus the storage
+rounding (BF16: 2^-8 relative; BF16 hi + lo: 2^-16).  The sum of squared
+errors must lie within its bound too.
+
+Drift over T sweeps: a sweep moves a factor by step * (g - lambda x)
+(step 1e-3) and stores it back.  FP32 storage rounds it with relative error
+2^-24 and the FP32 gradient sums add a few more units: after T sweeps the
+factors stay within about (T + 1) * 8 * 2^-24 of the largest entry (bound
+used 2e-6).  BF16 storage rounds every entry once at load and once per
+sweep: |x_gpu - x_64| <= (T + 1) * 2^-8 * max|x|; two planes give
+(T + 1) * 2^-16 * max|x|, plus the FP32 terms.
 """
 import json
 import os
@@ -207,3 +213,35 @@ def test_hub_item_block_update(env):
     assert np.max(np.abs(Pg - P)) <= 2e-6 * np.max(np.abs(P))
     assert np.max(np.abs(Qg - Q)) <= 2e-6 * np.max(np.abs(Q))
     assert np.all(np.abs(sse - want) <= 1e-5 * want)
+
+
+@pytest.mark.parametrize("K,precision", [(32, 0), (16, 0), (64, 0), (32, 1), (32, 2), (64, 2)])
+def test_each_sweep_within_per_entry_bound(env, small, K, precision):
+    torch, C = env
+    bp = small
+    u_store = {0: 0.0, 1: O.U_BF16, 2: O.U_BF16X2}[precision]
+    d = upload(torch, C, bp)
+    ioff, iuser, irate = O.item_major(bp.U, bp.I, bp.user_offsets, bp.items, bp.ratings)
+    P0, Q0 = graphgen.cf_factors(bp.U, bp.I, K, seed=2)
+    h = C.cf_create(bp.U, bp.I, K, precision, *d)
+    C.cf_set_factors(h, _dev(torch, P0, torch.float32), _dev(torch, Q0, torch.float32))
+    Pg = torch.empty((bp.U, K), dtype=torch.float32, device="cuda")
+    Qg = torch.empty((bp.I, K), dtype=torch.float32, device="cuda")
+    sse = torch.zeros(1, dtype=torch.float64, device="cuda")
+    worst = 0.0
+    for t in range(4):
+        C.cf_get_factors(h, Pg, Qg)  # what the GPU's next sweep reads
+        P = Pg.cpu().numpy().astype(np.float64)
+        Q = Qg.cpu().numpy().astype(np.float64)
+        C.cf_sweep(h, 1, LAM, STEP, sse)
+        C.cf_get_factors(h, Pg, Qg)
+        Pn, Qn, s64, bP, bQ, bs = O.cf_sweep_bound(bp.U, bp.I, bp.user_offsets, bp.items,
+                                                   bp.ratings, ioff, iuser, irate, P, Q, LAM,
+                                                   STEP, u_store=u_store)
+        eP = np.abs(Pg.cpu().numpy().astype(np.float64) - Pn)
+        eQ = np.abs(Qg.cpu().numpy().astype(np.float64) - Qn)
+        assert np.all(eP <= bP), f"sweep {t}: {np.sum(eP > bP)} P entries outside the bound"
+        assert np.all(eQ <= bQ), f"sweep {t}: {np.sum(eQ > bQ)} Q entries outside the bound"
+        assert abs(float(sse.item()) - s64) <= bs
+        worst = max(worst, float(np.max(eP / bP)), float(np.max(eQ / bQ)))
+    assert worst > 0.0  # the GPU's rounding is seen at all (not a copy of the oracle)

@@ -125,8 +125,11 @@ def test_batched_ppr_rmat22_sampled_columns(env):
 
 
 def test_cf_netflix_shape_two_sweeps(env):
-    """The full rating graph, K = 32: two FP32 sweeps within 2e-6 of FP64 and
-    the SSE within 1e-5; BF16 hi+lo within its storage bound."""
+    """The full rating graph, K = 32, FP32 and BF16 hi+lo storage: each sweep
+    entry by entry within the oracle's rounding bound at sampled users and
+    items (from the factors the GPU holds before it); after two sweeps the
+    factors within 2e-6 (FP32) or the storage bound (BF16 hi+lo) of the
+    largest FP64 entry, and the FP32 SSE within 1e-5."""
     torch, C, P = env
     bp = graphgen.bipartite(seed=1)
     dev = lambda a, dt: torch.as_tensor(np.ascontiguousarray(a), dtype=dt).cuda()  # noqa: E731
@@ -146,14 +149,37 @@ def test_cf_netflix_shape_two_sweeps(env):
                                Qw, 0.05, 1e-3)
         want_sse.append(e)
     want_sse = np.array(want_sse)
+    # per-entry checks at sampled rows: random users, the busiest users, and
+    # items from the long tail up to hubs of several hundred thousand ratings
+    # (the block-per-item update path)
+    rng = np.random.default_rng(11)
+    udeg, ideg = np.diff(bp.user_offsets), np.diff(io)
+    users = np.unique(np.concatenate([rng.choice(bp.U, 4096, replace=False),
+                                      np.argsort(udeg)[-16:]]))
+    by_deg = np.argsort(ideg)[::-1]
+    items = np.unique(np.concatenate([by_deg[[20, 100, 1000, 5000]],
+                                      rng.choice(bp.I, 60, replace=False)]))
+    items = items[ideg[items] <= 1_000_000]
     for prec, tol in ((C.CF_FP32, 2e-6), (C.CF_BF16X2, 3 * 2.0 ** -16 + 2e-6)):
         h = C.cf_create(bp.U, bp.I, 32, prec, uoff, uitem, urate, ioff, iuser, irate)
         C.cf_set_factors(h, dev(P0, torch.float32), dev(Q0, torch.float32))
         sse = torch.zeros(2, dtype=torch.float64, device="cuda")
-        C.cf_sweep(h, 2, 0.05, 1e-3, sse)
         Pg = torch.empty((bp.U, 32), dtype=torch.float32, device="cuda")
         Qg = torch.empty((bp.I, 32), dtype=torch.float32, device="cuda")
-        C.cf_get_factors(h, Pg, Qg)
+        u_store = 0.0 if prec == C.CF_FP32 else O.U_BF16X2
+        for t in range(2):
+            C.cf_get_factors(h, Pg, Qg)  # what this sweep reads
+            Pr, Qr = Pg.cpu().numpy().astype(np.float64), Qg.cpu().numpy().astype(np.float64)
+            C.cf_sweep(h, 1, 0.05, 1e-3, sse[t:t + 1])
+            C.cf_get_factors(h, Pg, Qg)
+            Pn, Qn, _, bP, bQ, _ = O.cf_sweep_bound(bp.U, bp.I, bp.user_offsets, bp.items,
+                                                    bp.ratings, io, iu, ir, Pr, Qr, 0.05, 1e-3,
+                                                    u_store=u_store, users=users, items=items)
+            eP = np.abs(Pg.cpu().numpy()[users].astype(np.float64) - Pn[users])
+            eQ = np.abs(Qg.cpu().numpy()[items].astype(np.float64) - Qn[items])
+            assert np.all(eP <= bP), f"sweep {t}: {np.sum(eP > bP)} sampled P entries outside"
+            assert np.all(eQ <= bQ), f"sweep {t}: {np.sum(eQ > bQ)} sampled Q entries outside"
+        # drift of the two sweeps from the oracle's own trajectory
         assert np.max(np.abs(Pg.cpu().numpy() - Pw)) <= tol * np.max(np.abs(Pw))
         assert np.max(np.abs(Qg.cpu().numpy() - Qw)) <= tol * np.max(np.abs(Qw))
         if prec == C.CF_FP32:
