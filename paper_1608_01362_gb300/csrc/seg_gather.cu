@@ -368,18 +368,21 @@ __device__ __forceinline__ void staged_chunk(const uint32_t (&pk)[8], uint32_t f
   constexpr int CHUNK = kStagedChunk;
   const int lane = threadIdx.x & 31;
   T v[IPL];
+  const uint32_t tmax2 = tmax | (tmax << 16);  // both 16-bit halves clamped at once
   if (n == CHUNK) {
 #pragma unroll
-    for (int u = 0; u < IPL; ++u) {
-      const uint32_t idx = (u & 1) ? (pk[u >> 1] >> 16) : (pk[u >> 1] & 0xFFFFu);
-      v[u] = tab[idx < tmax ? idx : tmax];
+    for (int u = 0; u < IPL; u += 2) {
+      const uint32_t q = __vminu2(pk[u >> 1], tmax2);
+      v[u] = tab[q & 0xFFFFu];
+      v[u + 1] = tab[q >> 16];
     }
   } else {  // a segment's last chunk: lanes past its end hold nothing
     const int nl = n - lane * IPL;
 #pragma unroll
-    for (int u = 0; u < IPL; ++u) {
-      const uint32_t idx = (u & 1) ? (pk[u >> 1] >> 16) : (pk[u >> 1] & 0xFFFFu);
-      v[u] = u < nl ? tab[idx < tmax ? idx : tmax] : Op::identity();
+    for (int u = 0; u < IPL; u += 2) {
+      const uint32_t q = __vminu2(pk[u >> 1], tmax2);
+      v[u] = u < nl ? tab[q & 0xFFFFu] : Op::identity();
+      v[u + 1] = u + 1 < nl ? tab[q >> 16] : Op::identity();
     }
     fl &= nl >= IPL ? 0xFFFFu : (nl <= 0 ? 0u : ((1u << nl) - 1u));
   }
