@@ -104,16 +104,6 @@ __global__ void list_degree_kernel(const int32_t* __restrict__ list, int64_t n,
   }
 }
 
-// last i in [0, n) with rend[i] <= k (rend ascending, rend[0] = 0 <= k)
-__device__ __forceinline__ int64_t row_of(const int64_t* rend, int64_t n, int64_t k) {
-  int64_t lo = 0, hi = n;
-  while (lo < hi) {
-    const int64_t mid = (lo + hi) >> 1;
-    if (rend[mid] <= k) lo = mid + 1; else hi = mid;
-  }
-  return lo - 1;
-}
-
 // Append v to lists at a position from one atomic per warp.
 __device__ __forceinline__ void append(bool take, int32_t v, int32_t* lists, int32_t* counter) {
   const unsigned m = __ballot_sync(0xffffffffu, take);
@@ -125,21 +115,58 @@ __device__ __forceinline__ void append(bool take, int32_t v, int32_t* lists, int
   if (take) lists[base + __popc(m & ((1u << lane) - 1u))] = v;
 }
 
-// Push: one thread per out-edge of the frontier (list, n vertices, m edges).
-__global__ void push_kernel(const int32_t* __restrict__ list, int64_t n,
-                            const int64_t* __restrict__ rend, int64_t m,
-                            const int64_t* __restrict__ out_off, const int32_t* __restrict__ out_dst,
-                            int32_t L, int32_t* __restrict__ level, double* __restrict__ sigma,
-                            int32_t* __restrict__ lists, int32_t* __restrict__ counter) {
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t k0 = (int64_t)blockIdx.x * blockDim.x; k0 < m; k0 += stride) {
+// The out-edges [0, m) of a list's vertices laid end to end (row i = list
+// position i, starting at rend[i]) are cut into merge-path tiles of rows +
+// edges (tile_row / tile_edge, as for the gather); the block of tile t keeps
+// the starts rend[r0 .. r1] of the tile's rows in shared memory, so each of
+// its edges finds its row with a binary search in shared memory.  Returns
+// the number of row starts loaded (0: the tile has no edges).
+__device__ __forceinline__ int load_tile_rows(const int64_t* __restrict__ rend, int64_t n,
+                                              const int32_t* __restrict__ tile_row,
+                                              const int32_t* __restrict__ tile_edge,
+                                              int64_t* s_start, int64_t& r0, int64_t& e0,
+                                              int64_t& e1) {
+  const int64_t t = blockIdx.x;
+  r0 = tile_row[t];
+  e0 = tile_edge[t];
+  e1 = tile_edge[t + 1];
+  if (e0 >= e1) return 0;
+  const int64_t rl = tile_row[t + 1] < n - 1 ? tile_row[t + 1] : n - 1;
+  const int cnt = (int)(rl - r0 + 1);  // <= kTileItems + 1
+  for (int j = threadIdx.x; j < cnt; j += blockDim.x) s_start[j] = rend[r0 + j];
+  __syncthreads();
+  return cnt;
+}
+
+// last j in [0, cnt) with s_start[j] <= k (s_start ascending, s_start[0] <= k)
+__device__ __forceinline__ int tile_row_of(const int64_t* s_start, int cnt, int64_t k) {
+  int lo = 0, hi = cnt;
+  while (lo < hi) {
+    const int mid = (lo + hi) >> 1;
+    if (s_start[mid] <= k) lo = mid + 1; else hi = mid;
+  }
+  return lo - 1;
+}
+
+// Push: the frontier's (list, n vertices) out-edges, a tile per block.
+__global__ void __launch_bounds__(kThreads)
+push_kernel(const int32_t* __restrict__ list, int64_t n, const int64_t* __restrict__ rend,
+            const int32_t* __restrict__ tile_row, const int32_t* __restrict__ tile_edge,
+            const int64_t* __restrict__ out_off, const int32_t* __restrict__ out_dst, int32_t L,
+            int32_t* __restrict__ level, double* __restrict__ sigma,
+            int32_t* __restrict__ lists, int32_t* __restrict__ counter) {
+  __shared__ int64_t s_start[kTileItems + 1];
+  int64_t r0, e0, e1;
+  const int cnt = load_tile_rows(rend, n, tile_row, tile_edge, s_start, r0, e0, e1);
+  if (cnt == 0) return;
+  for (int64_t k0 = e0; k0 < e1; k0 += blockDim.x) {
     const int64_t k = k0 + threadIdx.x;  // the warp stays converged for the append
     bool take = false;
     int32_t w = 0;
-    if (k < m) {
-      const int64_t i = row_of(rend, n, k);
-      const int32_t u = list[i];
-      w = out_dst[out_off[u] + (k - rend[i])];
+    if (k < e1) {
+      const int j = tile_row_of(s_start, cnt, k);
+      const int32_t u = list[r0 + j];
+      w = out_dst[out_off[u] + (k - s_start[j])];
       const int32_t old = atomicCAS(level + w, -1, L + 1);
       take = old == -1;
       if (old == -1 || old == L + 1) atomicAdd(sigma + w, sigma[u]);
@@ -189,15 +216,19 @@ __global__ void deepest_kernel(const int32_t* __restrict__ list, int64_t n,
   }
 }
 
-// The out-rows of a level's vertices end to end.
-__global__ void expand_kernel(const int32_t* __restrict__ list, int64_t n,
-                              const int64_t* __restrict__ rend, int64_t m,
-                              const int64_t* __restrict__ out_off,
-                              const int32_t* __restrict__ out_dst, int32_t* __restrict__ col_v) {
-  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < m;
-       k += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t i = row_of(rend, n, k);
-    col_v[k] = out_dst[out_off[list[i]] + (k - rend[i])];
+// The out-rows of a level's vertices end to end, a tile per block.
+__global__ void __launch_bounds__(kThreads)
+expand_kernel(const int32_t* __restrict__ list, int64_t n, const int64_t* __restrict__ rend,
+              const int32_t* __restrict__ tile_row, const int32_t* __restrict__ tile_edge,
+              const int64_t* __restrict__ out_off, const int32_t* __restrict__ out_dst,
+              int32_t* __restrict__ col_v) {
+  __shared__ int64_t s_start[kTileItems + 1];
+  int64_t r0, e0, e1;
+  const int cnt = load_tile_rows(rend, n, tile_row, tile_edge, s_start, r0, e0, e1);
+  if (cnt == 0) return;
+  for (int64_t k = e0 + threadIdx.x; k < e1; k += blockDim.x) {
+    const int j = tile_row_of(s_start, cnt, k);
+    col_v[k] = out_dst[out_off[list[r0 + j]] + (k - s_start[j])];
   }
 }
 
@@ -268,6 +299,19 @@ int level_rows(cg_bc* h, const int32_t* list, int64_t n, int64_t* m, cudaStream_
   return read_i64(h, h->rend + n, m, s);
 }
 
+int grow_vt(cg_bc* h, int64_t ntiles);
+
+// Merge-path tiles of a list's n rows and m out-edges (rend: row starts,
+// rend[n] = m) into h->vt_row / h->vt_edge; *ntiles = their number.
+int level_tiles(cg_bc* h, int64_t n, int64_t m, int64_t* ntiles, cudaStream_t s) {
+  *ntiles = ceil_div(n + m, kTileItems);
+  CG_TRY(grow_vt(h, *ntiles));
+  tile_partition_kernel<int64_t><<<grid_for(*ntiles + 1, 256), 256, 0, s>>>(
+      h->rend + 1, n, m, kTileItems, *ntiles, h->vt_row, h->vt_edge);
+  CG_LAUNCH_CHECK();
+  return CG_OK;
+}
+
 int grow_vt(cg_bc* h, int64_t ntiles) {
   if (ntiles + 1 <= h->vt_cap) return CG_OK;
   cudaFree(h->vt_row);
@@ -330,9 +374,12 @@ int run_source(cg_bc* h, int32_t src, double* bc, cudaStream_t s) {
         CG_LAUNCH_CHECK();
         ++h->pull_levels;
       } else {  // push from the frontier's out-edges
-        push_kernel<<<grid_for(m, kThreads), kThreads, 0, s>>>(list, n, h->rend, m, h->out_off,
-                                                              h->out_dst, L, h->level, h->sigma,
-                                                              h->lists, h->counter);
+        int64_t ntiles = 0;
+        CG_TRY(level_tiles(h, n, m, &ntiles, s));
+        push_kernel<<<(unsigned)ntiles, kThreads, 0, s>>>(list, n, h->rend, h->vt_row,
+                                                          h->vt_edge, h->out_off, h->out_dst, L,
+                                                          h->level, h->sigma, h->lists,
+                                                          h->counter);
         CG_LAUNCH_CHECK();
         ++h->push_levels;
       }
@@ -364,13 +411,11 @@ int run_source(cg_bc* h, int32_t src, double* bc, cudaStream_t s) {
     int64_t m = 0;
     CG_TRY(level_rows(h, list, n, &m, s));
     if (m > 0) {
-      expand_kernel<<<grid_for(m, kThreads), kThreads, 0, s>>>(list, n, h->rend, m, h->out_off,
-                                                              h->out_dst, h->col_v);
-      CG_LAUNCH_CHECK();
-      const int64_t ntiles = ceil_div(n + m, kTileItems);
-      CG_TRY(grow_vt(h, ntiles));
-      tile_partition_kernel<int64_t><<<grid_for(ntiles + 1, 256), 256, 0, s>>>(
-          h->rend + 1, n, m, kTileItems, ntiles, h->vt_row, h->vt_edge);
+      int64_t ntiles = 0;
+      CG_TRY(level_tiles(h, n, m, &ntiles, s));
+      expand_kernel<<<(unsigned)ntiles, kThreads, 0, s>>>(list, n, h->rend, h->vt_row,
+                                                          h->vt_edge, h->out_off, h->out_dst,
+                                                          h->col_v);
       CG_LAUNCH_CHECK();
       gather_tile_kernel<SumF64, kTileThreads, kTileIPT, false, int64_t>
           <<<(unsigned)ntiles, kTileThreads, 0, s>>>(h->rend + 1, h->col_v, h->xval, V,
