@@ -45,6 +45,7 @@ struct cg_bc {
   double* delta = nullptr;     // [V] dependencies
   double* xval = nullptr;      // [V] gathered values (see above), 0 elsewhere
   double* acc = nullptr;       // [V] gathered sums
+  uint32_t* xbits = nullptr;   // [V/32 + 1] one bit per vertex: xval may be non-zero
   int32_t* lists = nullptr;    // [V] reached vertices, level after level
   int32_t* deg = nullptr;      // [V] out-degrees of one level's vertices
   int64_t* rend = nullptr;     // [V+1] their exclusive prefix (rend[n] = total)
@@ -73,22 +74,31 @@ constexpr int kThreads = 256;
 
 __global__ void bc_reset_kernel(int32_t V, int32_t* __restrict__ level,
                                 double* __restrict__ sigma, double* __restrict__ delta,
-                                double* __restrict__ xval) {
+                                double* __restrict__ xval, uint32_t* __restrict__ xbits) {
   for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < V;
        v += (int64_t)gridDim.x * blockDim.x) {
     level[v] = -1;
     sigma[v] = 0.0;
     delta[v] = 0.0;
     xval[v] = 0.0;
+    if ((v & 31) == 0) xbits[v >> 5] = 0u;
   }
 }
 
+__device__ __forceinline__ void set_bit(uint32_t* bits, int32_t v, bool on) {
+  if (on)
+    atomicOr(bits + (v >> 5), 1u << (v & 31));
+  else
+    atomicAnd(bits + (v >> 5), ~(1u << (v & 31)));
+}
+
 __global__ void bc_seed_kernel(int32_t s, int32_t* __restrict__ level, double* __restrict__ sigma,
-                               double* __restrict__ xval, int32_t* __restrict__ lists,
-                               int32_t* __restrict__ counter) {
+                               double* __restrict__ xval, uint32_t* __restrict__ xbits,
+                               int32_t* __restrict__ lists, int32_t* __restrict__ counter) {
   level[s] = 0;
   sigma[s] = 1.0;
   xval[s] = 1.0;
+  set_bit(xbits, s, true);
   lists[0] = s;
   *counter = 1;
 }
@@ -195,24 +205,28 @@ __global__ void pull_update_kernel(int32_t V, const double* __restrict__ acc, in
   }
 }
 
-// x over the vertices of a list: sigma (forward frontier) or 0.
+// x over the vertices of a list: sigma (forward frontier) or 0, with the
+// vertices' bits in xbits.
 __global__ void set_x_kernel(const int32_t* __restrict__ list, int64_t n,
                              const double* __restrict__ sigma, double* __restrict__ xval,
-                             bool clear) {
+                             uint32_t* __restrict__ xbits, bool clear) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
     const int32_t u = list[i];
     xval[u] = clear ? 0.0 : sigma[u];
+    set_bit(xbits, u, !clear);
   }
 }
 
 // The deepest level: delta = 0, x = 1 / sigma.
 __global__ void deepest_kernel(const int32_t* __restrict__ list, int64_t n,
-                               const double* __restrict__ sigma, double* __restrict__ xval) {
+                               const double* __restrict__ sigma, double* __restrict__ xval,
+                               uint32_t* __restrict__ xbits) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
     const int32_t u = list[i];
     xval[u] = 1.0 / sigma[u];
+    set_bit(xbits, u, true);
   }
 }
 
@@ -237,13 +251,15 @@ expand_kernel(const int32_t* __restrict__ list, int64_t n, const int64_t* __rest
 __global__ void dependency_kernel(const int32_t* __restrict__ list, int64_t n,
                                   const double* __restrict__ sums, const double* __restrict__ sigma,
                                   double* __restrict__ delta, double* __restrict__ xval,
-                                  double* __restrict__ bc, int32_t source) {
+                                  uint32_t* __restrict__ xbits, double* __restrict__ bc,
+                                  int32_t source) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
     const int32_t u = list[i];
     const double d = sigma[u] * sums[i];
     delta[u] = d;
     xval[u] = (1.0 + d) / sigma[u];
+    set_bit(xbits, u, true);
     if (u != source) bc[u] += d;
   }
 }
@@ -351,9 +367,10 @@ int order_levels(cg_bc* h, int32_t depth, cudaStream_t s) {
 int run_source(cg_bc* h, int32_t src, double* bc, cudaStream_t s) {
   const int32_t V = h->V;
   bc_reset_kernel<<<grid_for(V, kThreads), kThreads, 0, s>>>(V, h->level, h->sigma, h->delta,
-                                                               h->xval);
+                                                               h->xval, h->xbits);
   CG_LAUNCH_CHECK();
-  bc_seed_kernel<<<1, 1, 0, s>>>(src, h->level, h->sigma, h->xval, h->lists, h->counter);
+  bc_seed_kernel<<<1, 1, 0, s>>>(src, h->level, h->sigma, h->xval, h->xbits, h->lists,
+                                 h->counter);
   CG_LAUNCH_CHECK();
   h->lbase.assign(1, 0);
   h->lbase.push_back(1);
@@ -367,7 +384,7 @@ int run_source(cg_bc* h, int32_t src, double* bc, cudaStream_t s) {
     if (m > 0) {
       if ((double)m * h->alpha > (double)h->E) {  // pull over the in-edge CSR
         CG_TRY((run_tile_gather<SumF64, false, int64_t>(h->in_plan, h->in_off + 1, h->in_src,
-                                                        h->xval, V, h->acc, s)));
+                                                        h->xval, V, h->acc, s, h->xbits)));
         pull_update_kernel<<<grid_for(V, kThreads), kThreads, 0, s>>>(V, h->acc, L, h->level,
                                                                       h->sigma, h->lists,
                                                                       h->counter);
@@ -389,11 +406,12 @@ int run_source(cg_bc* h, int32_t src, double* bc, cudaStream_t s) {
     if (cnt == h->lbase[L + 1]) break;  // nothing new: L is the deepest level
     h->lbase.push_back(cnt);
     // the frontier moves on: x = sigma on level L+1 only
-    set_x_kernel<<<grid_for(n, kThreads), kThreads, 0, s>>>(list, n, h->sigma, h->xval, true);
+    set_x_kernel<<<grid_for(n, kThreads), kThreads, 0, s>>>(list, n, h->sigma, h->xval, h->xbits,
+                                                            true);
     CG_LAUNCH_CHECK();
     const int64_t n1 = cnt - h->lbase[L + 1];
     set_x_kernel<<<grid_for(n1, kThreads), kThreads, 0, s>>>(h->lists + h->lbase[L + 1], n1,
-                                                             h->sigma, h->xval, false);
+                                                             h->sigma, h->xval, h->xbits, false);
     CG_LAUNCH_CHECK();
   }
   const int32_t depth = (int32_t)h->lbase.size() - 1;  // levels 0 .. depth-1
@@ -401,7 +419,7 @@ int run_source(cg_bc* h, int32_t src, double* bc, cudaStream_t s) {
   {
     const int64_t b = h->lbase[depth - 1], n = h->lbase[depth] - b;
     deepest_kernel<<<grid_for(n, kThreads), kThreads, 0, s>>>(h->lists + b, n, h->sigma,
-                                                              h->xval);
+                                                              h->xval, h->xbits);
     CG_LAUNCH_CHECK();
   }
   // backward: levels depth-2 .. 0
@@ -417,10 +435,10 @@ int run_source(cg_bc* h, int32_t src, double* bc, cudaStream_t s) {
                                                           h->vt_edge, h->out_off, h->out_dst,
                                                           h->col_v);
       CG_LAUNCH_CHECK();
-      gather_tile_kernel<SumF64, kTileThreads, kTileIPT, false, int64_t>
+      gather_tile_kernel<SumF64, kTileThreads, kTileIPT, false, int64_t, true>
           <<<(unsigned)ntiles, kTileThreads, 0, s>>>(h->rend + 1, h->col_v, h->xval, V,
                                                      h->vt_row, h->vt_edge, h->acc, h->vt_carry,
-                                                     h->vt_carry_row);
+                                                     h->vt_carry_row, h->xbits);
       CG_LAUNCH_CHECK();
       carry_fixup_kernel<SumF64><<<grid_for(ntiles, 256, 4), 256, 0, s>>>(
           h->vt_carry, h->vt_carry_row, ntiles, n, h->acc);
@@ -429,7 +447,8 @@ int run_source(cg_bc* h, int32_t src, double* bc, cudaStream_t s) {
       CG_CUDA(cudaMemsetAsync(h->acc, 0, sizeof(double) * (size_t)n, s));
     }
     dependency_kernel<<<grid_for(n, kThreads), kThreads, 0, s>>>(list, n, h->acc, h->sigma,
-                                                                h->delta, h->xval, bc, src);
+                                                                h->delta, h->xval, h->xbits, bc,
+                                                                src);
     CG_LAUNCH_CHECK();
   }
   h->last_source = src;
@@ -501,6 +520,8 @@ int bc_create(const int64_t* in_offsets, const int32_t* in_src, const int64_t* o
   if (e == cudaSuccess) e = cudaMalloc((void**)&h->delta, v8);
   if (e == cudaSuccess) e = cudaMalloc((void**)&h->xval, v8);
   if (e == cudaSuccess) e = cudaMalloc((void**)&h->acc, v8);
+  if (e == cudaSuccess)
+    e = cudaMalloc((void**)&h->xbits, sizeof(uint32_t) * ((size_t)V / 32 + 1));
   if (e == cudaSuccess) e = cudaMalloc((void**)&h->lists, v4);
   if (e == cudaSuccess) e = cudaMalloc((void**)&h->deg, v4);
   if (e == cudaSuccess) e = cudaMalloc((void**)&h->rend, sizeof(int64_t) * ((size_t)V + 1));
@@ -536,6 +557,7 @@ int bc_destroy(cg_bc* h) {
   cudaFree(h->delta);
   cudaFree(h->xval);
   cudaFree(h->acc);
+  cudaFree(h->xbits);
   cudaFree(h->lists);
   cudaFree(h->deg);
   cudaFree(h->rend);

@@ -95,13 +95,17 @@ __global__ void tile_partition_kernel(const RowEndT* __restrict__ row_end, int64
 
 // The gather tile kernel.  row_end[i] = first edge after row i (global edge
 // index); col: global source IDs; PROBE sends every gathered read to x[0].
-template <class Op, int THREADS, int IPT, bool PROBE, typename RowEndT>
+// MASKED: xmask holds one bit per source; x is read only where the bit is
+// set (the identity elsewhere), so a sparse x (a frontier) costs a bit test
+// from a small, cache-resident array instead of a value read per edge.
+template <class Op, int THREADS, int IPT, bool PROBE, typename RowEndT, bool MASKED = false>
 __global__ void __launch_bounds__(THREADS)
 gather_tile_kernel(const RowEndT* __restrict__ row_end, const int32_t* __restrict__ col,
                    const typename Op::T* __restrict__ x, int32_t nx,
                    const int32_t* __restrict__ tile_row, const int32_t* __restrict__ tile_edge,
                    typename Op::T* __restrict__ out, typename Op::T* __restrict__ carry,
-                   int32_t* __restrict__ carry_row) {
+                   int32_t* __restrict__ carry_row,
+                   const uint32_t* __restrict__ xmask = nullptr) {
   using T = typename Op::T;
   constexpr int TILE = THREADS * IPT;
   constexpr int WARPS = THREADS / 32;
@@ -144,7 +148,8 @@ gather_tile_kernel(const RowEndT* __restrict__ row_end, const int32_t* __restric
 #pragma unroll
     for (int u = 0; u < IPT; ++u) {
       const int32_t cu = c[u];
-      const bool ok = cu >= 0 && cu < nx;
+      bool ok = cu >= 0 && cu < nx;
+      if constexpr (MASKED) ok = ok && ((__ldg(xmask + (cu >> 5)) >> (cu & 31)) & 1u);
       v[u] = ok ? ld_gather(x + (PROBE ? 0 : cu)) : Op::identity();
     }
 #pragma unroll
@@ -293,15 +298,23 @@ inline void free_tile_plan(TilePlan* p) {
 
 inline int64_t tile_plan_bytes(const TilePlan& p) { return 16 * (p.ntiles + 1); }
 
-// Launch gather + fix-up.  row_end points at the first row's end.
+// Launch gather + fix-up.  row_end points at the first row's end.  xmask
+// (optional): one bit per source, x read only where it is set.
 template <class Op, bool PROBE, typename RowEndT>
 int run_tile_gather(const TilePlan& p, const RowEndT* row_end, const int32_t* col,
-               const typename Op::T* x, int32_t nx, typename Op::T* out, cudaStream_t s) {
+                    const typename Op::T* x, int32_t nx, typename Op::T* out, cudaStream_t s,
+                    const uint32_t* xmask = nullptr) {
   if (p.ntiles == 0) return CG_OK;
-  gather_tile_kernel<Op, kTileThreads, kTileIPT, PROBE, RowEndT>
-      <<<(unsigned)p.ntiles, kTileThreads, 0, s>>>(
-          row_end, col, x, nx, p.tile_row, p.tile_edge, out,
-          reinterpret_cast<typename Op::T*>(p.carry), p.carry_row);
+  if (xmask)
+    gather_tile_kernel<Op, kTileThreads, kTileIPT, PROBE, RowEndT, true>
+        <<<(unsigned)p.ntiles, kTileThreads, 0, s>>>(
+            row_end, col, x, nx, p.tile_row, p.tile_edge, out,
+            reinterpret_cast<typename Op::T*>(p.carry), p.carry_row, xmask);
+  else
+    gather_tile_kernel<Op, kTileThreads, kTileIPT, PROBE, RowEndT>
+        <<<(unsigned)p.ntiles, kTileThreads, 0, s>>>(
+            row_end, col, x, nx, p.tile_row, p.tile_edge, out,
+            reinterpret_cast<typename Op::T*>(p.carry), p.carry_row);
   CG_LAUNCH_CHECK();
   carry_fixup_kernel<Op><<<grid_for(p.ntiles, 256, 4), 256, 0, s>>>(
       reinterpret_cast<const typename Op::T*>(p.carry), p.carry_row, p.ntiles, p.nrows, out);
