@@ -1013,7 +1013,7 @@ def run_bc(args):
         torch.cuda.synchronize()
         prep = time.time() - t0
         tune = {}
-        for alpha in (4.0, 16.0, 64.0):  # push/pull switch, timed on the first source
+        for alpha in (0.0, 2.0, 4.0, 16.0, 64.0):  # push/pull switch (0: push only), timed on two sources
             C.bc_set_direction(bc.h, alpha)
             bc.run(S[:1])
             a, z = ev(), ev()

@@ -10,9 +10,10 @@
 //         prefix sum of the frontier's out-degrees): an unvisited w gets level
 //         L+1 by compare-and-swap and joins the next frontier; every edge into
 //         a level-(L+1) vertex adds sigma[u] to sigma[w] with an FP64 atomic;
-//   pull (large frontier: the merge-path tile gather over the in-edge CSR of
-//         x = sigma on the frontier, 0 elsewhere): an unvisited v whose sum is
-//         non-zero gets level L+1 and sigma = the sum.
+//   pull (large frontier, bottom-up: the merge-path tile gather over the
+//         in-rows of the unvisited vertices, laid end to end, of x = sigma on
+//         the frontier, 0 elsewhere): an unvisited v whose sum is non-zero
+//         gets level L+1 and sigma = the sum.
 // sigma counts shortest paths: integers, exact in FP64 in any order below
 // 2^53, so levels and sigma do not depend on the direction or the order.
 // Pull is taken when (frontier out-edges) * alpha > E.
@@ -55,7 +56,6 @@ struct cg_bc {
   uint32_t* keys = nullptr;    // [V] sort scratch: their levels
   uint32_t* keys_out = nullptr;  // [V]
   int64_t* h_pin = nullptr;    // pinned host words for the per-level counts
-  cg::TilePlan in_plan;        // tiles of the in-edge CSR (8-byte carries)
   int32_t* vt_row = nullptr;   // tiles of a level's virtual CSR
   int32_t* vt_edge = nullptr;
   double* vt_carry = nullptr;
@@ -103,14 +103,15 @@ __global__ void bc_seed_kernel(int32_t s, int32_t* __restrict__ level, double* _
   *counter = 1;
 }
 
-// Row lengths of the out-edge CSR for the vertices of a list (taken from the
-// out-CSR's own offsets, so every expanded edge lies inside its row).
+// Row lengths in a CSR (off: the out- or in-edge offsets) for the vertices of
+// a list (taken from the expanded CSR's own offsets, so every expanded edge
+// lies inside its row).
 __global__ void list_degree_kernel(const int32_t* __restrict__ list, int64_t n,
-                                   const int64_t* __restrict__ out_off, int32_t* __restrict__ deg) {
+                                   const int64_t* __restrict__ off, int32_t* __restrict__ deg) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
     const int32_t u = list[i];
-    deg[i] = (int32_t)(out_off[u + 1] - out_off[u]);
+    deg[i] = (int32_t)(off[u + 1] - off[u]);
   }
 }
 
@@ -185,23 +186,46 @@ push_kernel(const int32_t* __restrict__ list, int64_t n, const int64_t* __restri
   }
 }
 
-// After a pull gather: an unvisited v with a non-zero sum is on level L+1.
-__global__ void pull_update_kernel(int32_t V, const double* __restrict__ acc, int32_t L,
+// Bottom-up step: the unvisited vertices that have in-edges (their IDs in
+// ascending order) ...
+__global__ void unvisited_flag_kernel(int32_t V, const int32_t* __restrict__ level,
+                                      const int64_t* __restrict__ in_off,
+                                      int32_t* __restrict__ flag) {
+  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < V;
+       v += (int64_t)gridDim.x * blockDim.x)
+    flag[v] = level[v] == -1 && in_off[v + 1] > in_off[v];
+}
+
+__global__ void unvisited_compact_kernel(int32_t V, const int32_t* __restrict__ level,
+                                         const int64_t* __restrict__ in_off,
+                                         const int64_t* __restrict__ pos,
+                                         int32_t* __restrict__ ids) {
+  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < V;
+       v += (int64_t)gridDim.x * blockDim.x)
+    if (level[v] == -1 && in_off[v + 1] > in_off[v]) ids[pos[v]] = (int32_t)v;
+}
+
+// ... and after the gather of their in-rows: one with a non-zero sum (a
+// frontier in-neighbour) is on level L+1.
+__global__ void pull_update_kernel(const int32_t* __restrict__ ids, int64_t n,
+                                   const double* __restrict__ acc, int32_t L,
                                    int32_t* __restrict__ level, double* __restrict__ sigma,
                                    int32_t* __restrict__ lists, int32_t* __restrict__ counter) {
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t v0 = (int64_t)blockIdx.x * blockDim.x; v0 < V; v0 += stride) {
-    const int64_t v = v0 + threadIdx.x;
+  for (int64_t i0 = (int64_t)blockIdx.x * blockDim.x; i0 < n; i0 += stride) {
+    const int64_t i = i0 + threadIdx.x;  // the warp stays converged for the append
     bool take = false;
-    if (v < V && level[v] == -1) {
-      const double a = acc[v];
+    int32_t v = 0;
+    if (i < n) {
+      v = ids[i];
+      const double a = acc[i];
       if (a != 0.0) {
         level[v] = L + 1;
         sigma[v] = a;
         take = true;
       }
     }
-    append(take, (int32_t)v, lists, counter);
+    append(take, v, lists, counter);
   }
 }
 
@@ -230,11 +254,12 @@ __global__ void deepest_kernel(const int32_t* __restrict__ list, int64_t n,
   }
 }
 
-// The out-rows of a level's vertices end to end, a tile per block.
+// The rows (of the CSR off / adj) of a list's vertices end to end, a tile per
+// block.
 __global__ void __launch_bounds__(kThreads)
 expand_kernel(const int32_t* __restrict__ list, int64_t n, const int64_t* __restrict__ rend,
               const int32_t* __restrict__ tile_row, const int32_t* __restrict__ tile_edge,
-              const int64_t* __restrict__ out_off, const int32_t* __restrict__ out_dst,
+              const int64_t* __restrict__ off, const int32_t* __restrict__ adj,
               int32_t* __restrict__ col_v) {
   __shared__ int64_t s_start[kTileItems + 1];
   int64_t r0, e0, e1;
@@ -242,7 +267,7 @@ expand_kernel(const int32_t* __restrict__ list, int64_t n, const int64_t* __rest
   if (cnt == 0) return;
   for (int64_t k = e0 + threadIdx.x; k < e1; k += blockDim.x) {
     const int j = tile_row_of(s_start, cnt, k);
-    col_v[k] = out_dst[out_off[list[r0 + j]] + (k - s_start[j])];
+    col_v[k] = adj[off[list[r0 + j]] + (k - s_start[j])];
   }
 }
 
@@ -364,6 +389,48 @@ int order_levels(cg_bc* h, int32_t depth, cudaStream_t s) {
   return radix_sort_pairs(h->keys, h->ids, h->keys_out, h->lists, n, bits, s);
 }
 
+// One bottom-up level: the unvisited vertices that have in-edges (ids, in
+// ID order) gather x = sigma on the frontier (0 elsewhere, tested through
+// xbits) over their in-rows laid end to end; a non-zero sum puts a vertex on
+// level L+1 with that sum as its path count.  Visited vertices' rows are
+// never read.
+int pull_level(cg_bc* h, int32_t L, cudaStream_t s) {
+  const int32_t V = h->V;
+  unvisited_flag_kernel<<<grid_for(V, kThreads), kThreads, 0, s>>>(V, h->level, h->in_off,
+                                                                    h->deg);
+  CG_LAUNCH_CHECK();
+  CG_TRY(exclusive_scan_i32_to_i64(h->deg, h->rend, V, s));
+  unvisited_compact_kernel<<<grid_for(V, kThreads), kThreads, 0, s>>>(V, h->level, h->in_off,
+                                                                       h->rend, h->ids);
+  CG_LAUNCH_CHECK();
+  int64_t n = 0, m = 0;
+  CG_TRY(read_i64(h, h->rend + V, &n, s));
+  if (n == 0) return CG_OK;
+  list_degree_kernel<<<grid_for(n, kThreads), kThreads, 0, s>>>(h->ids, n, h->in_off, h->deg);
+  CG_LAUNCH_CHECK();
+  CG_TRY(exclusive_scan_i32_to_i64(h->deg, h->rend, n, s));
+  CG_TRY(read_i64(h, h->rend + n, &m, s));
+  if (m == 0) return CG_OK;
+  int64_t ntiles = 0;
+  CG_TRY(level_tiles(h, n, m, &ntiles, s));
+  expand_kernel<<<(unsigned)ntiles, kThreads, 0, s>>>(h->ids, n, h->rend, h->vt_row, h->vt_edge,
+                                                      h->in_off, h->in_src, h->col_v);
+  CG_LAUNCH_CHECK();
+  gather_tile_kernel<SumF64, kTileThreads, kTileIPT, false, int64_t, true>
+      <<<(unsigned)ntiles, kTileThreads, 0, s>>>(h->rend + 1, h->col_v, h->xval, V, h->vt_row,
+                                                 h->vt_edge, h->acc, h->vt_carry,
+                                                 h->vt_carry_row, h->xbits);
+  CG_LAUNCH_CHECK();
+  carry_fixup_kernel<SumF64><<<grid_for(ntiles, 256, 4), 256, 0, s>>>(h->vt_carry,
+                                                                     h->vt_carry_row, ntiles, n,
+                                                                     h->acc);
+  CG_LAUNCH_CHECK();
+  pull_update_kernel<<<grid_for(n, kThreads), kThreads, 0, s>>>(h->ids, n, h->acc, L, h->level,
+                                                                h->sigma, h->lists, h->counter);
+  CG_LAUNCH_CHECK();
+  return CG_OK;
+}
+
 int run_source(cg_bc* h, int32_t src, double* bc, cudaStream_t s) {
   const int32_t V = h->V;
   bc_reset_kernel<<<grid_for(V, kThreads), kThreads, 0, s>>>(V, h->level, h->sigma, h->delta,
@@ -382,13 +449,8 @@ int run_source(cg_bc* h, int32_t src, double* bc, cudaStream_t s) {
     int64_t m = 0;
     CG_TRY(level_rows(h, list, n, &m, s));
     if (m > 0) {
-      if ((double)m * h->alpha > (double)h->E) {  // pull over the in-edge CSR
-        CG_TRY((run_tile_gather<SumF64, false, int64_t>(h->in_plan, h->in_off + 1, h->in_src,
-                                                        h->xval, V, h->acc, s, h->xbits)));
-        pull_update_kernel<<<grid_for(V, kThreads), kThreads, 0, s>>>(V, h->acc, L, h->level,
-                                                                      h->sigma, h->lists,
-                                                                      h->counter);
-        CG_LAUNCH_CHECK();
+      if ((double)m * h->alpha > (double)h->E) {  // pull (bottom-up)
+        CG_TRY(pull_level(h, L, s));
         ++h->pull_levels;
       } else {  // push from the frontier's out-edges
         int64_t ntiles = 0;
@@ -532,7 +594,6 @@ int bc_create(const int64_t* in_offsets, const int32_t* in_src, const int64_t* o
   if (e == cudaSuccess) e = cudaMalloc((void**)&h->keys_out, v4);
   if (e == cudaSuccess) e = cudaHostAlloc((void**)&h->h_pin, 2 * sizeof(int64_t), 0);
   int st = e == cudaSuccess ? CG_OK : cuda_fail(e, "bc_create", __FILE__, __LINE__);
-  if (st == CG_OK) st = plan_tiles<int64_t>(in_offsets + 1, V, E, &h->in_plan, stream, 8);
   if (st == CG_OK) {
     e = cudaStreamSynchronize(stream);
     if (e != cudaSuccess) st = cuda_fail(e, "bc_create", __FILE__, __LINE__);
@@ -551,7 +612,6 @@ int bc_destroy(cg_bc* h) {
   cudaGetDevice(&cur);
   if (cur != h->device) cudaSetDevice(h->device);
   cudaDeviceSynchronize();
-  free_tile_plan(&h->in_plan);
   cudaFree(h->level);
   cudaFree(h->sigma);
   cudaFree(h->delta);
