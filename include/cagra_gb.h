@@ -198,7 +198,9 @@ int pr_plan_bounds(const int32_t *dev_outdeg, int32_t V, int32_t smem_vertices,
  * segment's source values into shared memory and serves every read of the
  * segment from there.  The other segments are read through L1/L2 by a
  * second launch (1024 threads, 2 blocks per SM, no shared memory).  threads:
- * 512 or 1024; ctas_per_sm <= 2048/threads.  Results do not depend on it.
+ * 512 or 1024; ctas_per_sm <= 1024/threads (the staged kernel holds 64
+ * registers per thread): 1 at 1024 threads, 1 or 2 at 512.  Results do not
+ * depend on it; CG_ERR_INVALID_ARG otherwise (the previous shape stays).
  * Default after pr_build_segments: 1024, 1, -1.  Synchronizes the stream.
  */
 int pr_set_gather_config(cg_segmented *seg, int32_t threads, int32_t ctas_per_sm,
