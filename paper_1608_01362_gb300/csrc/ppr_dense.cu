@@ -27,8 +27,9 @@
 //           accumulators in tensor memory (64 columns), four K-steps per plane
 //           per chunk, issued by one thread and committed to an mbarrier;
 //   stages  three shared-memory stages (two CTAs per SM): the copies of
-//           chunk i+1 are in flight while chunk i is expanded (256 threads, a
-//           byte -> 8 BF16 lookup table) and the tensor cores work on i-1;
+//           chunks i+1 and i+2 are in flight while chunk i is expanded (256
+//           threads, a byte -> 8 BF16 lookup table) and the tensor cores work
+//           on i-1;
 //   sparse  64-source chunks with no edge in a tile's rows are skipped (a
 //           per-tile list built once);
 //   out     tcgen05.ld of the accumulators (warp w: rows 32w..32w+31), stored
@@ -55,7 +56,7 @@ constexpr int kTileB = kCols * kDK * 2;    // 8 KB per plane
 constexpr int kTileBits = kDM * kDK / 8;   // 1 KB of bitmap per tile chunk
 constexpr int kStage = kTileA + 2 * kTileB + kTileBits;  // 33 KB
 constexpr int kStages = 3;                 // shared-memory stages (two CTAs per SM fit)
-constexpr int kAhead = 1;                  // chunks whose copies are issued ahead
+constexpr int kAhead = 2;                  // chunks whose copies are issued ahead
 constexpr int kDThreads = 256;             // threads per CTA: two per destination row
 constexpr uint32_t kDenseWaitPolls = 1u << 26;
 
@@ -186,7 +187,7 @@ __device__ __forceinline__ uint32_t tile_off(int r, int k) {
 // adds the parts in order into rows 128t .. of out_rows.
 // bits_t: the bitmap tile-major, 1 KB (128 rows x 2 words) per (tile, chunk).
 // Pipeline over the part's chunks i (stage i % 3): thread 0 issues the bulk
-// copies of chunk i+1 (bitmap, B hi, B lo) once the MMAs of chunk i-2 that
+// copies of chunk i+2 (bitmap, B hi, B lo) once the MMAs of chunk i-1 that
 // read that stage are done (in general chunk i + kAhead after chunk
 // i + kAhead - kStages); all threads wait for chunk i's copies, expand the
 // A tile from the staged bitmap, and thread 0 issues chunk i's 8 MMAs and
