@@ -178,7 +178,11 @@ push_kernel(const int32_t* __restrict__ list, int64_t n, const int64_t* __restri
       const int j = tile_row_of(s_start, cnt, k);
       const int32_t u = list[r0 + j];
       w = out_dst[out_off[u] + (k - s_start[j])];
-      const int32_t old = atomicCAS(level + w, -1, L + 1);
+      // a target seen visited on an earlier level needs no atomic; one that
+      // reads unvisited takes the compare-and-swap (it may lose to another
+      // edge of this level, which then reads L + 1)
+      int32_t old = __ldcg(level + w);
+      if (old == -1) old = atomicCAS(level + w, -1, L + 1);
       take = old == -1;
       if (old == -1 || old == L + 1) atomicAdd(sigma + w, sigma[u]);
     }
