@@ -11,9 +11,9 @@
 //         L+1 by compare-and-swap and joins the next frontier; every edge into
 //         a level-(L+1) vertex adds sigma[u] to sigma[w] with an FP64 atomic;
 //   pull (large frontier, bottom-up: the merge-path tile gather over the
-//         in-rows of the unvisited vertices, laid end to end, of x = sigma on
-//         the frontier, 0 elsewhere): an unvisited v whose sum is non-zero
-//         gets level L+1 and sigma = the sum.
+//         in-rows of the unvisited vertices, read through their list, of
+//         x = sigma on the frontier, 0 elsewhere): an unvisited v whose sum is
+//         non-zero gets level L+1 and sigma = the sum.
 // sigma counts shortest paths: integers, exact in FP64 in any order below
 // 2^53, so levels and sigma do not depend on the direction or the order.
 // Pull is taken when (frontier out-edges) * alpha > E.
@@ -21,8 +21,9 @@
 // Backward phase, deepest level first: for every u at level L,
 //   delta[u] = sigma[u] * sum over out-neighbours w at level L+1 of
 //              (1 + delta[w]) / sigma[w]
-// as a gather over the out-rows of level L's vertices laid end to end (a
-// "virtual" CSR of that level), with x = (1 + delta) / sigma on level L+1 and
+// as a gather over the out-rows of level L's vertices taken in the order of
+// the level's list (a "virtual" CSR of that level: the tile gather reads each
+// edge through the list), with x = (1 + delta) / sigma on level L+1 and
 // 0 on every other level (out-neighbours of a level-L vertex lie at levels
 // <= L+1, and levels <= L are still 0), by the same tile gather; the level
 // lists are first put in (level, vertex ID) order, so the summation order is
@@ -50,7 +51,6 @@ struct cg_bc {
   int32_t* lists = nullptr;    // [V] reached vertices, level after level
   int32_t* deg = nullptr;      // [V] out-degrees of one level's vertices
   int64_t* rend = nullptr;     // [V+1] their exclusive prefix (rend[n] = total)
-  int32_t* col_v = nullptr;    // [E] their out-rows end to end
   int32_t* counter = nullptr;  // [1] next free position in lists
   int32_t* ids = nullptr;      // [V] sort scratch: reached vertices in ID order
   uint32_t* keys = nullptr;    // [V] sort scratch: their levels
@@ -258,23 +258,6 @@ __global__ void deepest_kernel(const int32_t* __restrict__ list, int64_t n,
   }
 }
 
-// The rows (of the CSR off / adj) of a list's vertices end to end, a tile per
-// block.
-__global__ void __launch_bounds__(kThreads)
-expand_kernel(const int32_t* __restrict__ list, int64_t n, const int64_t* __restrict__ rend,
-              const int32_t* __restrict__ tile_row, const int32_t* __restrict__ tile_edge,
-              const int64_t* __restrict__ off, const int32_t* __restrict__ adj,
-              int32_t* __restrict__ col_v) {
-  __shared__ int64_t s_start[kTileItems + 1];
-  int64_t r0, e0, e1;
-  const int cnt = load_tile_rows(rend, n, tile_row, tile_edge, s_start, r0, e0, e1);
-  if (cnt == 0) return;
-  for (int64_t k = e0 + threadIdx.x; k < e1; k += blockDim.x) {
-    const int j = tile_row_of(s_start, cnt, k);
-    col_v[k] = adj[off[list[r0 + j]] + (k - s_start[j])];
-  }
-}
-
 // delta of level L from the gathered sums; bc += delta (not for the source);
 // x = (1 + delta) / sigma for the next level up.
 __global__ void dependency_kernel(const int32_t* __restrict__ list, int64_t n,
@@ -417,13 +400,12 @@ int pull_level(cg_bc* h, int32_t L, cudaStream_t s) {
   if (m == 0) return CG_OK;
   int64_t ntiles = 0;
   CG_TRY(level_tiles(h, n, m, &ntiles, s));
-  expand_kernel<<<(unsigned)ntiles, kThreads, 0, s>>>(h->ids, n, h->rend, h->vt_row, h->vt_edge,
-                                                      h->in_off, h->in_src, h->col_v);
-  CG_LAUNCH_CHECK();
-  gather_tile_kernel<SumF64, kTileThreads, kTileIPT, false, int64_t, true>
-      <<<(unsigned)ntiles, kTileThreads, 0, s>>>(h->rend + 1, h->col_v, h->xval, V, h->vt_row,
+  // the in-rows of the listed vertices, read through the list (no copy)
+  gather_tile_kernel<SumF64, kTileThreads, kTileIPT, false, int64_t, true, true>
+      <<<(unsigned)ntiles, kTileThreads, 0, s>>>(h->rend + 1, nullptr, h->xval, V, h->vt_row,
                                                  h->vt_edge, h->acc, h->vt_carry,
-                                                 h->vt_carry_row, h->xbits);
+                                                 h->vt_carry_row, h->xbits, h->ids, h->in_off,
+                                                 h->in_src);
   CG_LAUNCH_CHECK();
   carry_fixup_kernel<SumF64><<<grid_for(ntiles, 256, 4), 256, 0, s>>>(h->vt_carry,
                                                                      h->vt_carry_row, ntiles, n,
@@ -497,14 +479,12 @@ int run_source(cg_bc* h, int32_t src, double* bc, cudaStream_t s) {
     if (m > 0) {
       int64_t ntiles = 0;
       CG_TRY(level_tiles(h, n, m, &ntiles, s));
-      expand_kernel<<<(unsigned)ntiles, kThreads, 0, s>>>(list, n, h->rend, h->vt_row,
-                                                          h->vt_edge, h->out_off, h->out_dst,
-                                                          h->col_v);
-      CG_LAUNCH_CHECK();
-      gather_tile_kernel<SumF64, kTileThreads, kTileIPT, false, int64_t, true>
-          <<<(unsigned)ntiles, kTileThreads, 0, s>>>(h->rend + 1, h->col_v, h->xval, V,
+      // the out-rows of level L's vertices, read through the level list
+      gather_tile_kernel<SumF64, kTileThreads, kTileIPT, false, int64_t, true, true>
+          <<<(unsigned)ntiles, kTileThreads, 0, s>>>(h->rend + 1, nullptr, h->xval, V,
                                                      h->vt_row, h->vt_edge, h->acc, h->vt_carry,
-                                                     h->vt_carry_row, h->xbits);
+                                                     h->vt_carry_row, h->xbits, list, h->out_off,
+                                                     h->out_dst);
       CG_LAUNCH_CHECK();
       carry_fixup_kernel<SumF64><<<grid_for(ntiles, 256, 4), 256, 0, s>>>(
           h->vt_carry, h->vt_carry_row, ntiles, n, h->acc);
@@ -591,7 +571,6 @@ int bc_create(const int64_t* in_offsets, const int32_t* in_src, const int64_t* o
   if (e == cudaSuccess) e = cudaMalloc((void**)&h->lists, v4);
   if (e == cudaSuccess) e = cudaMalloc((void**)&h->deg, v4);
   if (e == cudaSuccess) e = cudaMalloc((void**)&h->rend, sizeof(int64_t) * ((size_t)V + 1));
-  if (e == cudaSuccess) e = cudaMalloc((void**)&h->col_v, sizeof(int32_t) * (size_t)(E > 0 ? E : 1));
   if (e == cudaSuccess) e = cudaMalloc((void**)&h->counter, sizeof(int32_t));
   if (e == cudaSuccess) e = cudaMalloc((void**)&h->ids, v4);
   if (e == cudaSuccess) e = cudaMalloc((void**)&h->keys, v4);
@@ -625,7 +604,6 @@ int bc_destroy(cg_bc* h) {
   cudaFree(h->lists);
   cudaFree(h->deg);
   cudaFree(h->rend);
-  cudaFree(h->col_v);
   cudaFree(h->counter);
   cudaFree(h->ids);
   cudaFree(h->keys);

@@ -98,14 +98,23 @@ __global__ void tile_partition_kernel(const RowEndT* __restrict__ row_end, int64
 // MASKED: xmask holds one bit per source; x is read only where the bit is
 // set (the identity elsewhere), so a sparse x (a frontier) costs a bit test
 // from a small, cache-resident array instead of a value read per edge.
-template <class Op, int THREADS, int IPT, bool PROBE, typename RowEndT, bool MASKED = false>
+// VIRT: the rows are rows of another CSR (voff, vadj) taken in the order of
+// a vertex list vlist (row i = vertex vlist[i]; row_end: their lengths'
+// inclusive prefix); each edge's source is read through the list
+// (vadj[voff[vlist[i]] + position in the row]) instead of from col, so a
+// subset of a graph's rows is gathered without being copied out first.
+template <class Op, int THREADS, int IPT, bool PROBE, typename RowEndT, bool MASKED = false,
+          bool VIRT = false>
 __global__ void __launch_bounds__(THREADS)
 gather_tile_kernel(const RowEndT* __restrict__ row_end, const int32_t* __restrict__ col,
                    const typename Op::T* __restrict__ x, int32_t nx,
                    const int32_t* __restrict__ tile_row, const int32_t* __restrict__ tile_edge,
                    typename Op::T* __restrict__ out, typename Op::T* __restrict__ carry,
                    int32_t* __restrict__ carry_row,
-                   const uint32_t* __restrict__ xmask = nullptr) {
+                   const uint32_t* __restrict__ xmask = nullptr,
+                   const int32_t* __restrict__ vlist = nullptr,
+                   const int64_t* __restrict__ voff = nullptr,
+                   const int32_t* __restrict__ vadj = nullptr) {
   using T = typename Op::T;
   constexpr int TILE = THREADS * IPT;
   constexpr int WARPS = THREADS / 32;
@@ -136,13 +145,36 @@ gather_tile_kernel(const RowEndT* __restrict__ row_end, const int32_t* __restric
   const int nr = min(max(r1 - r0, 0), TILE);
   const int ne = min(max(e1 - e0, 0), TILE - nr);
 
-  // 1. edges: stream col, gather x
+  if constexpr (VIRT) {  // row ends first: each edge finds its row among them
+    for (int i = tid; i < nr; i += THREADS)
+      s_rend[pad32(i)] = (int32_t)((int64_t)row_end[r0 + i] - e0);
+    __syncthreads();
+  }
+  // 1. edges: stream col (or read the sources through the list), gather x
   {
     int32_t c[IPT];
+    if constexpr (VIRT) {
+      const int64_t start0 = r0 > 0 ? (int64_t)row_end[r0 - 1] : 0;  // row r0's first edge
 #pragma unroll
-    for (int u = 0; u < IPT; ++u) {
-      const int j = u * THREADS + tid;
-      c[u] = j < ne ? __ldcs(col + e0 + j) : -1;
+      for (int u = 0; u < IPT; ++u) {
+        const int j = u * THREADS + tid;
+        c[u] = -1;
+        if (j < ne) {
+          int lo = 0, hi = nr;  // rows of the tile ending at or before edge j
+          while (lo < hi) {
+            const int mid = (lo + hi) >> 1;
+            if (s_rend[pad32(mid)] <= j) lo = mid + 1; else hi = mid;
+          }
+          const int64_t start = lo == 0 ? start0 : (int64_t)e0 + s_rend[pad32(lo - 1)];
+          c[u] = __ldg(vadj + __ldg(voff + __ldg(vlist + r0 + lo)) + ((int64_t)e0 + j - start));
+        }
+      }
+    } else {
+#pragma unroll
+      for (int u = 0; u < IPT; ++u) {
+        const int j = u * THREADS + tid;
+        c[u] = j < ne ? __ldcs(col + e0 + j) : -1;
+      }
     }
     T v[IPT];
 #pragma unroll
@@ -159,8 +191,9 @@ gather_tile_kernel(const RowEndT* __restrict__ row_end, const int32_t* __restric
     }
   }
   // 2. row ends relative to e0 (in [0, ne] for the tile's rows)
-  for (int i = tid; i < nr; i += THREADS)
-    s_rend[pad32(i)] = (int32_t)((int64_t)row_end[r0 + i] - e0);
+  if constexpr (!VIRT)
+    for (int i = tid; i < nr; i += THREADS)
+      s_rend[pad32(i)] = (int32_t)((int64_t)row_end[r0 + i] - e0);
   __syncthreads();
 
   // 3. sequential walk over this thread's merged items
