@@ -175,6 +175,7 @@ batch_pagerank_kernel(BatchArgs a) {
   extern __shared__ __align__(16) float xs[];  // contrib, then the gathered sums
   __shared__ int s_g;
   __shared__ double s_red[2][WARPS];
+  __shared__ double s_D;
   const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
   for (;;) {
     __syncthreads();
@@ -283,21 +284,43 @@ batch_pagerank_kernel(BatchArgs a) {
       for (int v = tid; v < V; v += THREADS) xs[v] = 0.0f;
       __syncthreads();
       const int nrows = (int)(a.rbase[g + 1] - rb);
-      for (int r = tid; r < nrows; r += THREADS) {
-        const int32_t dv = a.idx[rb + r];
-        if ((uint32_t)dv < (uint32_t)V) xs[dv] = a.interm[rb + r];
+      for (int r0 = tid; r0 < nrows; r0 += THREADS * 4) {  // four rows' loads in flight
+        int32_t dv[4];
+        float val[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int r = r0 + u * THREADS;
+          dv[u] = r < nrows ? a.idx[rb + r] : -1;
+          val[u] = r < nrows ? a.interm[rb + r] : 0.0f;
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+          if ((uint32_t)dv[u] < (uint32_t)V) xs[dv[u]] = val[u];
       }
       __syncthreads();
       // 4. vertex update, next contrib, FP64 dangling mass and residual
       const float Dv = (float)(D * invV);
       float dpart = 0.0f, rpart = 0.0f;
-      for (int v = tid; v < V; v += THREADS) {
-        const float r = base + a.d * (xs[v] + Dv);
-        const float iv = inv[v];
-        rpart += fabsf(r - rank[v]);
-        rank[v] = r;
-        xs[v] = r * iv;
-        if (iv == 0.0f) dpart += r;
+      constexpr int U = 8;  // vertices per thread whose inputs are loaded together
+      for (int v0 = tid; v0 < V; v0 += THREADS * U) {
+        float iv[U], old[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          const int v = v0 + u * THREADS;
+          iv[u] = v < V ? inv[v] : 0.0f;
+          old[u] = v < V ? rank[v] : 0.0f;
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {  // the same vertex order as one at a time
+          const int v = v0 + u * THREADS;
+          if (v < V) {
+            const float r = base + a.d * (xs[v] + Dv);
+            rpart += fabsf(r - old[u]);
+            rank[v] = r;
+            xs[v] = r * iv[u];
+            if (iv[u] == 0.0f) dpart += r;
+          }
+        }
       }
       const double dd = warp_sum((double)dpart), rr = warp_sum((double)rpart);
       if (lane == 0) {
@@ -305,14 +328,20 @@ batch_pagerank_kernel(BatchArgs a) {
         s_red[1][w] = rr;
       }
       __syncthreads();
-      double Dn = 0.0, Rn = 0.0;
-      for (int q = 0; q < WARPS; ++q) {
-        Dn += s_red[0][q];
-        Rn += s_red[1][q];
+      // one thread adds the warps' sums in warp order (FP64 runs at a small
+      // fraction of the FP32 rate on this GPU: every thread repeating the loop
+      // cost more than the rest of the update) and shares the result
+      if (tid == 0) {
+        double Dn = 0.0, Rn = 0.0;
+        for (int q = 0; q < WARPS; ++q) {
+          Dn += s_red[0][q];
+          Rn += s_red[1][q];
+        }
+        s_D = Dn;
+        if (a.resid) a.resid[(int64_t)g * a.iters + it] = Rn;
       }
-      D = Dn;
-      if (tid == 0 && a.resid) a.resid[(int64_t)g * a.iters + it] = Rn;
       __syncthreads();
+      D = s_D;
     }
   }
 }
