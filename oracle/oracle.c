@@ -125,8 +125,10 @@ static double orc_gamma(double m, double u) {
  * summation tree).  With e_t[v] the bound after t iterations, the error of
  * the computed contributions is at most e_t[u]/outdeg(u) plus (2 u_acc +
  * u_store) c[u] (the reciprocal degree and the product round once each), the
- * dangling sum is off by at most the sum of e_t over dangling vertices, and
- * the update adds at most u_acc (4 d (S_v + Dsh_v) + r_{t+1}[v] + 7 Tsh_v),
+ * dangling sum is off by at most the sum of e_t over dangling vertices plus
+ * gamma_m D (the evaluation may form it from partial sums of up to m = 256
+ * ranks in the arithmetic format before adding those in FP64), and the
+ * update adds at most u_acc (4 d (S_v + Dsh_v) + r_{t+1}[v] + 7 Tsh_v),
  * where Dsh_v = D/V (uniform) or [v = seed] D is v's share of the dangling
  * mass and Tsh_v = (1-d)/V or [v = seed](1-d) its share of the teleport:
  * the conversion of the dangling share, the sum with S_v, the product with
@@ -138,7 +140,7 @@ static double orc_gamma(double m, double u) {
  *   e_{t+1}[v] = (1 + g + 4u)(1 + 2u + u_store) * P_v + (1 + g + 8u) * rho_v
  *   P_v   = d sum_{u -> v} e_t[u]/outdeg(u) + d * (seed < 0 ? Ed/V : [v = seed] Ed)
  *   rho_v = (g + 2u + u_store) d S_v + u (4 d (S_v + Dsh_v) + r_{t+1}[v] + 7 Tsh_v)
- *           + (gamma64_{n+8} + 2 gamma64_V) r_{t+1}[v]
+ *           + gamma_m d Dsh_v + (gamma64_{n+8} + 2 gamma64_V) r_{t+1}[v]
  * with g = gamma_{n-1}(u_acc), Ed = sum of e_t over dangling vertices, and
  * the gamma64 terms covering this FP64 evaluation's own rounding (and the
  * FP64 dangling sums on both sides).  e_0 = u_acc r_0 (1/V rounded once; the
@@ -156,6 +158,7 @@ int orc_pagerank_bound(int64_t V, const int64_t *offsets, const int32_t *src,
                        double *iter_seconds) {
     if (V < 1 || seed >= V) return -2;
     const double u64 = ldexp(1.0, -53);
+    const double gm = orc_gamma(256.0, u_acc);  /* FP32 partials of the dangling mass */
     int64_t *outdeg = (int64_t *)malloc((size_t)V * sizeof(int64_t));
     double *contrib = (double *)malloc((size_t)V * sizeof(double));
     double *next = (double *)malloc((size_t)V * sizeof(double));
@@ -195,7 +198,7 @@ int orc_pagerank_bound(int64_t V, const int64_t *offsets, const int32_t *src,
             const double Tsh = seed < 0 ? (1.0 - d) / (double)V : (v == seed ? 1.0 - d : 0.0);
             const double rho = (g + 2.0 * u_acc + u_store) * d * S +
                                u_acc * (4.0 * d * (S + Dsh) + next[v] + 7.0 * Tsh) +
-                               (orc_gamma(n + 8.0, u64) + gV) * next[v];
+                               gm * d * Dsh + (orc_gamma(n + 8.0, u64) + gV) * next[v];
             enext[v] = ((1.0 + g + 4.0 * u_acc) * (1.0 + 2.0 * u_acc + u_store) * P +
                         (1.0 + g + 8.0 * u_acc) * rho) * (1.0 + 1e-9);
         }

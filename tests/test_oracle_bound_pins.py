@@ -68,10 +68,12 @@ def _row_sums32(offsets, src, c, order, rng=None, drop=None):
 
 
 def _pagerank32(g, iters, seed=-1, order="forward", store=None, drop=None, rng_seed=0,
-                base_fp32=False):
+                base_fp32=False, dangling_parts=0):
     """The iteration evaluated in FP32 (FP64 dangling sum, as the GPU path).
     base_fp32: form (1-d)/V in FP32 from the rounded d (as the small-graph
-    batch kernel does) instead of rounding the FP64 value once."""
+    batch kernel does) instead of rounding the FP64 value once.
+    dangling_parts > 0: the dangling mass from FP32 partial sums of that many
+    consecutive dangling ranks, added in FP64 (as the GPU's update kernels)."""
     V = g.V
     rng = np.random.default_rng(rng_seed)
     outdeg = np.bincount(g.src, minlength=V)
@@ -88,6 +90,14 @@ def _pagerank32(g, iters, seed=-1, order="forward", store=None, drop=None, rng_s
         r[seed] = 1.0
     for _ in range(iters):
         Dm = float(np.sum(r[outdeg == 0].astype(np.float64)))
+        if dangling_parts > 0:
+            rd = r[outdeg == 0]
+            Dm = 0.0
+            for i in range(0, len(rd), dangling_parts):
+                part = np.float32(0.0)
+                for x in rd[i:i + dangling_parts]:
+                    part = np.float32(part + x)
+                Dm += float(part)
         c = (r * inv).astype(np.float32)
         if store is not None:
             c = store(c)
@@ -145,6 +155,18 @@ def test_fp32_evaluations_stay_inside_the_bound(name, order):
     want, bound = O.pagerank_bound(g.offsets, g.src, iters=20)
     for base_fp32 in (False, True):
         got = _pagerank32(g, 20, order=order, rng_seed=7, base_fp32=base_fp32)
+        err = np.abs(got.astype(np.float64) - want)
+        assert np.all(err <= bound), float(np.max(err / bound))
+
+
+@pytest.mark.parametrize("name", ["rmat10", "ragged"])
+def test_fp32_dangling_partials_stay_inside_the_bound(name):
+    """The bound covers a dangling mass formed from FP32 partial sums of up
+    to 256 ranks (the update kernels' per-lane partials) before FP64."""
+    g = GRAPHS[name]
+    want, bound = O.pagerank_bound(g.offsets, g.src, iters=20)
+    for parts in (16, 256):
+        got = _pagerank32(g, 20, order="forward", dangling_parts=parts)
         err = np.abs(got.astype(np.float64) - want)
         assert np.all(err <= bound), float(np.max(err / bound))
 
