@@ -57,7 +57,7 @@ constexpr int kTileBits = kDM * kDK / 8;   // 1 KB of bitmap per tile chunk
 constexpr int kStage = kTileA + 2 * kTileB + kTileBits;  // 33 KB
 constexpr int kStages = 3;                 // shared-memory stages (two CTAs per SM fit)
 constexpr int kAhead = 2;                  // chunks whose copies are issued ahead
-constexpr int kDThreads = 256;             // threads per CTA: two per destination row
+constexpr int kDThreads = 256;             // expander threads per CTA: two per destination row
 constexpr uint32_t kDenseWaitPolls = 1u << 26;
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -94,6 +94,14 @@ __device__ __forceinline__ void bulk_copy(void* dst, const void* src, uint32_t b
           "r"(smem_u32(dst)),
       "l"(src), "r"(bytes), "r"(smem_u32(bar))
       : "memory");
+}
+
+// Arrive on bar (release: this thread's earlier shared-memory writes are
+// visible to a thread that sees the phase complete).
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("{ .reg .b64 st;\n\tmbarrier.arrive.shared::cta.b64 st, [%0]; }" ::"r"(
+                   smem_u32(bar))
+               : "memory");
 }
 
 // Wait for the phase of parity ph; false after kDenseWaitPolls polls.
@@ -186,31 +194,37 @@ __device__ __forceinline__ uint32_t tile_off(int r, int k) {
 // its partial rows to partial[p][128t ..]; the tile's last part to finish
 // adds the parts in order into rows 128t .. of out_rows.
 // bits_t: the bitmap tile-major, 1 KB (128 rows x 2 words) per (tile, chunk).
-// Pipeline over the part's chunks i (stage i % 3): thread 0 issues the bulk
-// copies of chunk i+2 (bitmap, B hi, B lo) once the MMAs of chunk i-1 that
-// read that stage are done (in general chunk i + kAhead after chunk
-// i + kAhead - kStages); all threads wait for chunk i's copies, expand the
-// A tile from the staged bitmap, and thread 0 issues chunk i's 8 MMAs and
-// commits them to the stage's mbarrier.
-__global__ void __launch_bounds__(kDThreads, 2)
+// Warp-specialised pipeline over the part's chunks i (stage i % 3), linked by
+// mbarriers only (no block barrier per chunk):
+//   warps 0-7 (256 threads, two per destination row) wait for chunk i's
+//     copies (loaded[s]), expand the A tile from the staged bitmap and arrive
+//     on a_ready[s] (one arrival per warp);
+//   warp 8, one thread, waits for a_ready[s], issues chunk i's 8 MMAs and
+//     commits them to mma_done[s]; then issues the copies of chunk i + 2
+//     (bitmap, B hi, B lo) into the stage that chunk i - 1's MMAs read, once
+//     those are done (mma_done of chunk i - 1).
+// The expanders run up to two chunks ahead of the tensor cores.
+__global__ void __launch_bounds__(kDThreads + 32, 2)
 dense_tile_kernel(const uint32_t* __restrict__ bits_t, int32_t h, int parts,
                   const int32_t* __restrict__ tile_off_list, const int32_t* __restrict__ chunks,
                   const uint8_t* __restrict__ ct_hi, const uint8_t* __restrict__ ct_lo,
                   float* __restrict__ partial, unsigned* __restrict__ done,
                   float* __restrict__ out_rows, unsigned* __restrict__ fault) {
   extern __shared__ __align__(1024) uint8_t sm[];
-  __shared__ __align__(8) uint64_t bar_load[kStages], bar_mma[kStages];
+  __shared__ __align__(8) uint64_t bar_load[kStages], bar_ready[kStages], bar_mma[kStages];
   __shared__ uint32_t s_taddr;
   __shared__ uint4 s_lut[256];  // byte -> 8 BF16 values, 1.0 where the bit is set
   __shared__ bool s_last;
+  __shared__ int s_ok;
   const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
+  const bool expander = tid < kDThreads;  // warps 0-7; warp 8 copies and issues the MMAs
   const int t = blockIdx.x / parts, part = blockIdx.x % parts;
   const int nall = tile_off_list[t + 1] - tile_off_list[t];
   const int c0 = tile_off_list[t] + (int)((int64_t)part * nall / parts);
   const int nch = tile_off_list[t] + (int)((int64_t)(part + 1) * nall / parts) - c0;
   const int nchunk = h / kDK;
-  // epilogue: warp w holds TMEM lanes 32(w%4).. and columns 32(w/4)..
-  const int erow = 32 * (w & 3) + lane, ecol = 32 * (w >> 2);
+  // epilogue: warp w < 8 holds TMEM lanes 32(w%4).. and columns 32(w/4)..
+  const int erow = 32 * (w & 3) + lane, ecol = 32 * ((w >> 2) & 1);
   const int64_t dst = (int64_t)t * kDM + erow;  // hub destination of this thread's half row
   float4* prow = reinterpret_cast<float4*>(partial + ((int64_t)part * h + dst) * kCols + ecol);
   // the tile's parts: each stores its partial rows; the last part to finish
@@ -220,7 +234,7 @@ dense_tile_kernel(const uint32_t* __restrict__ bits_t, int32_t h, int parts,
     __syncthreads();
     if (tid == 0) s_last = atomicAdd(done + t, 1u) == (unsigned)parts - 1;
     __syncthreads();
-    if (!s_last) return;
+    if (!s_last || !expander) return;
     __threadfence();
     float4 acc[8];
     for (int q = 0; q < 8; ++q) acc[q] = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -238,12 +252,13 @@ dense_tile_kernel(const uint32_t* __restrict__ bits_t, int32_t h, int parts,
     if (tid == 0) done[t] = 0u;  // ready for the next launch
   };
   if (nch == 0) {  // no hub-block edge for this part
+    if (expander)
 #pragma unroll
-    for (int q = 0; q < 8; ++q) prow[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+      for (int q = 0; q < 8; ++q) prow[q] = make_float4(0.f, 0.f, 0.f, 0.f);
     finish();
     return;
   }
-  {
+  if (expander) {
     uint32_t p[4];
 #pragma unroll
     for (int q = 0; q < 4; ++q)
@@ -260,57 +275,61 @@ dense_tile_kernel(const uint32_t* __restrict__ bits_t, int32_t h, int parts,
   if (tid == 0) {
     for (int q = 0; q < kStages; ++q) {
       mbar_init(&bar_load[q], 1);
+      mbar_init(&bar_ready[q], kDThreads / 32);
       mbar_init(&bar_mma[q], 1);
     }
     fence_mbar_init();
+    s_ok = 1;
   }
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
   const uint32_t taddr = s_taddr;
-  // thread 0: the copies of chunk j into stage j % kStages
-  auto issue = [&](int j) {
-    uint8_t* st = sm + (j % kStages) * kStage;
-    uint64_t* bl = &bar_load[j % kStages];
-    const int c = chunks[c0 + j];
-    bulk_expect(bl, 2 * kTileB + kTileBits);
-    bulk_copy(st + kTileA, ct_hi + (int64_t)c * kTileB, kTileB, bl);
-    bulk_copy(st + kTileA + kTileB, ct_lo + (int64_t)c * kTileB, kTileB, bl);
-    bulk_copy(st + kTileA + 2 * kTileB,
-              reinterpret_cast<const uint8_t*>(bits_t) + ((int64_t)t * nchunk + c) * kTileBits,
-              kTileBits, bl);
-  };
-  if (tid == 0)
-    for (int j = 0; j < kAhead && j < nch; ++j) issue(j);
   bool ok = true;
-  for (int i = 0; i < nch && ok; ++i) {
-    const int s = i % kStages;
-    uint8_t* A = sm + s * kStage;
-    const uint8_t* Bh = A + kTileA;
-    const uint8_t* Bl = Bh + kTileB;
-    const uint32_t* Bt = reinterpret_cast<const uint32_t*>(Bl + kTileB);
-    if (tid == 0 && i + kAhead < nch) {
-      // the stage of chunk j = i + kAhead was last read by the MMAs of chunk j - kStages
-      const int j = i + kAhead, old = j - kStages;
-      if (old >= 0 && !mbar_wait(&bar_mma[old % kStages], (old / kStages) & 1)) ok = false;
-      if (ok) issue(j);
-    }
-    // chunk i's copies (bitmap, B tiles); its A stage was read by the MMAs of
-    // chunk i - kStages, which completed before chunk i's copies were issued
-    if (!mbar_wait(&bar_load[s], (i / kStages) & 1)) ok = false;
-    {  // thread t: row t/2, sources 32(t%2) .. 32(t%2)+31 (one bitmap word)
-      const int r = tid >> 1, hw = tid & 1;
-      const uint32_t word = Bt[2 * r + hw];
+  if (expander) {
+    for (int i = 0; i < nch; ++i) {
+      const int s = i % kStages;
+      uint8_t* A = sm + s * kStage;
+      const uint32_t* Bt = reinterpret_cast<const uint32_t*>(A + kTileA + 2 * kTileB);
+      // chunk i's copies landed (they were issued after the MMAs of chunk
+      // i - kStages, the last readers of this stage's A tile, were done)
+      if (!mbar_wait(&bar_load[s], (i / kStages) & 1)) {
+        ok = false;
+        break;
+      }
+      {  // thread t: row t/2, sources 32(t%2) .. 32(t%2)+31 (one bitmap word)
+        const int r = tid >> 1, hw = tid & 1;
+        const uint32_t word = Bt[2 * r + hw];
 #pragma unroll
-      for (int q = 0; q < 4; ++q)
-        *reinterpret_cast<uint4*>(A + tile_off(r, 32 * hw + 8 * q)) = s_lut[(word >> (8 * q)) & 0xFFu];
+        for (int q = 0; q < 4; ++q)
+          *reinterpret_cast<uint4*>(A + tile_off(r, 32 * hw + 8 * q)) = s_lut[(word >> (8 * q)) & 0xFFu];
+      }
+      fence_proxy_async_smem();  // the generic-proxy writes, before the MMAs read them
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&bar_ready[s]);
     }
-    fence_proxy_async_smem();
-    ok = __syncthreads_and(ok);
-    if (!ok) break;
-    if (tid == 0) {
+  } else if (lane == 0) {  // warp 8: copies and MMAs
+    auto issue = [&](int j) {  // the copies of chunk j into stage j % kStages
+      uint8_t* st = sm + (j % kStages) * kStage;
+      uint64_t* bl = &bar_load[j % kStages];
+      const int c = chunks[c0 + j];
+      bulk_expect(bl, 2 * kTileB + kTileBits);
+      bulk_copy(st + kTileA, ct_hi + (int64_t)c * kTileB, kTileB, bl);
+      bulk_copy(st + kTileA + kTileB, ct_lo + (int64_t)c * kTileB, kTileB, bl);
+      bulk_copy(st + kTileA + 2 * kTileB,
+                reinterpret_cast<const uint8_t*>(bits_t) + ((int64_t)t * nchunk + c) * kTileBits,
+                kTileBits, bl);
+    };
+    for (int j = 0; j < kAhead && j < nch; ++j) issue(j);
+    for (int i = 0; i < nch; ++i) {
+      const int s = i % kStages;
+      if (!mbar_wait(&bar_ready[s], (i / kStages) & 1)) {
+        ok = false;
+        break;
+      }
       tc_fence_after();
-      const uint32_t a0 = smem_u32(A), h0 = smem_u32(Bh), l0 = smem_u32(Bl);
+      const uint8_t* A = sm + s * kStage;
+      const uint32_t a0 = smem_u32(A), h0 = smem_u32(A + kTileA), l0 = smem_u32(A + kTileA + kTileB);
 #pragma unroll
       for (int kk = 0; kk < kDK / 16; ++kk) {
         const uint64_t ad = smem_desc(a0 + kk * 256, 128, 1024);
@@ -318,20 +337,35 @@ dense_tile_kernel(const uint32_t* __restrict__ bits_t, int32_t h, int parts,
         mma_bf16(taddr, ad, smem_desc(l0 + kk * 256, 128, 1024), 1u);
       }
       mma_commit(&bar_mma[s]);  // arrives once this thread's MMAs so far have completed
+      const int j = i + kAhead;
+      if (j < nch) {
+        // stage j % kStages was last read by the MMAs of chunk j - kStages
+        const int old = j - kStages;
+        if (old >= 0 && !mbar_wait(&bar_mma[old % kStages], (old / kStages) & 1)) {
+          ok = false;
+          break;
+        }
+        issue(j);
+      }
     }
   }
-  // the last chunk's commit covers every MMA issued before it
+  // the last chunk's commit covers every MMA issued before it; a thread that
+  // gave up waiting stops the others' epilogue through s_ok
+  if (!ok) atomicAnd(&s_ok, 0);
   const int last = nch - 1;
-  if (ok && !mbar_wait(&bar_mma[last % kStages], (last / kStages) & 1)) ok = false;
-  ok = __syncthreads_and(ok);
+  if (ok && expander && !mbar_wait(&bar_mma[last % kStages], (last / kStages) & 1))
+    atomicAnd(&s_ok, 0);
+  tc_fence_before();
+  __syncthreads();
   tc_fence_after();
-  if (ok) {
+  ok = s_ok != 0;
+  if (ok && expander) {
     float v[32];
     tmem_ld32(taddr + ((uint32_t)(32 * (w & 3)) << 16) + (uint32_t)ecol, v);
 #pragma unroll
     for (int q = 0; q < 8; ++q)
       prow[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
-  } else if (lane == 0) {
+  } else if (!ok && tid == 0) {
     atomicOr(fault, 1u);
   }
   tc_fence_before();
@@ -477,7 +511,7 @@ int ppr_dense_launch(cg_ppr* p, cudaStream_t s) {
   const int smem = kStages * kStage;
   CG_CUDA(cudaFuncSetAttribute((const void*)dense_tile_kernel,
                                cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-  dense_tile_kernel<<<(p->dense_h / kDM) * p->dense_parts, kDThreads, smem, s>>>(
+  dense_tile_kernel<<<(p->dense_h / kDM) * p->dense_parts, kDThreads + 32, smem, s>>>(
       p->dense_bits_t, p->dense_h, p->dense_parts, p->dense_tile_off, p->dense_tile_chunks,
       p->ct_hi, p->ct_lo, p->dense_partial, p->dense_done, p->interm + p->dense_rows0 * kCols,
       p->dense_fault_dev);
