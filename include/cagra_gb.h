@@ -682,7 +682,7 @@ int cg_transpose_csr(const int64_t *dev_in_offsets, const int32_t *dev_in_src, i
  * dev_in_src: the pull direction) and its out-edge CSR (dev_out_offsets,
  * dev_out_dst, e.g. from cg_transpose_csr: the push direction and the
  * dependency sums); both caller-owned, validated, and read for the handle's
- * lifetime.  The handle (library-owned, about 60 V + 4 E bytes) holds the
+ * lifetime.  The handle (library-owned, about 60 V bytes) holds the
  * per-source state.  CG_ERR_INVALID_ARG on bad sizes or CSRs.  Synchronizes.
  *
  * bc_run: for each of the nsources host vertex IDs (each in [0, V), repeats
@@ -690,12 +690,13 @@ int cg_transpose_csr(const int64_t *dev_in_offsets, const int32_t *dev_in_src, i
  * zero it before the first call to get the centrality of the whole set).
  * Each BFS level runs push (one thread per out-edge of the frontier, found
  * through a prefix sum of the frontier's degrees; level by compare-and-swap,
- * sigma by FP64 atomic adds) or pull (a merge-path tile gather over the
- * in-edges of sigma on the frontier, 0 elsewhere) as the frontier's
- * out-edges times alpha stay below or exceed E.  sigma values are integers
- * and exact in FP64 below 2^53, so levels and sigma are the same in any order
- * or direction; delta sums run in a fixed order (deterministic).  Reads two
- * counts per level on the host: synchronizes the stream.
+ * sigma by FP64 atomic adds) or pull, bottom-up (a merge-path tile gather
+ * over the in-edges of the unvisited vertices of sigma on the frontier, 0
+ * elsewhere) as the frontier's out-edges times alpha stay below or exceed E.
+ * sigma values are integers and exact in FP64 below 2^53, so levels and sigma
+ * are the same in any order or direction; delta sums run in a fixed order
+ * (deterministic).  Reads a few counts per level on the host: synchronizes
+ * the stream.
  *
  * bc_set_direction: alpha >= 0 (default 16; 0 always pushes, a huge value
  * pulls every level with a non-empty frontier).
