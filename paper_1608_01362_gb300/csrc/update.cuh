@@ -164,8 +164,23 @@ __device__ __forceinline__ void warp_vertex_update(const float* acc, int64_t v0,
       }
     }
   }
-  *dsum = warp_sum((double)dpart);
-  *rsum = warp_sum((double)rpart);
+  // the lanes' partials: summed in FP32 over groups of 2o lanes as long as a
+  // group's sum stays within 256 ranks (each lane holds at most ceil(n/32)),
+  // then the groups in FP64 (FP64 runs at a small fraction of the FP32 rate)
+  const int per_lane = (n + 31) >> 5;
+  int o = 16;
+  while (o >= 1 && 2 * o * per_lane > 256) o >>= 1;
+  for (int f = o; f >= 1; f >>= 1) {
+    dpart += __shfl_down_sync(0xffffffffu, dpart, f);
+    rpart += __shfl_down_sync(0xffffffffu, rpart, f);
+  }
+  double dd = (double)dpart, rr = (double)rpart;
+  for (int f = 16; f > o; f >>= 1) {
+    dd += __shfl_down_sync(0xffffffffu, dd, f);
+    rr += __shfl_down_sync(0xffffffffu, rr, f);
+  }
+  *dsum = dd;
+  *rsum = rr;
 }
 
 // Per-block FP64 partials, then the last block to finish reduces all
