@@ -322,7 +322,20 @@ batch_pagerank_kernel(BatchArgs a) {
           }
         }
       }
-      const double dd = warp_sum((double)dpart), rr = warp_sum((double)rpart);
+      // the lanes' partials in FP32 over groups of 2o lanes while a group
+      // holds at most 256 ranks (ceil(V / THREADS) per lane), then in FP64
+      const int per_lane = (V + THREADS - 1) / THREADS;
+      int o = 16;
+      while (o >= 1 && 2 * o * per_lane > 256) o >>= 1;
+      for (int f = o; f >= 1; f >>= 1) {
+        dpart += __shfl_down_sync(0xffffffffu, dpart, f);
+        rpart += __shfl_down_sync(0xffffffffu, rpart, f);
+      }
+      double dd = (double)dpart, rr = (double)rpart;
+      for (int f = 16; f > o; f >>= 1) {
+        dd += __shfl_down_sync(0xffffffffu, dd, f);
+        rr += __shfl_down_sync(0xffffffffu, rr, f);
+      }
       if (lane == 0) {
         s_red[0][w] = dd;
         s_red[1][w] = rr;
