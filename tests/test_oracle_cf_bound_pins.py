@@ -166,3 +166,21 @@ def test_selected_rows_equal_full_bound(case):
     assert sb is None
     np.testing.assert_allclose(sP, bP[us], rtol=1e-12, atol=0)
     np.testing.assert_allclose(sQ, bQ[it], rtol=1e-12, atol=0)
+
+
+def test_bf16_pair_storage_rounding_pinned():
+    """The storage readings the bounds rely on: a BF16 value is x rounded to
+    8 significant bits (relative error <= 2^-8), and a hi + lo pair is
+    within 2^-16 |x| of x with hi + lo exact in FP32 (so decoding the pair
+    adds no rounding)."""
+    rng = np.random.default_rng(3)
+    x = (rng.standard_normal(200_000) * np.exp2(rng.integers(-30, 30, 200_000))).astype(np.float32)
+    x = x[x != 0]
+    h = _bf16(x).astype(np.float64)
+    x64 = x.astype(np.float64)
+    assert np.all(np.abs(h - x64) <= O.U_BF16 * np.abs(x64))
+    hi = _bf16(x)
+    lo = _bf16((x - hi).astype(np.float32))
+    exact = hi.astype(np.float64) + lo.astype(np.float64)
+    assert np.array_equal((hi + lo).astype(np.float64), exact)  # the FP32 sum is exact
+    assert np.all(np.abs(exact - x64) <= O.U_BF16X2 * np.abs(x64))
