@@ -34,14 +34,33 @@ def _hilo(x):
     return (h + lo).astype(np.float32)
 
 
+def _add_toward_zero(a, b):
+    """FP32 a + b rounded toward zero, for non-negative a and b.  Their FP64
+    sum is exact when the exponents differ by at most 29; otherwise the
+    smaller operand lies below the FP32 result's last bit, FP64 rounds it
+    by less than that, and truncation drops it either way."""
+    y = a.astype(np.float64) + b.astype(np.float64)
+    f = y.astype(np.float32)
+    over = np.abs(f.astype(np.float64)) > np.abs(y)
+    f[over] = np.nextafter(f[over], np.float32(0.0))
+    return f
+
+
 def _row_sums32(offsets, src, c, order, rng=None, drop=None):
-    """Per-row FP32 sums of c[src[e]] in the given association order."""
+    """Per-row FP32 sums of c[src[e]] in the given association order
+    ("truncated": left to right, every addition rounded toward zero)."""
     V = len(offsets) - 1
     deg = np.diff(offsets)
     vals = c[src].astype(np.float32)
     if drop is not None:
         vals = vals.copy()
         vals[drop] = np.float32(0.0)
+    if order == "truncated":
+        acc = np.zeros(V, np.float32)
+        for j in range(int(deg.max(initial=0))):
+            m = deg > j
+            acc[m] = _add_toward_zero(acc[m], vals[offsets[:-1][m] + j])
+        return acc
     if order in ("forward", "reverse", "shuffled"):
         idx = np.arange(len(src))
         if order == "shuffled":
@@ -180,6 +199,38 @@ def test_personalised_column_with_stored_contributions_inside_the_bound(store, u
         for order in ("forward", "pairwise"):
             got = _pagerank32(g, 20, seed=seed, order=order, store=store)
             assert np.all(np.abs(got.astype(np.float64) - want) <= bound)
+
+
+@pytest.mark.parametrize("store,u_store", [(None, 0.0), (_hilo, O.U_BF16X2)])
+def test_truncating_row_sums_inside_the_doubled_unit_bound(store, u_store):
+    """The dense hub block's tensor-core sums may truncate instead of
+    rounding to nearest; the parity tests of that path take the bound with
+    u = 2^-23 (twice FP32's unit roundoff) for the row sums.  A personalised
+    column whose every row-sum addition rounds toward zero stays inside that
+    bound, and uses a visible share of it."""
+    worst = 0.0
+    for name in ("rmat10", "ragged", "cycle", "in_star"):
+        g = GRAPHS[name]
+        seed = int(np.argmax(np.bincount(g.src, minlength=g.V)))
+        want, bound = O.pagerank_bound(g.offsets, g.src, iters=20, seed=seed,
+                                       u_acc=2.0 ** -23, u_store=u_store)
+        got = _pagerank32(g, 20, seed=seed, order="truncated", store=store)
+        err = np.abs(got.astype(np.float64) - want)
+        assert np.all(err <= bound), (name, float(np.max(err / bound)))
+        m = bound > 0
+        worst = max(worst, float(np.max(err[m] / bound[m])))
+    assert worst >= 0.02
+
+
+def test_toward_zero_addition_never_rounds_up():
+    rng = np.random.default_rng(11)
+    a = rng.random(100_000).astype(np.float32)
+    b = (rng.random(100_000) * np.exp2(rng.integers(-30, 3, 100_000))).astype(np.float32)
+    t = _add_toward_zero(a, b).astype(np.float64)
+    exact = a.astype(np.float64) + b.astype(np.float64)
+    n = (a + b).astype(np.float64)  # numpy: round to nearest
+    assert np.all(t <= exact) and np.all(exact - t < np.spacing(t.astype(np.float32)))
+    assert np.any(t < n)  # differs from round-to-nearest where nearest rounds up
 
 
 def test_bound_is_not_vacuous():
