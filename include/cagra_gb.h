@@ -641,8 +641,11 @@ int pr_iterate_plain_noalloc(const int64_t *dev_offsets, const int32_t *dev_src,
  * over the rest's segmented graph (same V and vertex numbering).  dev_bits is
  * caller-owned and must stay valid while the handle is used.  From then on
  * ppr_batched_iterate also runs the tensor-core launch (phase 8 of
- * ppr_batched_step: one 128-thread CTA per 128 hub destinations; 64-source
- * chunks without an edge in a tile are skipped), and each merge phase repacks
+ * ppr_batched_step: the 64-source chunks of each 128-destination tile that
+ * hold an edge are split over up to 8 CTAs of eight expander warps and one
+ * MMA/copy warp, two CTAs per SM; the tile's last CTA to finish adds the
+ * parts in part order, so the result does not depend on timing), and each
+ * merge phase repacks
  * the hubs' contributions into the operand layout.  CG_ERR_UNSUPPORTED on a GPU without
  * tcgen05 (compute capability other than 10.x); CG_ERR_INVALID_ARG on a bad h
  * or a second attach.  A launch whose bounded waits (operand copies, tensor

@@ -14,22 +14,26 @@
 // the hub-block edges are removed from the segmented graph the gather walks
 // (cg_split_hub_block).
 //
-// Kernel (CTAs of 256 threads; each 128-destination tile's chunk list split
-// over `parts` CTAs, whose partial rows the tile's last CTA to finish adds in
-// part order, so the merge sees one dense row per hub destination):
+// Kernel (CTAs of 288 threads: eight expander warps and one MMA/copy warp;
+// each 128-destination tile's chunk list split over `parts` CTAs, whose
+// partial rows the tile's last CTA to finish adds in part order, so the merge
+// sees one dense row per hub destination):
 //   A tile  128 destinations x 64 sources, BF16 0/1, expanded into shared
-//           memory from the chunk's 1 KB of bitmap (thread t: destination t);
+//           memory from the chunk's 1 KB of bitmap by the expander warps (two
+//           threads per destination row, a byte -> 8 BF16 lookup table), which
+//           then arrive on the stage's bar_ready mbarrier;
 //   B tiles 64 columns x 64 sources for the hi and the lo plane, pre-packed
 //           in global memory in the operand layout (ppr_dense_pack, after each
 //           merge); bitmap and B tiles arrive by three bulk TMA copies per
-//           chunk, issued two chunks ahead;
+//           chunk, issued by one thread of the MMA/copy warp two chunks ahead
+//           once the stage's earlier MMAs have completed;
 //   MMA     tcgen05.mma.cta_group::1.kind::f16, M = 128, N = 64, K = 16, FP32
 //           accumulators in tensor memory (64 columns), four K-steps per plane
-//           per chunk, issued by one thread and committed to an mbarrier;
+//           per chunk, issued by that same thread when the stage is ready and
+//           committed to the stage's bar_mma mbarrier;
 //   stages  three shared-memory stages (two CTAs per SM): the copies of
-//           chunks i+1 and i+2 are in flight while chunk i is expanded (256
-//           threads, a byte -> 8 BF16 lookup table) and the tensor cores work
-//           on i-1;
+//           chunks i+1 and i+2 are in flight while chunk i is expanded and the
+//           tensor cores work on i-1; no block-wide barrier per chunk;
 //   sparse  64-source chunks with no edge in a tile's rows are skipped (a
 //           per-tile list built once);
 //   out     tcgen05.ld of the accumulators (warp w: rows 32w..32w+31), stored
@@ -197,12 +201,12 @@ __device__ __forceinline__ uint32_t tile_off(int r, int k) {
 // Warp-specialised pipeline over the part's chunks i (stage i % 3), linked by
 // mbarriers only (no block barrier per chunk):
 //   warps 0-7 (256 threads, two per destination row) wait for chunk i's
-//     copies (loaded[s]), expand the A tile from the staged bitmap and arrive
-//     on a_ready[s] (one arrival per warp);
-//   warp 8, one thread, waits for a_ready[s], issues chunk i's 8 MMAs and
-//     commits them to mma_done[s]; then issues the copies of chunk i + 2
+//     copies (bar_load[s]), expand the A tile from the staged bitmap and arrive
+//     on bar_ready[s] (one arrival per warp);
+//   warp 8, one thread, waits for bar_ready[s], issues chunk i's 8 MMAs and
+//     commits them to bar_mma[s]; then issues the copies of chunk i + 2
 //     (bitmap, B hi, B lo) into the stage that chunk i - 1's MMAs read, once
-//     those are done (mma_done of chunk i - 1).
+//     those are done (bar_mma of chunk i - 1).
 // The expanders run up to two chunks ahead of the tensor cores.
 __global__ void __launch_bounds__(kDThreads + 32, 2)
 dense_tile_kernel(const uint32_t* __restrict__ bits_t, int32_t h, int parts,
