@@ -122,6 +122,38 @@ def test_fig4_destination_sets_and_expansion_factor():
         assert set(cols.tolist()) <= set(members)
 
 
+@pytest.mark.parametrize("k", [1, 2, 3, 8, 30, 300])
+def test_expansion_factor_of_a_uniform_random_graph(k):
+    """Section III-D's model of q for a uniformly sparse graph: a segment of m
+    sources reaches a destination with probability 1 - (1 - p)^m, so
+    E[q] = sum over segments and destinations of that probability / V
+    (k (1 - (1 - p)^(V/k)) for equal segments; here with the self-loop the
+    cleaned graph drops, m - 1 for a destination inside its own segment).
+    The indicators are independent, so q of one directed G(V, p) sample lies
+    within a few standard deviations of E[q]; counting a segment's edges
+    instead of its distinct destinations (q = E/V, about 9) lies far outside
+    that band up to k = 30."""
+    V, p = 3000, 0.003
+    rng = np.random.default_rng(21)
+    adj = rng.random((V, V), dtype=np.float32) < p  # adj[u, v]: edge u -> v
+    u, v = np.nonzero(adj)
+    g = graphgen.from_edges(V, u, v)
+    q = O.build_segments(g.offsets, g.src, k=k, B=256).q
+    b = O.uniform_bounds(V, k)
+    mean = var = 0.0
+    for s in range(k):
+        m = int(b[s + 1] - b[s])
+        inside = 1.0 - (1.0 - p) ** (m - 1)   # destinations in the segment
+        outside = 1.0 - (1.0 - p) ** m
+        mean += m * inside + (V - m) * outside
+        var += m * inside * (1 - inside) + (V - m) * outside * (1 - outside)
+    mean, sd = mean / V, np.sqrt(var) / V
+    assert abs(q - mean) <= 6 * sd, (q, mean, sd)
+    assert q <= min(k, g.E / V)
+    if k <= 30:
+        assert abs(g.E / V - mean) > 20 * sd
+
+
 def _brute_segments(V, offsets, src, bounds):
     """Dictionary-of-lists restatement of Algorithm 2 for tiny graphs."""
     k = len(bounds) - 1
