@@ -136,7 +136,6 @@ class SegmentedPageRank(_PageRankBase):
         C.pr_iterate(self.seg, self.g.inv, rank_in, contrib_in, rank_out, contrib_out, damping,
                      iterations, self.dangling, resid)
 
-
     def run_ppr(self, seed: int, iterations: int = 20, damping: float = 0.85, resid=None):
         """Personalised PageRank of one seed (original ID): one-hot start,
         `iterations` iterations; returns (rank in original IDs, residuals)."""
@@ -222,7 +221,8 @@ def time_iterations(pr, iterations: int = 3, damping: float = 0.85, reps: int = 
     return times[len(times) // 2]
 
 
-def default_candidates(uniform_k=(1, 4), shapes=GATHER_SHAPES, min_deg=(4.0, 16.0, 24.0, 32.0, 48.0, 64.0, 256.0),
+def default_candidates(uniform_k=(1, 4), shapes=GATHER_SHAPES,
+                       min_deg=(4.0, 16.0, 24.0, 32.0, 48.0, 64.0, 256.0),
                        tables=(-1, 0), affine_deg=(16.0, 24.0, 32.0, 48.0)):
     """Autotuner search space: the paper's uniform split into k segments, and
     the GPU plan (shared-memory segments over the hot head, L2 segments over
