@@ -172,6 +172,16 @@ int pr_build_segments(const int64_t *dev_offsets, const int32_t *dev_src,
 int cg_segmented_get_info(const cg_segmented *seg, cg_segmented_info *info);
 
 /*
+ * The expansion factor of Section III-D alone: *q_rows_total = the subgraph
+ * rows summed over the segments (each segment's distinct destinations),
+ * *q = rows / V (0 for V = 0), *device_bytes = device memory the handle
+ * holds.  Any output pointer may be NULL.  Host only, no device work;
+ * CG_ERR_INVALID_ARG on a NULL handle.
+ */
+int cg_segmented_stats(const cg_segmented *seg, int64_t *q_rows_total, double *q,
+                       size_t *device_bytes);
+
+/*
  * Segment sizes for this GPU (Section III-D's segment-size choice, re-derived
  * for an SM's shared memory and the L2): after frequency-based clustering the
  * hottest sources come first, so the vertex range is cut into segments of
@@ -462,6 +472,11 @@ int pr_batch_set_threads(cg_batch *batch, int32_t threads);
  */
 int pr_batch_run(cg_batch *batch, int32_t iterations, double damping, float *dev_rank,
                  double *dev_resid, cudaStream_t stream);
+
+/* The same call as pr_batch_run, under the name of the batched small-graph
+ * form: same arguments, same launch, same errors. */
+int pr_batched_graphs_run(cg_batch *batch, int32_t iterations, double damping, float *dev_rank,
+                          double *dev_resid, cudaStream_t stream);
 
 /* ----------------------------------- batched personalised PageRank (64) */
 

@@ -26,13 +26,14 @@ EXPORTS = [
     "cg_status_string", "cg_last_error_message", "cg_version",
     "cg_out_degree", "cg_inv_outdeg", "cg_cluster", "cg_relabel_csr", "cg_permute4",
     "cg_permute_rows",
-    "pr_build_segments", "cg_segmented_get_info", "pr_plan_bounds", "pr_set_gather_config",
+    "pr_build_segments", "cg_segmented_get_info", "cg_segmented_stats", "pr_plan_bounds", "pr_set_gather_config",
     "pr_gather_table_capacity", "pr_set_gather_overlap", "cg_segmented_export",
     "cg_segmented_destroy", "cg_seg_gather", "cg_seg_gather_phases", "merge",
     "pr_init", "pr_contrib", "pr_iterate", "pr_merge_update", "pr_plain_create", "pr_plain_destroy", "pr_iterate_plain",
     "pr_iterate_plain_noalloc", "pr_noalloc_limits",
     "lp_iterate", "lp_run",
     "pr_batch_create", "pr_batch_destroy", "pr_batch_set_threads", "pr_batch_run",
+    "pr_batched_graphs_run",
     "pr_init_ppr", "pr_iterate_ppr",
     "ppr_batched_create", "ppr_batched_destroy", "ppr_batched_bytes", "ppr_batched_init",
     "ppr_batched_iterate", "ppr_batched_step",
@@ -84,6 +85,7 @@ def load(path: str | None = None):
             "pr_build_segments": (ctypes.c_int, [vp, vp, i32, i64, i32, vp, i32,
                                                  ctypes.POINTER(vp), vp]),
             "cg_segmented_get_info": (ctypes.c_int, [vp, ctypes.POINTER(SegInfo)]),
+            "cg_segmented_stats": (ctypes.c_int, [vp, vp, vp, vp]),
             "pr_plan_bounds": (ctypes.c_int, [vp, i32, i32, dbl, i32, i32, vp, vp, vp]),
             "pr_set_gather_config": (ctypes.c_int, [vp, i32, i32, i32, vp]),
             "pr_gather_table_capacity": (ctypes.c_int, [i32]),
@@ -111,6 +113,7 @@ def load(path: str | None = None):
             "pr_batch_destroy": (ctypes.c_int, [vp]),
             "pr_batch_set_threads": (ctypes.c_int, [vp, i32]),
             "pr_batch_run": (ctypes.c_int, [vp, i32, dbl, vp, vp, vp]),
+            "pr_batched_graphs_run": (ctypes.c_int, [vp, i32, dbl, vp, vp, vp]),
             "pr_init_ppr": (ctypes.c_int, [vp, i32, i32, vp, vp, vp, vp]),
             "pr_iterate_ppr": (ctypes.c_int, [vp, vp, vp, vp, vp, vp, dbl, i32, i32, vp, vp,
                                               vp]),
@@ -251,6 +254,13 @@ class Segmented:
         _check(load().cg_segmented_get_info(self.handle, ctypes.byref(inf)),
                "cg_segmented_get_info")
         return {f: getattr(inf, f) for f, _ in SegInfo._fields_}
+
+    def stats(self) -> tuple[int, float, int]:
+        """(subgraph rows, expansion factor q, device bytes held)."""
+        rows, q, nbytes = ctypes.c_int64(), ctypes.c_double(), ctypes.c_size_t()
+        _check(load().cg_segmented_stats(self.handle, ctypes.byref(rows), ctypes.byref(q),
+                                         ctypes.byref(nbytes)), "cg_segmented_stats")
+        return rows.value, q.value, nbytes.value
 
 
 def pr_build_segments(offsets, src, num_segments: int, bounds=None, merge_block: int = 512,
@@ -619,6 +629,12 @@ def pr_batch_set_threads(batch: Batch, threads: int):
 def pr_batch_run(batch: Batch, iterations: int, damping: float, rank, resid=None, stream=None):
     _check(load().pr_batch_run(batch.handle, iterations, damping, _ptr(rank), _ptr(resid),
                                _stream(stream)), "pr_batch_run")
+
+
+def pr_batched_graphs_run(batch: Batch, iterations: int, damping: float, rank, resid=None,
+                          stream=None):
+    _check(load().pr_batched_graphs_run(batch.handle, iterations, damping, _ptr(rank),
+                                        _ptr(resid), _stream(stream)), "pr_batched_graphs_run")
 
 
 def cg_split_hub_block(offsets, src, h: int, out_offsets, out_src, bits, stream=None) -> int:

@@ -597,4 +597,9 @@ int pr_batch_run(cg_batch* b, int32_t iterations, double damping, float* rank,
   return CG_OK;
 }
 
+int pr_batched_graphs_run(cg_batch* b, int32_t iterations, double damping, float* rank,
+                          double* resid, cudaStream_t stream) {
+  return pr_batch_run(b, iterations, damping, rank, resid, stream);
+}
+
 }  // extern "C"

@@ -534,6 +534,15 @@ int cg_segmented_get_info(const cg_segmented* g, cg_segmented_info* info) {
   return CG_OK;
 }
 
+int cg_segmented_stats(const cg_segmented* g, int64_t* q_rows_total, double* q,
+                       size_t* device_bytes) {
+  CG_ARG(g != nullptr, "cg_segmented_stats: null handle");
+  if (q_rows_total) *q_rows_total = g->rows;
+  if (q) *q = g->V ? (double)g->rows / (double)g->V : 0.0;
+  if (device_bytes) *device_bytes = (size_t)g->bytes;
+  return CG_OK;
+}
+
 int pr_set_gather_config(cg_segmented* g, int32_t threads, int32_t ctas_per_sm,
                          int32_t table_vertices, cudaStream_t stream) {
   CG_ARG(g != nullptr, "pr_set_gather_config: null handle");

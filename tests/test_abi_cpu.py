@@ -65,6 +65,9 @@ def test_status_strings_without_gpu(lib):
     st = lib.pr_build_segments(None, None, ctypes.c_int32(0), ctypes.c_int64(0), ctypes.c_int32(1),
                                None, ctypes.c_int32(16), ctypes.byref(out), None)
     assert st == -1 and b"V must be" in lib.cg_last_error_message()
+    q = ctypes.c_double(-1.0)
+    assert lib.cg_segmented_stats(None, None, ctypes.byref(q), None) == -1
+    assert b"null handle" in lib.cg_last_error_message() and q.value == -1.0
 
 
 def test_binding_refuses_without_library(tmp_path):

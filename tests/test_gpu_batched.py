@@ -69,6 +69,11 @@ def test_batched_cuda_graph_replay_and_determinism(C):
     graph.replay()
     torch.cuda.synchronize()
     assert torch.equal(bp.rank, first)
+    # the same launch under the batched small-graph name
+    bp.rank.zero_()
+    C.pr_batched_graphs_run(bp.batch, 20, 0.85, bp.rank)
+    torch.cuda.synchronize()
+    assert torch.equal(bp.rank, first)
 
 
 def test_batch_rejects_oversized_graph(C):

@@ -230,6 +230,9 @@ def test_segmented_pagerank_parity(C, torch_mod, rmat16, rmat16_oracle, k, clust
     check_pagerank(rank, want, bound, what=f"segmented k={k} cluster={cluster} B={B}")
     assert resid_ok(resid, want_resid)
     assert pr.info["num_segments"] == k
+    rows, q, nbytes = pr.seg.stats()
+    assert (rows, q, nbytes) == (pr.info["rows"], pr.info["q"], pr.info["device_bytes"])
+    assert q <= min(k, rmat16.E / rmat16.V)
 
 
 @pytest.mark.parametrize("k,cluster,B", [(1, None, 4096), (3, 0, 1000), (16, 1, 512),
