@@ -189,9 +189,10 @@ def bipartite(U: int = 480_189, I: int = 17_770, R: int = 99_000_000, mu: float 
 
 def small_graph_batch(count: int = 1024, seed: int = 1, scale_lo: int = 8, scale_hi: int = 15,
                       edge_factor: int = 16):
-    """`count` directed RMAT graphs; graph g has scale drawn uniformly in
-    [scale_lo, scale_hi] from stream (seed, g) and RMAT seed mix(seed ^ g)
-    (the first draw of that stream).  Returns a list of CSR."""
+    """`count` directed RMAT graphs.  Graph g takes two draws of SplitMix64
+    stream (seed, g): the first gives its scale, uniform in [scale_lo,
+    scale_hi] (the draw times the range count, high 64 bits), the second,
+    cut to 63 bits, its RMAT seed.  Returns a list of CSR."""
     out = []
     for g in range(count):
         d = splitmix_draws(seed, g, 2)

@@ -466,3 +466,19 @@ def test_rmat_quadrant_probabilities_at_every_level():
         db = (dst >> level) & 1
         share = np.bincount(2 * sb + db, minlength=4) / g.E
         assert np.all(np.abs(share - want) <= 0.005), (level, share)
+
+
+def test_small_graph_batch_scales_and_determinism():
+    """Graph g of the batch: scale from the first draw of stream (seed, g),
+    uniform over [scale_lo, scale_hi]; the same seed gives the same batch."""
+    a = graphgen.small_graph_batch(count=160, seed=1, scale_lo=5, scale_hi=8)
+    b = graphgen.small_graph_batch(count=160, seed=1, scale_lo=5, scale_hi=8)
+    scales = np.array([int(g.V).bit_length() - 1 for g in a])
+    assert all(g.V == 1 << s for g, s in zip(a, scales))
+    counts = np.bincount(scales, minlength=9)[5:]
+    assert counts.sum() == 160 and counts.min() >= 20  # every scale, roughly 40 each
+    for g, h in zip(a, b):
+        assert np.array_equal(g.offsets, h.offsets) and np.array_equal(g.src, h.src)
+    for i, s in enumerate(scales):
+        d = graphgen.splitmix_draws(1, i, 2)
+        assert 5 + ((int(d[0]) * 4) >> 64) == s
